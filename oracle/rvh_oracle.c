@@ -1,0 +1,325 @@
+/*
+ * rvh oracle -- TEST INFRASTRUCTURE ONLY (see rvh_oracle.h).
+ *
+ * Plain single-threaded FP64 C, built with -ffp-contract=off so that every
+ * multiply and add below rounds exactly where it is written; fused
+ * multiply-adds appear only as explicit fma() calls.
+ *
+ * Parity pins: the not-gpu tests check this file against closed forms
+ * (noise-free recovery), brute force on tiny clusters, exact symmetries and
+ * numpy's least squares; see tests/test_oracle.py.
+ */
+#include "rvh_oracle.h"
+
+#include <math.h>
+#include <stdlib.h>
+#include <string.h>
+
+/* ---------------------------------------------------------------------------
+ * Philox4x32-10 (Salmon, Moraes, Dror, Shaw, "Parallel random numbers: as
+ * easy as 1, 2, 3", SC'11).  Stands in for the "random numbers spanning
+ * indices for every cluster" that Alg. 1 takes as input.
+ * ------------------------------------------------------------------------- */
+void oracle_philox4x32_10(const uint32_t ctr[4], const uint32_t key[2], uint32_t out[4]) {
+  const uint32_t mult0 = 0xD2511F53u, mult1 = 0xCD9E8D57u;  /* round multipliers */
+  const uint32_t weyl0 = 0x9E3779B9u, weyl1 = 0xBB67AE85u;  /* key schedule increments */
+  uint32_t x0 = ctr[0], x1 = ctr[1], x2 = ctr[2], x3 = ctr[3];
+  uint32_t k0 = key[0], k1 = key[1];
+  for (int round = 0; round < 10; ++round) {
+    if (round > 0) {
+      k0 += weyl0;
+      k1 += weyl1;
+    }
+    uint64_t p0 = (uint64_t)mult0 * x0;
+    uint64_t p1 = (uint64_t)mult1 * x2;
+    uint32_t hi0 = (uint32_t)(p0 >> 32), lo0 = (uint32_t)p0;
+    uint32_t hi1 = (uint32_t)(p1 >> 32), lo1 = (uint32_t)p1;
+    uint32_t y0 = hi1 ^ x1 ^ k0;
+    uint32_t y1 = lo1;
+    uint32_t y2 = hi0 ^ x3 ^ k1;
+    uint32_t y3 = lo0;
+    x0 = y0; x1 = y1; x2 = y2; x3 = y3;
+  }
+  out[0] = x0; out[1] = x1; out[2] = x2; out[3] = x3;
+}
+
+/* floor(w * n / 2^32): a 32-bit random word scaled to [0, n). */
+static uint32_t scale_to_range(uint32_t w, uint32_t n) {
+  return (uint32_t)(((uint64_t)w * (uint64_t)n) >> 32);
+}
+
+int oracle_draw(uint64_t seed, int32_t cluster, int32_t h, int32_t n, int32_t k, int32_t* q) {
+  if (n < k || (k != 2 && k != 3)) return -1;
+  uint32_t ctr[4] = {(uint32_t)h, (uint32_t)cluster, 0u, 0u};
+  uint32_t key[2] = {(uint32_t)(seed & 0xFFFFFFFFu), (uint32_t)(seed >> 32)};
+  uint32_t w[4];
+  oracle_philox4x32_10(ctr, key, w);
+  /* first index uniform on [0, n); second uniform on the n-1 others */
+  uint32_t q0 = scale_to_range(w[0], (uint32_t)n);
+  uint32_t q1 = scale_to_range(w[1], (uint32_t)n - 1u);
+  if (q1 >= q0) q1 += 1u;
+  q[0] = (int32_t)q0;
+  q[1] = (int32_t)q1;
+  if (k == 3) {
+    /* third index uniform on the n-2 indices not yet taken */
+    uint32_t lo = q0 < q1 ? q0 : q1;
+    uint32_t hi = q0 < q1 ? q1 : q0;
+    uint32_t q2 = scale_to_range(w[2], (uint32_t)n - 2u);
+    if (q2 >= lo) q2 += 1u;
+    if (q2 >= hi) q2 += 1u;
+    q[2] = (int32_t)q2;
+  }
+  return 0;
+}
+
+/* The h-th k-subset (k = 2 or 3) of {0..n-1} in lexicographic order; returns
+ * -1 when h is past the last one.  Used by the brute-force tests. */
+static int enumerate_subset(int64_t h, int32_t n, int32_t k, int32_t* q) {
+  if (h < 0) return -1;
+  if (k == 2) {
+    for (int32_t a = 0; a < n - 1; ++a) {
+      int64_t span = n - 1 - a;
+      if (h < span) { q[0] = a; q[1] = a + 1 + (int32_t)h; return 0; }
+      h -= span;
+    }
+    return -1;
+  }
+  for (int32_t a = 0; a < n - 2; ++a) {
+    for (int32_t b = a + 1; b < n - 1; ++b) {
+      int64_t span = n - 1 - b;
+      if (h < span) { q[0] = a; q[1] = b; q[2] = b + 1 + (int32_t)h; return 0; }
+      h -= span;
+    }
+  }
+  return -1;
+}
+
+/* 2x2 determinant |x y; z w| = x*w - y*z, one rounding for the product y*z
+ * and one for the fused x*w - (y*z). */
+static double det2(double x, double y, double z, double w) {
+  return fma(x, w, -(y * z));
+}
+
+/* 3x3 determinant by cofactor expansion along row 0 (rows m0, m1, m2). */
+static double det3(const double* m0, const double* m1, const double* m2) {
+  double k0 = det2(m1[1], m1[2], m2[1], m2[2]);
+  double k1 = det2(m1[0], m1[2], m2[0], m2[2]);
+  double k2 = det2(m1[0], m1[1], m2[0], m2[1]);
+  return fma(m0[2], k2, fma(-m0[1], k1, m0[0] * k0));
+}
+
+/* Solve the k x k system with rows a[0..k-1] (a[i] has k entries) and right
+ * side w by Cramer's rule.  Returns the determinant; v is written only when
+ * |det| >= eps (the conditioning test).  NaN determinants are rejected. */
+static double cramer_solve(int k, const double* a0, const double* a1, const double* a2,
+                           const double* w, double eps, double* v, int* ok) {
+  if (k == 2) {
+    double det = det2(a0[0], a0[1], a1[0], a1[1]);
+    *ok = fabs(det) >= eps;
+    if (*ok) {
+      v[0] = det2(w[0], a0[1], w[1], a1[1]) / det;
+      v[1] = det2(a0[0], w[0], a1[0], w[1]) / det;
+      v[2] = 0.0;
+    }
+    return det;
+  }
+  double det = det3(a0, a1, a2);
+  *ok = fabs(det) >= eps;
+  if (*ok) {
+    for (int col = 0; col < 3; ++col) {
+      double r0[3] = {a0[0], a0[1], a0[2]};
+      double r1[3] = {a1[0], a1[1], a1[2]};
+      double r2[3] = {a2[0], a2[1], a2[2]};
+      r0[col] = w[0];
+      r1[col] = w[1];
+      r2[col] = w[2];
+      v[col] = det3(r0, r1, r2) / det;
+    }
+  }
+  return det;
+}
+
+/* Doppler residual of point row a (k entries) with Doppler w under velocity v:
+ * the deviation from Eq. (LSQ_eq), r = w - a.v. */
+static double residual(int k, const double* a, double w, const double* v) {
+  if (k == 2) return w - fma(v[0], a[0], v[1] * a[1]);
+  return w - fma(v[0], a[0], fma(v[1], a[1], v[2] * a[2]));
+}
+
+static void write_invalid(int32_t out, double* vx, double* vy, double* vz, double* heading,
+                          int32_t* inlier_count, int32_t* best, int32_t* status, int32_t bits) {
+  vx[out] = NAN;
+  vy[out] = NAN;
+  if (vz) vz[out] = NAN;
+  heading[out] = NAN;
+  inlier_count[out] = 0;
+  best[out] = -1;
+  status[out] = bits;
+}
+
+int oracle_estimate(const double* azimuth, const double* elevation, const double* doppler,
+                    const int32_t* offsets, int32_t n_clusters,
+                    const int32_t* subset, int32_t n_subset, const orc_params* p,
+                    double* vx, double* vy, double* vz, double* heading,
+                    int32_t* inlier_count, int32_t* best_hypothesis, int32_t* status,
+                    uint8_t* mask, int32_t* hyp_counts, uint8_t* fragile) {
+  if (!p || !offsets || !azimuth || !doppler || n_clusters < 0) return -1;
+  const int k = p->model_dim;
+  if (k != 2 && k != 3) return -1;
+  if ((k == 3) != (elevation != NULL)) return -1;
+  if (p->num_hypotheses < 1 || !(p->tau >= 0.0)) return -1;
+  const int32_t H = p->num_hypotheses;
+  const double tau = p->tau;
+  const int32_t n_out = subset ? n_subset : n_clusters;
+
+  for (int32_t oi = 0; oi < n_out; ++oi) {
+    const int32_t ci = subset ? subset[oi] : oi;
+    if (ci < 0 || ci >= n_clusters) return -1;
+    const int64_t o = offsets[ci];
+    const int32_t n = (int32_t)(offsets[ci + 1] - offsets[ci]);
+    if (fragile) fragile[oi] = 0;
+    for (int32_t q = 0; q < n; ++q) mask[o + q] = 0;
+    if (hyp_counts)
+      for (int32_t h = 0; h < H; ++h) hyp_counts[(int64_t)oi * H + h] = -1;
+
+    if (n < k) {
+      write_invalid(oi, vx, vy, vz, heading, inlier_count, best_hypothesis, status,
+                    ORC_TOO_FEW_POINTS);
+      continue;
+    }
+
+    /* Rows of A_i (Eq. eq:LSQPerCluster): (cos t, sin t) in 2D; with an
+     * elevation e, (cos t cos e, sin t cos e, sin e). */
+    double* a = (double*)malloc(sizeof(double) * 3 * (size_t)n);
+    double* w = (double*)malloc(sizeof(double) * (size_t)n);
+    int32_t* counts = (int32_t*)malloc(sizeof(int32_t) * (size_t)H);
+    double* hyp_v = (double*)malloc(sizeof(double) * 3 * (size_t)H);
+    for (int32_t q = 0; q < n; ++q) {
+      double t = azimuth[o + q];
+      double c = cos(t), s = sin(t);
+      if (k == 2) {
+        a[3 * q + 0] = c;
+        a[3 * q + 1] = s;
+        a[3 * q + 2] = 0.0;
+      } else {
+        double e = elevation[o + q];
+        double ce = cos(e), se = sin(e);
+        a[3 * q + 0] = c * ce;
+        a[3 * q + 1] = s * ce;
+        a[3 * q + 2] = se;
+      }
+      w[q] = doppler[o + q];
+    }
+
+    /* Alg. 1 for every trial h: draw the minimal set, solve it, count the
+     * points within tau.  The winner is the first trial with the largest
+     * count (Sec. III-A). */
+    int32_t best = -1, best_count = -1;
+    double min_det_margin = INFINITY;
+    for (int32_t h = 0; h < H; ++h) {
+      int32_t qs[3] = {0, 0, 0};
+      int drawn = p->enumerate ? enumerate_subset(h, n, k, qs)
+                               : oracle_draw(p->seed, ci, h, n, k, qs);
+      counts[h] = -1;
+      if (drawn != 0) continue;
+      double rhs[3] = {w[qs[0]], w[qs[1]], k == 3 ? w[qs[2]] : 0.0};
+      double v[3] = {0.0, 0.0, 0.0};
+      int ok = 0;
+      double det = cramer_solve(k, &a[3 * qs[0]], &a[3 * qs[1]], k == 3 ? &a[3 * qs[2]] : NULL,
+                                rhs, p->cond_eps, v, &ok);
+      double dm = fabs(fabs(det) - p->cond_eps);
+      if (dm < min_det_margin) min_det_margin = dm;
+      if (!ok) continue;
+      int32_t count = 0;
+      for (int32_t q = 0; q < n; ++q)
+        if (fabs(residual(k, &a[3 * q], w[q], v)) <= tau) ++count;
+      counts[h] = count;
+      hyp_v[3 * h + 0] = v[0];
+      hyp_v[3 * h + 1] = v[1];
+      hyp_v[3 * h + 2] = v[2];
+      if (count > best_count) {
+        best_count = count;
+        best = h;
+      }
+    }
+    if (hyp_counts)
+      for (int32_t h = 0; h < H; ++h) hyp_counts[(int64_t)oi * H + h] = counts[h];
+
+    int frag = min_det_margin < 1e-13;
+    if (best < 0) {
+      write_invalid(oi, vx, vy, vz, heading, inlier_count, best_hypothesis, status,
+                    ORC_ALL_DEGENERATE);
+      if (fragile) fragile[oi] = (uint8_t)frag;
+      free(a); free(w); free(counts); free(hyp_v);
+      continue;
+    }
+
+    /* Fragility log: any residual test of a trial that is within one of the
+     * winning count, decided within relative 1e-11 of tau. */
+    if (fragile) {
+      for (int32_t h = 0; h < H && !frag; ++h) {
+        if (counts[h] < 0 || counts[h] < best_count - 1) continue;
+        const double* v = &hyp_v[3 * h];
+        double scale = fabs(v[0]) + fabs(v[1]) + fabs(v[2]);
+        for (int32_t q = 0; q < n; ++q) {
+          double r = residual(k, &a[3 * q], w[q], v);
+          if (fabs(fabs(r) - tau) <= 1e-11 * (scale + fabs(w[q]) + tau)) { frag = 1; break; }
+        }
+      }
+    }
+
+    /* Inlier mask of the winner (the per-cluster mask; the frame mask of
+     * Sec. III-A is their union over clusters) and the refine sums over the
+     * inliers in index order: G = sum a a^T, g = sum a w. */
+    const double* vb = &hyp_v[3 * best];
+    int32_t n_in = 0;
+    double G[3][3] = {{0, 0, 0}, {0, 0, 0}, {0, 0, 0}};
+    double g[3] = {0, 0, 0};
+    for (int32_t q = 0; q < n; ++q) {
+      const double* aq = &a[3 * q];
+      if (!(fabs(residual(k, aq, w[q], vb)) <= tau)) continue;
+      mask[o + q] = 1;
+      ++n_in;
+      for (int r = 0; r < k; ++r) {
+        for (int c = r; c < k; ++c) G[r][c] = fma(aq[r], aq[c], G[r][c]);
+        g[r] = fma(aq[r], w[q], g[r]);
+      }
+    }
+    for (int r = 0; r < k; ++r)
+      for (int c = 0; c < r; ++c) G[r][c] = G[c][r];
+
+    /* Eq. (eq:LSQPerCluster): v = A^+ v_r = (A^T A)^-1 A^T v_r on the
+     * inliers, solved by Cramer's rule; singular or short systems fall back
+     * to the winning minimal-set velocity. */
+    double trace = 0.0;
+    for (int r = 0; r < k; ++r) trace += G[r][r];
+    double limit = 1e-12 * (k == 2 ? trace * trace : trace * trace * trace);
+    double vout[3] = {vb[0], vb[1], vb[2]};
+    int32_t st = 0;
+    double detG = k == 2 ? det2(G[0][0], G[0][1], G[1][0], G[1][1])
+                         : det3(G[0], G[1], G[2]);
+    if (fabs(fabs(detG) - limit) <= 1e-13 * (k == 2 ? trace * trace : trace * trace * trace))
+      frag = 1;
+    if (n_in >= k && fabs(detG) > limit) {
+      double vs[3];
+      int ok = 0;
+      cramer_solve(k, G[0], G[1], G[2], g, 0.0, vs, &ok);
+      vout[0] = vs[0];
+      vout[1] = vs[1];
+      vout[2] = k == 3 ? vs[2] : 0.0;
+    } else {
+      st |= ORC_LSQ_FALLBACK;
+    }
+
+    vx[oi] = vout[0];
+    vy[oi] = vout[1];
+    if (vz) vz[oi] = k == 3 ? vout[2] : 0.0;
+    heading[oi] = atan2(vout[1], vout[0]); /* Alg. 2 heading, quadrant-aware */
+    inlier_count[oi] = n_in;
+    best_hypothesis[oi] = best;
+    status[oi] = st;
+    if (fragile) fragile[oi] = (uint8_t)frag;
+    free(a); free(w); free(counts); free(hyp_v);
+  }
+  return 0;
+}

@@ -1,0 +1,81 @@
+/*
+ * rvh oracle -- TEST INFRASTRUCTURE ONLY.
+ *
+ * A plain, slow, single-threaded FP64 CPU restatement of the per-cluster
+ * velocity-profile RANSAC + least-squares refine of Singh, Sil and Sharma,
+ * "Parallelized Instantaneous Velocity and Heading Estimation of Objects
+ * using Single Imaging Radar" (arXiv 2012.12618):
+ *   - Alg. 1 (RANSAC kernel) and the winner rule of Sec. III-A, with the
+ *     cosine velocity-profile model of Eq. (LSQ_eq) as the hypothesis model;
+ *   - Eq. (LSQ_eq), Eq. (eq:LSQPerCluster) and Alg. 2 for the refine and the
+ *     heading.
+ *
+ * Only tests/, __graft_entry__.smoke() and the CPU-baseline leg of bench.py
+ * may load or call this library.  The CUDA product path shares no code with
+ * it and never calls it.
+ *
+ * Readings of the paper used here (each one is also listed in the design doc):
+ *   - hypotheses are exact minimal-set solves of the cosine model (2 points in
+ *     2D, 3 points in 3D), not the line fit in a normalised plane of Alg. 1;
+ *   - the residual is the Doppler residual |v_d - a.v| with the test
+ *     "|r| <= tau" (Alg. 1 thresholds with "<="), tau a fixed m/s value;
+ *   - the minimal sets come from Philox4x32-10 (Salmon et al., SC'11) keyed by
+ *     the seed, with counter (hypothesis, cluster, 0, 0), in place of the
+ *     host-side random index arrays that Alg. 1 requires;
+ *   - ties between trials go to the lowest hypothesis index (Sec. III-A picks
+ *     "the" trial with the most inliers and does not say which);
+ *   - the pseudo-inverse of Eq. (eq:LSQPerCluster) is computed through the
+ *     normal equations, with a fallback to the winning minimal-set velocity
+ *     when they are singular or have fewer than k rows;
+ *   - the heading is atan2(vy, vx) (Sec. III-B writes arctan(vy/vx)).
+ */
+#ifndef RVH_ORACLE_H
+#define RVH_ORACLE_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define ORC_TOO_FEW_POINTS 1
+#define ORC_ALL_DEGENERATE 2
+#define ORC_LSQ_FALLBACK 4
+
+typedef struct {
+  int32_t model_dim;      /* 2 or 3 */
+  int32_t num_hypotheses; /* H >= 1 */
+  double tau;             /* inlier iff |r| <= tau */
+  uint64_t seed;
+  double cond_eps;        /* minimal set rejected unless |det| >= cond_eps */
+  int32_t enumerate;      /* 0: Philox draws; 1: h-th k-subset, lexicographic */
+} orc_params;
+
+/* Philox4x32 with 10 rounds: out = Philox(ctr; key). */
+void oracle_philox4x32_10(const uint32_t ctr[4], const uint32_t key[2], uint32_t out[4]);
+
+/* The k distinct point indices (k = 2 or 3) of hypothesis h of a cluster of
+ * n points; q[0..k-1] in draw order.  Returns 0, or -1 if n < k. */
+int oracle_draw(uint64_t seed, int32_t cluster, int32_t h, int32_t n, int32_t k, int32_t* q);
+
+/* Estimate every cluster listed in `subset` (all clusters when subset is NULL).
+ * Inputs are FP64 (FP32 data widens exactly).  elevation == NULL means 2D.
+ * Per-cluster outputs are written at the cluster's position in the subset
+ * (its index when subset is NULL); mask is indexed by global point index and
+ * only the points of processed clusters are written.
+ * hyp_counts (optional) receives [n_out * H] exact counts (-1 = rejected).
+ * fragile (optional) receives 1 for a cluster where some decision that can
+ * change the outputs lies within rounding distance of its threshold.
+ * Returns 0, or -1 on invalid arguments. */
+int oracle_estimate(const double* azimuth, const double* elevation, const double* doppler,
+                    const int32_t* offsets, int32_t n_clusters,
+                    const int32_t* subset, int32_t n_subset, const orc_params* p,
+                    double* vx, double* vy, double* vz, double* heading,
+                    int32_t* inlier_count, int32_t* best_hypothesis, int32_t* status,
+                    uint8_t* mask, int32_t* hyp_counts, uint8_t* fragile);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif

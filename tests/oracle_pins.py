@@ -1,0 +1,287 @@
+"""Checks that pin the FP64 oracle to facts other than itself.
+
+Each check takes an oracle library handle (the built oracle, or a variant with
+a planted mistake, see test_oracle_mutants.py) and raises AssertionError on a
+violation.  What pins what:
+
+  philox      published known-answer vectors of Philox4x32-10 (SC'11)
+  draws       distinct, in-range and chi-square uniform minimal sets
+  recovery    closed form: noise-free clusters give back the true velocity
+              (Eq. LSQ_eq, Eq. eq:LSQPerCluster) and heading atan2(vy, vx)
+  brute       exhaustive all-pairs / all-triples RANSAC written with numpy
+              (np.linalg.solve per minimal set) on tiny clusters
+  symmetry    exact: azimuth -> -azimuth negates vy and the heading, keeps
+              the masks; Doppler and tau times 2^m scale the velocity by 2^m
+  rotation    azimuth -> azimuth + alpha rotates the velocity by alpha
+  lstsq       the refine equals numpy.linalg.lstsq on the inlier rows (the
+              least-squares comparator of the paper's Table II)
+  status      too-few-points, all-degenerate and least-squares fallback cases
+"""
+from __future__ import annotations
+
+import itertools
+import math
+import os
+
+import numpy as np
+
+import oracle
+from paper_2012_12618_gb300 import synth
+
+GOLDEN = os.path.join(os.path.dirname(os.path.abspath(__file__)), "golden")
+
+
+def _est(L, az, dop, off, **kw):
+    return oracle.estimate(az, dop, off, _lib=L, **kw)
+
+
+def check_philox(L):
+    path = os.path.join(GOLDEN, "philox4x32_10_kat.txt")
+    rows = [ln.split() for ln in open(path) if ln.strip() and not ln.startswith("#")]
+    assert len(rows) == 3
+    for r in rows:
+        words = [int(x, 16) for x in r]
+        out = oracle.philox4x32_10(words[0:4], words[4:6], _lib=L)
+        assert [int(x) for x in out] == words[6:10], (r, [hex(x) for x in out])
+
+
+def check_draws(L):
+    seed = 0x1234_5678_9ABC_DEF0
+    # the draw is the documented map of the Philox words: floor(w * n / 2^32) with skips
+    for h in range(50):
+        w = oracle.philox4x32_10([h, 7, 0, 0], [seed & 0xFFFFFFFF, seed >> 32], _lib=L)
+        n = 1000
+        q0 = (int(w[0]) * n) >> 32
+        q1 = (int(w[1]) * (n - 1)) >> 32
+        q1 += q1 >= q0
+        assert list(oracle.draw(seed, 7, h, n, 2, _lib=L)) == [q0, q1]
+    for n in (2, 3, 5, 17, 1000):
+        for h in range(300):
+            q = oracle.draw(seed, 3, h, n, 2, _lib=L)
+            assert q[0] != q[1] and 0 <= q.min() and q.max() < n
+            if n >= 3:
+                q = oracle.draw(seed, 3, h, n, 3, _lib=L)
+                assert len(set(q.tolist())) == 3 and 0 <= q.min() and q.max() < n
+    # chi-square uniformity of unordered pairs (n=5: 10 cells) and triples (n=6: 20 cells)
+    from scipy.stats import chisquare
+    for n, k, cells in ((5, 2, 10), (6, 3, 20)):
+        idx = {c: i for i, c in enumerate(itertools.combinations(range(n), k))}
+        counts = np.zeros(cells)
+        ordered = np.zeros((n, n))
+        for h in range(20000):
+            q = oracle.draw(99, 11, h, n, k, _lib=L)
+            counts[idx[tuple(sorted(q.tolist()))]] += 1
+            ordered[q[0], q[1]] += 1
+        assert chisquare(counts).pvalue > 1e-4, counts
+        # ordered first/second index: uniform over the n(n-1) ordered pairs
+        off = ordered[~np.eye(n, dtype=bool)]
+        assert chisquare(off).pvalue > 1e-4, ordered
+
+
+def _noise_free(rng, n, dim, v):
+    th = rng.uniform(-1.0, 1.0, n)
+    if dim == 2:
+        dop = v[0] * np.cos(th) + v[1] * np.sin(th)
+        return th, None, dop
+    el = rng.uniform(-0.26, 0.26, n)
+    dop = v[0] * np.cos(th) * np.cos(el) + v[1] * np.sin(th) * np.cos(el) + v[2] * np.sin(el)
+    return th, el, dop
+
+
+def check_recovery(L):
+    rng = np.random.default_rng(5)
+    for dim in (2, 3):
+        for trial in range(20):
+            v = rng.uniform(-30, 30, 3)
+            n = int(rng.integers(dim, 60))
+            th, el, dop = _noise_free(rng, n, dim, v)
+            o = _est(L, th, dop, [0, n], elevation=el, num_hypotheses=16, tau=0.1, seed=trial)
+            assert o["status"][0] == 0 or (n == dim and o["status"][0] == 0), o["status"]
+            assert o["inlier_count"][0] == n
+            assert abs(o["vx"][0] - v[0]) < 1e-10 and abs(o["vy"][0] - v[1]) < 1e-10
+            if dim == 3:
+                assert abs(o["vz"][0] - v[2]) < 1e-10
+            assert abs(o["heading"][0] - math.atan2(v[1], v[0])) < 1e-10
+
+
+def _brute(th, el, dop, tau, eps):
+    """All k-subsets in lexicographic order, each solved with np.linalg.solve."""
+    n = th.shape[0]
+    if el is None:
+        A = np.stack([np.cos(th), np.sin(th)], 1)
+    else:
+        A = np.stack([np.cos(th) * np.cos(el), np.sin(th) * np.cos(el), np.sin(el)], 1)
+    k = A.shape[1]
+    counts, vels, margin = [], [], np.inf
+    for q in itertools.combinations(range(n), k):
+        M = A[list(q)]
+        d = np.linalg.det(M)
+        margin = min(margin, abs(abs(d) - eps))
+        if not abs(d) >= eps:
+            counts.append(-1)
+            vels.append(None)
+            continue
+        v = np.linalg.solve(M, dop[list(q)])
+        r = np.abs(dop - A @ v)
+        margin = min(margin, np.min(np.abs(r - tau)))
+        counts.append(int((r <= tau).sum()))
+        vels.append(v)
+    return A, np.array(counts), vels, margin
+
+
+def check_brute(L):
+    rng = np.random.default_rng(11)
+    done = 0
+    while done < 24:
+        dim = 2 if done % 2 == 0 else 3
+        n = int(rng.integers(dim + 2, 11 if dim == 2 else 9))
+        v = rng.uniform(-20, 20, 3)
+        th, el, dop = _noise_free(rng, n, dim, v)
+        dop = dop + rng.normal(0, 0.05, n)
+        bad = rng.random(n) < 0.3
+        dop[bad] = rng.uniform(-40, 40, int(bad.sum()))
+        tau, eps = 0.1, (1e-4 if dim == 2 else 1e-6)
+        A, counts, vels, margin = _brute(th, el, dop, tau, eps)
+        if margin < 1e-9:
+            continue  # a decision too close to call across rounding orders
+        H = counts.shape[0]
+        o = _est(L, th, dop, [0, n], elevation=el, num_hypotheses=H, tau=tau, seed=1,
+                 cond_eps=eps, enumerate_subsets=True, want_counts=True)
+        assert np.array_equal(o["hyp_counts"][0], counts), (o["hyp_counts"][0], counts)
+        best = int(np.argmax(counts))          # first maximum
+        assert o["best_hypothesis"][0] == best
+        r = np.abs(dop - A @ vels[best])
+        assert np.array_equal(o["inlier_mask"].astype(bool), r <= tau)
+        # random draws can never beat the exhaustive search
+        o2 = _est(L, th, dop, [0, n], elevation=el, num_hypotheses=64, tau=tau, seed=done,
+                  cond_eps=eps, want_counts=True)
+        assert o2["hyp_counts"].max() <= counts.max()
+        assert o2["inlier_count"][0] == o2["hyp_counts"][0].max()
+        done += 1
+
+
+def _frame(name, n_clusters):
+    w = synth.WORKLOADS[name]
+    return w, synth.make_frame(w, n_clusters=n_clusters)
+
+
+def check_symmetry(L):
+    for name, nc in (("frame64", 48), ("dense3d", 12)):
+        w, f = _frame(name, nc)
+        kw = dict(num_hypotheses=w.num_hypotheses if name == "frame64" else 256, tau=w.tau, seed=3)
+        base = _est(L, f.azimuth, f.doppler, f.offsets, elevation=f.elevation, want_counts=True, **kw)
+        neg = _est(L, -f.azimuth.astype(np.float64), f.doppler, f.offsets, elevation=f.elevation,
+                   want_counts=True, **kw)
+        assert np.array_equal(base["hyp_counts"], neg["hyp_counts"])
+        assert np.array_equal(base["inlier_mask"], neg["inlier_mask"])
+        assert np.array_equal(base["best_hypothesis"], neg["best_hypothesis"])
+        assert np.array_equal(base["vx"], neg["vx"])
+        assert np.array_equal(base["vy"], -neg["vy"])
+        assert np.array_equal(base["vz"], neg["vz"])
+        assert np.array_equal(base["heading"], -neg["heading"])
+        for m in (-3, 5):
+            s = 2.0 ** m
+            sc = _est(L, f.azimuth, f.doppler.astype(np.float64) * s, f.offsets, elevation=f.elevation,
+                      want_counts=True, **dict(kw, tau=w.tau * s))
+            assert np.array_equal(base["hyp_counts"], sc["hyp_counts"])
+            assert np.array_equal(base["inlier_mask"], sc["inlier_mask"])
+            assert np.array_equal(base["vx"] * s, sc["vx"])
+            assert np.array_equal(base["vy"] * s, sc["vy"])
+            assert np.array_equal(base["vz"] * s, sc["vz"])
+            assert np.array_equal(base["heading"], sc["heading"])
+
+
+def check_rotation(L):
+    rng = np.random.default_rng(21)
+    for trial in range(20):
+        v = rng.uniform(-30, 30, 3)
+        n = 40
+        th, _, dop = _noise_free(rng, n, 2, v)
+        a = rng.uniform(-0.5, 0.5)
+        o = _est(L, th + a, dop, [0, n], num_hypotheses=8, tau=0.1, seed=trial)
+        ex = v[0] * math.cos(a) - v[1] * math.sin(a)
+        ey = v[0] * math.sin(a) + v[1] * math.cos(a)
+        assert abs(o["vx"][0] - ex) < 1e-10 and abs(o["vy"][0] - ey) < 1e-10
+        dh = (o["heading"][0] - (math.atan2(v[1], v[0]) + a) + math.pi) % (2 * math.pi) - math.pi
+        assert abs(dh) < 1e-10
+
+
+def check_lstsq(L):
+    for name, nc, H in (("frame64", 64, 256), ("dense3d", 16, 256)):
+        w, f = _frame(name, nc)
+        o = _est(L, f.azimuth, f.doppler, f.offsets, elevation=f.elevation, num_hypotheses=H,
+                 tau=w.tau, seed=1)
+        th = f.azimuth.astype(np.float64)
+        dop = f.doppler.astype(np.float64)
+        if f.elevation is None:
+            A = np.stack([np.cos(th), np.sin(th)], 1)
+        else:
+            el = f.elevation.astype(np.float64)
+            A = np.stack([np.cos(th) * np.cos(el), np.sin(th) * np.cos(el), np.sin(el)], 1)
+        checked = 0
+        for c in range(nc):
+            if o["status"][c] != 0:
+                continue
+            s, e = f.offsets[c], f.offsets[c + 1]
+            m = o["inlier_mask"][s:e].astype(bool)
+            assert m.sum() == o["inlier_count"][c]
+            ref = np.linalg.lstsq(A[s:e][m], dop[s:e][m], rcond=None)[0]
+            got = np.array([o["vx"][c], o["vy"][c], o["vz"][c]])[:A.shape[1]]
+            assert np.allclose(got, ref, rtol=1e-9, atol=1e-9), (c, got, ref)
+            assert abs(o["heading"][c] - math.atan2(ref[1], ref[0])) < 1e-9
+            checked += 1
+        assert checked >= nc // 2
+    # exactly k rows: the least-squares answer is the minimal solve
+    th = np.array([0.2, -0.7])
+    dop = np.array([3.0, -11.0])
+    o = _est(L, th, dop, [0, 2], num_hypotheses=4, tau=0.1, seed=9)
+    ref = np.linalg.solve(np.stack([np.cos(th), np.sin(th)], 1), dop)
+    assert o["status"][0] == 0 and o["inlier_count"][0] == 2
+    assert np.allclose([o["vx"][0], o["vy"][0]], ref, rtol=1e-12, atol=1e-12)
+
+
+def check_status(L):
+    # clusters of 0 and 1 points (2D), 2 points (3D): too few
+    th = np.array([0.1, 0.2, 0.3])
+    dop = np.array([1.0, 2.0, 3.0])
+    o = _est(L, th, dop, [0, 0, 1, 3], num_hypotheses=8, tau=0.1, seed=1)
+    assert list(o["status"][:2]) == [oracle.TOO_FEW_POINTS] * 2
+    assert o["status"][2] == 0
+    assert np.isnan(o["vx"][:2]).all() and list(o["best_hypothesis"][:2]) == [-1, -1]
+    o = _est(L, th[:2], dop[:2], [0, 2], elevation=np.zeros(2), num_hypotheses=8, tau=0.1, seed=1)
+    assert o["status"][0] == oracle.TOO_FEW_POINTS
+    # every point at one azimuth: every minimal set is singular
+    o = _est(L, np.full(6, 0.4), np.arange(6.0), [0, 6], num_hypotheses=32, tau=0.1, seed=1)
+    assert o["status"][0] == oracle.ALL_DEGENERATE and o["best_hypothesis"][0] == -1
+    assert o["inlier_mask"].sum() == 0 and np.isnan(o["heading"][0])
+    # tau = 0: winners with fewer than k inliers keep their minimal-set velocity
+    rng = np.random.default_rng(2)
+    seen = 0
+    for trial in range(40):
+        n = 12
+        th = rng.uniform(-1, 1, n)
+        dop = rng.uniform(-20, 20, n)
+        o = _est(L, th, dop, [0, n], num_hypotheses=8, tau=0.0, seed=trial, want_counts=True)
+        b = o["best_hypothesis"][0]
+        assert o["hyp_counts"][0][b] == o["hyp_counts"][0].max() == o["inlier_count"][0]
+        if o["inlier_count"][0] < 2:
+            assert o["status"][0] == oracle.LSQ_FALLBACK
+            q = oracle.draw(trial, 0, int(b), n, 2, _lib=L)
+            M = np.stack([np.cos(th[q]), np.sin(th[q])], 1)
+            ref = np.linalg.solve(M, dop[q])
+            assert np.allclose([o["vx"][0], o["vy"][0]], ref, rtol=1e-12, atol=1e-12)
+            seen += 1
+    assert seen > 0
+
+
+def check_planted(L):
+    w, f = _frame("frame64", 64)
+    o = _est(L, f.azimuth, f.doppler, f.offsets, num_hypotheses=w.num_hypotheses, tau=w.tau, seed=1)
+    m = o["inlier_mask"].astype(bool)
+    assert m[~f.outlier].mean() > 0.9 and m[f.outlier].mean() < 0.05
+    err = np.hypot(o["vx"] - f.truth_v[:, 0], o["vy"] - f.truth_v[:, 1])
+    assert np.median(err) < 0.05
+
+
+ALL_CHECKS = [check_philox, check_draws, check_recovery, check_brute, check_symmetry,
+              check_rotation, check_lstsq, check_status, check_planted]

@@ -1,0 +1,70 @@
+"""Planted mistakes in the oracle must trip at least one pin.
+
+Each case copies rvh_oracle.c, applies one plausible slip (a dropped term, a
+wrong sign or index, a transposed operand, an off-by-one in the draw, the
+wrong tie-break), compiles the copy on the CPU and runs the pins of
+oracle_pins.py against it.  A mutant that passes every pin would mean the
+pins cannot tell that slip from the real method.
+"""
+import os
+import subprocess
+
+import pytest
+
+import oracle
+from tests import oracle_pins
+
+MUTANTS = {
+    "det2_sign": ("return fma(x, w, -(y * z));", "return fma(x, w, (y * z));"),
+    "det3_cofactor_sign": ("fma(-m0[1], k1, m0[0] * k0)", "fma(m0[1], k1, m0[0] * k0)"),
+    "det3_minor_index": ("double k1 = det2(m1[0], m1[2], m2[0], m2[2]);",
+                         "double k1 = det2(m1[0], m1[2], m2[0], m2[1]);"),
+    "residual_transposed": ("return w - fma(v[0], a[0], v[1] * a[1]);",
+                            "return w - fma(v[0], a[1], v[1] * a[0]);"),
+    "residual_dropped_z": ("return w - fma(v[0], a[0], fma(v[1], a[1], v[2] * a[2]));",
+                           "return w - fma(v[0], a[0], v[1] * a[1]);"),
+    "rows_swapped": ("double c = cos(t), s = sin(t);", "double c = sin(t), s = cos(t);"),
+    "elev_row": ("a[3 * q + 2] = se;", "a[3 * q + 2] = ce;"),
+    "philox_no_key_bump": ("k0 += weyl0;", "k0 += 0u;"),
+    "philox_swapped_words": ("uint32_t y1 = lo1;", "uint32_t y1 = lo0;"),
+    "draw_skip_off_by_one": ("if (q1 >= q0) q1 += 1u;", "if (q1 > q0) q1 += 1u;"),
+    "draw3_skip_order": ("if (q2 >= lo) q2 += 1u;\n    if (q2 >= hi) q2 += 1u;",
+                         "if (q2 >= hi) q2 += 1u;\n    if (q2 >= lo) q2 += 1u;"),
+    "tiebreak_last": ("if (count > best_count) {", "if (count >= best_count) {"),
+    "refine_wrong_product": ("G[r][c] = fma(aq[r], aq[c], G[r][c]);",
+                             "G[r][c] = fma(aq[r], aq[r], G[r][c]);"),
+    "refine_dropped_rhs": ("g[r] = fma(aq[r], w[q], g[r]);", "g[r] = aq[r] * w[q];"),
+    "heading_swapped": ("heading[oi] = atan2(vout[1], vout[0]);",
+                        "heading[oi] = atan2(vout[0], vout[1]);"),
+    "cond_test_inverted": ("*ok = fabs(det) >= eps;\n    if (*ok) {\n      v[0]",
+                           "*ok = fabs(det) >= 0.5 * eps + 0.5;\n    if (*ok) {\n      v[0]"),
+    "fallback_limit_dropped": ("if (n_in >= k && fabs(detG) > limit) {",
+                               "if (fabs(detG) > 0.0) {"),
+}
+
+
+def _build_mutant(tmp_path, name):
+    src = open(oracle.SRC).read()
+    old, new = MUTANTS[name]
+    assert src.count(old) == 1, f"mutation site for {name} not unique in the oracle source"
+    mutated = tmp_path / f"{name}.c"
+    mutated.write_text(src.replace(old, new))
+    hdr = tmp_path / "rvh_oracle.h"
+    if not hdr.exists():
+        hdr.write_text(open(os.path.join(oracle.HERE, "rvh_oracle.h")).read())
+    so = tmp_path / f"lib{name}.so"
+    subprocess.run(["gcc", "-O2", "-std=c11", "-ffp-contract=off", "-fPIC", "-shared", "-w",
+                    "-o", str(so), str(mutated), "-lm"], check=True)
+    return oracle.load(str(so))
+
+
+@pytest.mark.parametrize("name", sorted(MUTANTS))
+def test_mutant_is_caught(tmp_path, name):
+    L = _build_mutant(tmp_path, name)
+    failed = []
+    for check in oracle_pins.ALL_CHECKS:
+        try:
+            check(L)
+        except (AssertionError, ValueError, FloatingPointError, IndexError, KeyError):
+            failed.append(check.__name__)
+    assert failed, f"mutant {name} passed every pin"
