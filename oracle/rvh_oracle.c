@@ -194,6 +194,7 @@ int oracle_estimate(const double* azimuth, const double* elevation, const double
     double* w = (double*)malloc(sizeof(double) * (size_t)n);
     int32_t* counts = (int32_t*)malloc(sizeof(int32_t) * (size_t)H);
     double* hyp_v = (double*)malloc(sizeof(double) * 3 * (size_t)H);
+    double* hyp_det = (double*)malloc(sizeof(double) * (size_t)H);
     for (int32_t q = 0; q < n; ++q) {
       double t = azimuth[o + q];
       double c = cos(t), s = sin(t);
@@ -229,6 +230,7 @@ int oracle_estimate(const double* azimuth, const double* elevation, const double
                                 rhs, p->cond_eps, v, &ok);
       double dm = fabs(fabs(det) - p->cond_eps);
       if (dm < min_det_margin) min_det_margin = dm;
+      hyp_det[h] = det;
       if (!ok) continue;
       int32_t count = 0;
       for (int32_t q = 0; q < n; ++q)
@@ -250,20 +252,23 @@ int oracle_estimate(const double* azimuth, const double* elevation, const double
       write_invalid(oi, vx, vy, vz, heading, inlier_count, best_hypothesis, status,
                     ORC_ALL_DEGENERATE);
       if (fragile) fragile[oi] = (uint8_t)frag;
-      free(a); free(w); free(counts); free(hyp_v);
+      free(a); free(w); free(counts); free(hyp_v); free(hyp_det);
       continue;
     }
 
-    /* Fragility log: any residual test of a trial that is within one of the
-     * winning count, decided within relative 1e-11 of tau. */
+    /* Fragility log: a residual test of a trial within one of the winning
+     * count whose margin |(|r| - tau)| is below what a few-ulp change of the
+     * row values (another libm's cos/sin) can move it: the trial's velocity
+     * moves by ~ulp * |v| / |det| and the residual by that times |a| <= 1. */
     if (fragile) {
       for (int32_t h = 0; h < H && !frag; ++h) {
         if (counts[h] < 0 || counts[h] < best_count - 1) continue;
         const double* v = &hyp_v[3 * h];
         double scale = fabs(v[0]) + fabs(v[1]) + fabs(v[2]);
+        double amp = 1e-14 * (1.0 + 1.0 / fabs(hyp_det[h]));
         for (int32_t q = 0; q < n; ++q) {
           double r = residual(k, &a[3 * q], w[q], v);
-          if (fabs(fabs(r) - tau) <= 1e-11 * (scale + fabs(w[q]) + tau)) { frag = 1; break; }
+          if (fabs(fabs(r) - tau) <= amp * (scale + fabs(w[q]) + tau)) { frag = 1; break; }
         }
       }
     }
@@ -319,7 +324,7 @@ int oracle_estimate(const double* azimuth, const double* elevation, const double
     best_hypothesis[oi] = best;
     status[oi] = st;
     if (fragile) fragile[oi] = (uint8_t)frag;
-    free(a); free(w); free(counts); free(hyp_v);
+    free(a); free(w); free(counts); free(hyp_v); free(hyp_det);
   }
   return 0;
 }
