@@ -1,0 +1,186 @@
+/*
+ * rvh.h -- radar velocity and heading: C ABI of the GB300 (sm_103a) library.
+ *
+ * The library estimates, for every cluster of an imaging-radar point cloud,
+ * the rigid-body velocity and heading of the object behind it, following
+ * Singh, Sil and Sharma, "Parallelized Instantaneous Velocity and Heading
+ * Estimation of Objects using Single Imaging Radar" (arXiv 2012.12618):
+ *
+ *   1. robust inlier detection by RANSAC (Sec. III-A, Alg. 1), one hypothesis
+ *      per trial, "max_trials x N_clusts" trials in parallel (Eq. 4);
+ *      the winning trial is the one with the most points within the
+ *      threshold, and the frame's inlier mask is the union of the per-cluster
+ *      masks (Sec. III-A, last paragraph);
+ *   2. the least-squares velocity v_i = A_i^+ v_r,i on the inliers
+ *      (Eq. LSQ_eq, Eq. eq:LSQPerCluster, Alg. 2);
+ *   3. the heading phi_i of (vx, vy) (Sec. III-B).
+ *
+ * Readings of the paper fixed by this interface:
+ *   - the hypothesis model is Eq. LSQ_eq itself, v_d = vx cos t + vy sin t
+ *     (2D), or vx cos t cos e + vy sin t cos e + vz sin e with an elevation e
+ *     (3D); a trial solves it exactly on 2 (3) points drawn without
+ *     replacement;
+ *   - a point is an inlier of a trial iff |v_d - a.v| <= inlier_threshold;
+ *   - the random minimal sets come from Philox4x32-10 (Salmon et al., SC'11)
+ *     with key (seed low word, seed high word) and counter
+ *     (hypothesis, cluster index within the frame, 0, 0); the first index is
+ *     floor(w0 * N / 2^32), the second floor(w1 * (N-1) / 2^32) skipping
+ *     the first, the third floor(w2 * (N-2) / 2^32) skipping the smaller and
+ *     then the larger of the two taken;
+ *   - a minimal set is rejected when |det| < cond_eps (its rows are unit
+ *     vectors, so |det| <= 1); rejected trials count -1;
+ *   - ties in the inlier count go to the lowest hypothesis index;
+ *   - the pseudo-inverse is taken through the FP64 normal equations of the
+ *     inliers; with fewer than k inliers, or |det(A^T A)| <= 1e-12 trace^k,
+ *     the winning minimal-set velocity is returned with RVH_STATUS_LSQ_FALLBACK;
+ *   - the heading is atan2(vy, vx) in (-pi, pi].
+ * Every inlier decision, count and winner index equals that of an FP64
+ * evaluation of the same formulas: scoring runs in FP32 with a rigorous
+ * per-trial error bound, and points whose FP32 residual is within the bound
+ * of the threshold are re-decided in FP64.
+ *
+ * Conventions: all functions return an RVH_* code (0 = success) unless noted.
+ * No function throws or aborts; no device-side trap or assert is used.
+ * Pointers may be host or device memory (detected per pointer); sizes are
+ * element counts.
+ */
+#ifndef RVH_H
+#define RVH_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* ---- return codes ---------------------------------------------------------------- */
+#define RVH_OK 0
+#define RVH_PENDING 1        /* rvh_poll: the ticket has not completed yet */
+#define RVH_EINVAL (-1)      /* invalid argument; nothing was launched */
+#define RVH_ENOMEM (-2)      /* the request does not fit the context's memory budget */
+#define RVH_EAGAIN (-3)      /* serving: budget or queue full right now; retry later */
+#define RVH_ECUDA (-4)       /* a CUDA call failed; rvh_last_error() has the message */
+#define RVH_ETIMEDOUT (-5)   /* rvh_wait: the ticket did not complete in time */
+
+/* ---- per-cluster status bits (rvh_result.status) --------------------------------- */
+#define RVH_STATUS_TOO_FEW_POINTS 1  /* N < k: no trial possible; outputs NaN, best -1 */
+#define RVH_STATUS_ALL_DEGENERATE 2  /* every minimal set failed the conditioning test */
+#define RVH_STATUS_LSQ_FALLBACK 4    /* normal equations singular or n_in < k */
+#define RVH_STATUS_BAD_OFFSETS 8     /* device-side CSR check failed for this cluster */
+
+typedef struct rvh_ctx rvh_ctx;
+
+/* One radar frame: structure-of-arrays points, grouped into clusters by CSR
+ * offsets (the clustering stage of Fig. 1 precedes this library).
+ * Cluster i owns points cluster_offsets[i] .. cluster_offsets[i+1]-1.
+ * Requirements: cluster_offsets[0] == 0, non-decreasing, and
+ * cluster_offsets[n_clusters] == n_points.  Host offsets are checked before
+ * any launch (RVH_EINVAL); device offsets are checked per cluster on the
+ * device (RVH_STATUS_BAD_OFFSETS, no out-of-range access). */
+typedef struct {
+  const float* azimuth;            /* [n_points] radians, measured from +x toward +y */
+  const float* elevation;          /* [n_points] radians, or NULL for the 2D model */
+  const float* doppler;            /* [n_points] m/s, the projected velocity v_r */
+  const int32_t* cluster_offsets;  /* [n_clusters + 1] */
+  int32_t n_clusters;              /* >= 0 */
+  int64_t n_points;                /* >= 0, < 2^31 */
+} rvh_frame;
+
+typedef struct {
+  int32_t model_dim;         /* 2 or 3; 3 requires elevation != NULL, 2 requires NULL */
+  int32_t num_hypotheses;    /* H >= 1: trials per cluster ("max_trials", Eq. 4) */
+  double inlier_threshold;   /* tau >= 0, m/s; inlier iff |residual| <= tau */
+  uint64_t seed;             /* Philox key */
+  double cond_eps;           /* minimal-set rejection; <= 0 selects 1e-4 (2D) / 1e-6 (3D) */
+} rvh_params;
+
+/* Caller-owned, caller-sized outputs.  Per-cluster arrays have n_clusters
+ * entries, inlier_mask has n_points.  vz may be NULL (it is written with 0
+ * for the 2D model when given). */
+typedef struct {
+  double* vx;                /* m/s, longitudinal (Sec. III-B) */
+  double* vy;                /* m/s, lateral */
+  double* vz;                /* m/s, vertical (3D model) */
+  double* heading;           /* rad, atan2(vy, vx) */
+  int32_t* inlier_count;     /* inliers of the winning trial */
+  int32_t* best_hypothesis;  /* winning trial index h, -1 if none */
+  int32_t* status;           /* RVH_STATUS_* bits */
+  uint8_t* inlier_mask;      /* 1 = inlier of its cluster's winning trial */
+} rvh_result;
+
+/* Creates a context on CUDA device `device` with its own stream.
+ * mem_budget_bytes (0 selects 4 GiB) caps the device memory the context
+ * allocates for scratch, staging and serving slots.  *out receives the
+ * context, or NULL on failure. */
+int rvh_create(rvh_ctx** out, int device, size_t mem_budget_bytes);
+
+/* Waits for the context's work, frees its memory, streams and events.
+ * NULL is ignored. */
+void rvh_destroy(rvh_ctx* ctx);
+
+/* Estimates one frame with the fused FP32/FP64-band persistent kernel.
+ * stream: a cudaStream_t, or NULL for the context's stream.
+ * When every input and output pointer is device memory the call is
+ * stream-ordered: it returns once the work is enqueued, and the results are
+ * valid after the stream reaches this point.  When any pointer is host
+ * memory, inputs are copied in and outputs copied back inside the call,
+ * which returns after the stream has completed.  A context's scratch is
+ * reused across calls; calls on one context are serialised on the device
+ * (a later call waits for the previous one). */
+int rvh_estimate(rvh_ctx* ctx, const rvh_frame* frame, const rvh_params* params,
+                 rvh_result* result, void* stream);
+
+/* The same computation and outputs with a plain all-FP64 GPU kernel, one
+ * launch per cluster (the baseline the fused kernel is measured against). */
+int rvh_estimate_baseline(rvh_ctx* ctx, const rvh_frame* frame, const rvh_params* params,
+                          rvh_result* result, void* stream);
+
+/* ---- streaming (serving) -------------------------------------------------------- */
+/* Queues a frame for continuous batching.  Host inputs are copied into the
+ * context's device pool before the call returns; device inputs must stay
+ * valid until the ticket completes.  Results are written to the caller's
+ * buffers (host or device) when the ticket completes.  RVH_EAGAIN: the pool
+ * or queue is full right now.  The frame is estimated with the same
+ * per-frame seed and cluster indices as rvh_estimate, so its results do not
+ * depend on which other frames share its batch. */
+int rvh_submit(rvh_ctx* ctx, const rvh_frame* frame, const rvh_params* params,
+               rvh_result* result, uint64_t* ticket);
+
+/* RVH_OK when the ticket has completed (its outputs are written), RVH_PENDING
+ * while it has not, RVH_EINVAL for an unknown ticket.  Never blocks. */
+int rvh_poll(rvh_ctx* ctx, uint64_t ticket);
+
+/* Blocks until the ticket completes or timeout_us passes (< 0: no limit);
+ * RVH_OK or RVH_ETIMEDOUT. */
+int rvh_wait(rvh_ctx* ctx, uint64_t ticket, int64_t timeout_us);
+
+/* Message of the last failing call on this thread ("" if none).  ctx may be NULL. */
+const char* rvh_last_error(rvh_ctx* ctx);
+
+/* ---- measurement and tuning ------------------------------------------------------ */
+typedef struct {
+  int64_t hypotheses;          /* trials scored (sum over clusters of H) */
+  int64_t pair_evals;          /* trial x point evaluations in the scoring pass */
+  int64_t candidates;          /* trials re-scored exactly (upper bound reached the lead) */
+  int64_t band_points;         /* point decisions taken in FP64 (inside the error band) */
+  int64_t fp64_hypotheses;     /* trials whose conditioning or bound needed FP64 */
+  float kernel_ms;             /* device time of the last fused launch (events) */
+  int32_t grid;                /* persistent CTAs of the last launch */
+  int32_t points_per_warp;     /* schedule of the last launch */
+  int32_t hyps_per_lane;
+} rvh_stats;
+
+/* Counters of the last rvh_estimate on this context (synchronises its stream). */
+int rvh_get_stats(rvh_ctx* ctx, rvh_stats* out);
+
+/* Fixes the scoring schedule: points_per_warp in {1, 8, 32} (lanes over points
+ * per trial group) and hyps_per_lane in {4, 8}; 0 restores the automatic
+ * choice. */
+int rvh_set_schedule(rvh_ctx* ctx, int32_t points_per_warp, int32_t hyps_per_lane);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* RVH_H */

@@ -1,0 +1,518 @@
+// C ABI of the rvh library (include/rvh.h): contexts, validation, the
+// estimate and baseline launch paths, statistics, and the serving loop.
+#include <algorithm>
+#include <atomic>
+#include <chrono>
+#include <cmath>
+#include <condition_variable>
+#include <cstring>
+#include <deque>
+#include <map>
+#include <mutex>
+#include <string>
+#include <thread>
+#include <vector>
+
+#include <cuda_runtime.h>
+
+#include "rvh.h"
+#include "rvh_kernels.h"
+#include "rvh_runtime.h"
+
+namespace {
+
+thread_local std::string g_err;
+
+int fail(int code, const std::string& msg) {
+  g_err = msg;
+  return code;
+}
+
+#define RVH_CUDA(x)                                                                           \
+  do {                                                                                        \
+    cudaError_t e_ = (x);                                                                     \
+    if (e_ != cudaSuccess) return fail(RVH_ECUDA, std::string(#x) + ": " + cudaGetErrorString(e_)); \
+  } while (0)
+
+constexpr size_t kAlign = 256;
+size_t align_up(size_t x) { return (x + kAlign - 1) & ~(kAlign - 1); }
+
+bool is_device_ptr(const void* p) {
+  if (!p) return false;
+  cudaPointerAttributes at{};
+  if (cudaPointerGetAttributes(&at, p) != cudaSuccess) {
+    cudaGetLastError();
+    return false;
+  }
+  return at.type == cudaMemoryTypeDevice || at.type == cudaMemoryTypeManaged;
+}
+
+// Host-side argument checks shared by every entry point.
+int check_args(const rvh_frame* f, const rvh_params* p, const rvh_result* r) {
+  if (!f || !p || !r) return fail(RVH_EINVAL, "frame, params and result must be non-NULL");
+  if (f->n_clusters < 0) return fail(RVH_EINVAL, "n_clusters < 0");
+  if (f->n_points < 0 || f->n_points > 0x7fffffffLL) return fail(RVH_EINVAL, "n_points out of range [0, 2^31)");
+  if (p->model_dim != 2 && p->model_dim != 3) return fail(RVH_EINVAL, "model_dim must be 2 or 3");
+  if ((p->model_dim == 3) != (f->elevation != nullptr))
+    return fail(RVH_EINVAL, "model_dim 3 needs elevation, model_dim 2 needs elevation == NULL");
+  if (p->num_hypotheses < 1) return fail(RVH_EINVAL, "num_hypotheses must be >= 1");
+  if (std::isnan(p->inlier_threshold) || p->inlier_threshold < 0)
+    return fail(RVH_EINVAL, "inlier_threshold must be >= 0");
+  if (std::isnan(p->cond_eps)) return fail(RVH_EINVAL, "cond_eps is NaN");
+  if (f->n_points > 0 && (!f->azimuth || !f->doppler)) return fail(RVH_EINVAL, "azimuth/doppler NULL");
+  if (f->n_clusters > 0 && !f->cluster_offsets) return fail(RVH_EINVAL, "cluster_offsets NULL");
+  if (f->n_clusters > 0 && (!r->vx || !r->vy || !r->heading || !r->inlier_count || !r->best_hypothesis || !r->status))
+    return fail(RVH_EINVAL, "result arrays NULL");
+  if (f->n_points > 0 && !r->inlier_mask) return fail(RVH_EINVAL, "inlier_mask NULL");
+  if (f->n_clusters == 0 && f->n_points != 0) return fail(RVH_EINVAL, "points without clusters");
+  return RVH_OK;
+}
+
+int check_host_offsets(const int32_t* off, int32_t n, int64_t n_points) {
+  if (off[0] != 0) return fail(RVH_EINVAL, "cluster_offsets[0] != 0");
+  for (int32_t i = 0; i < n; ++i)
+    if (off[i + 1] < off[i]) return fail(RVH_EINVAL, "cluster_offsets not non-decreasing at " + std::to_string(i));
+  if ((int64_t)off[n] != n_points) return fail(RVH_EINVAL, "cluster_offsets[n_clusters] != n_points");
+  return RVH_OK;
+}
+
+double default_eps(int dim) { return dim == 2 ? 1e-4 : 1e-6; }
+
+rvh::TauPair tau_pair(double tau) {
+  float f = (float)tau;
+  rvh::TauPair t;
+  t.lo = ((double)f > tau) ? std::nextafter(f, -INFINITY) : f;
+  t.hi = ((double)f < tau) ? std::nextafter(f, INFINITY) : f;
+  return t;
+}
+
+float round_up_f(double x) {
+  float f = (float)x;
+  return ((double)f < x) ? std::nextafter(f, INFINITY) : f;
+}
+float round_down_f(double x) {
+  float f = (float)x;
+  return ((double)f > x) ? std::nextafter(f, -INFINITY) : f;
+}
+
+}  // namespace
+
+// ---------------------------------------------------------------------------------------
+struct ServeReq;
+
+struct rvh_ctx {
+  int device = 0;
+  size_t budget = 0;
+  size_t used = 0;
+  int sms = 0;
+  cudaStream_t stream = nullptr;
+  // scratch of rvh_estimate / rvh_estimate_baseline
+  void* scratch = nullptr;
+  size_t scratch_bytes = 0;
+  cudaEvent_t last_done = nullptr;
+  cudaEvent_t ev0 = nullptr, ev1 = nullptr;
+  unsigned long long* stats_d = nullptr;
+  bool have_launch = false;
+  rvh_stats last{};
+  int pw_fixed = 0, hpl_fixed = 0;
+  int nmax_smem = 2048;
+  int hchunk = 1024;
+  int occ[4] = {0, 0, 0, 0};
+  std::mutex mu;  // serialises rvh_estimate calls on this context
+  rvh::Server* server = nullptr;
+};
+
+namespace rvh {
+
+int ctx_alloc(rvh_ctx* ctx, void** p, size_t bytes) {
+  if (ctx->used + bytes > ctx->budget)
+    return fail(RVH_ENOMEM, "memory budget exceeded (" + std::to_string(ctx->used + bytes) + " > " +
+                                std::to_string(ctx->budget) + " bytes)");
+  cudaError_t e = cudaMalloc(p, bytes);
+  if (e != cudaSuccess) {
+    cudaGetLastError();
+    return fail(RVH_ENOMEM, std::string("cudaMalloc: ") + cudaGetErrorString(e));
+  }
+  ctx->used += bytes;
+  return RVH_OK;
+}
+
+void ctx_free(rvh_ctx* ctx, void* p, size_t bytes) {
+  if (!p) return;
+  cudaFree(p);
+  ctx->used -= bytes;
+}
+
+int ctx_device(rvh_ctx* ctx) { return ctx->device; }
+int ctx_sms(rvh_ctx* ctx) { return ctx->sms; }
+
+void choose_schedule(rvh_ctx* ctx, int H, int* pw, int* hpl) {
+  if (ctx->pw_fixed) {
+    *pw = ctx->pw_fixed;
+    *hpl = ctx->hpl_fixed ? ctx->hpl_fixed : 4;
+    return;
+  }
+  if (H >= 1024) {
+    *pw = 1;
+    *hpl = 4;
+  } else {
+    *pw = 8;
+    *hpl = 4;
+  }
+}
+
+// Fills the per-frame descriptor; the pointers must already be device pointers.
+void fill_desc(FrameDesc& d, const rvh_frame& f, const rvh_params& p, const float* az, const float* el,
+               const float* dop, const int32_t* off, float4* rows_g, const rvh_result& out) {
+  const int dim = p.model_dim;
+  const double eps = p.cond_eps > 0 ? p.cond_eps : default_eps(dim);
+  const double eD = (dim == 2 ? 1.081e-6 : 6.20e-6) + 0x1p-50;
+  d.az = az;
+  d.el = el;
+  d.dop = dop;
+  d.offsets = off;
+  d.n_clusters = f.n_clusters;
+  d.H = p.num_hypotheses;
+  d.n_points = f.n_points;
+  d.rows_g = rows_g;
+  d.tau = p.inlier_threshold;
+  d.eps = eps;
+  d.tau32 = tau_pair(p.inlier_threshold);
+  d.acc = round_up_f(eps + eD);
+  d.rej = (eps - eD > 0) ? round_down_f(eps - eD) : -1.0f;
+  d.key = make_uint2((uint32_t)(p.seed & 0xFFFFFFFFu), (uint32_t)(p.seed >> 32));
+  d.vx = out.vx;
+  d.vy = out.vy;
+  d.vz = out.vz;
+  d.heading = out.heading;
+  d.inlier_count = out.inlier_count;
+  d.best = out.best_hypothesis;
+  d.status = out.status;
+  d.mask = out.inlier_mask;
+}
+
+int configure_dim(rvh_ctx* ctx, int dim) {
+  const size_t smem = fused_smem_bytes(ctx->nmax_smem, ctx->hchunk);
+  if (ctx->occ[dim] == 0) {
+    RVH_CUDA(fused_configure(dim, smem));
+    int b = 0;
+    RVH_CUDA(fused_occupancy(dim, smem, &b));
+    ctx->occ[dim] = std::max(1, b);
+  }
+  return RVH_OK;
+}
+
+// Launches worklist + fused kernel for a prepared batch.
+int launch_batch(rvh_ctx* ctx, FusedArgs& a, int dim, cudaStream_t s, cudaEvent_t t0, cudaEvent_t t1) {
+  int rc = configure_dim(ctx, dim);
+  if (rc) return rc;
+  const size_t smem = fused_smem_bytes(ctx->nmax_smem, ctx->hchunk);
+  a.nmax_smem = ctx->nmax_smem;
+  a.hchunk = ctx->hchunk;
+  const int grid = std::max(1, std::min(ctx->sms * ctx->occ[dim], a.n_items));
+  RVH_CUDA(launch_worklist(a, s));
+  if (t0) RVH_CUDA(cudaEventRecord(t0, s));
+  RVH_CUDA(launch_fused(dim, a, grid, smem, s));
+  if (t1) RVH_CUDA(cudaEventRecord(t1, s));
+  ctx->last.grid = grid;
+  return RVH_OK;
+}
+
+}  // namespace rvh
+
+using namespace rvh;
+
+extern "C" {
+
+int rvh_create(rvh_ctx** out, int device, size_t mem_budget_bytes) {
+  if (!out) return fail(RVH_EINVAL, "out is NULL");
+  *out = nullptr;
+  int n = 0;
+  cudaError_t e = cudaGetDeviceCount(&n);
+  if (e != cudaSuccess || n == 0) {
+    cudaGetLastError();
+    return fail(RVH_ECUDA, std::string("no CUDA device: ") + (e != cudaSuccess ? cudaGetErrorString(e) : "count 0"));
+  }
+  if (device < 0 || device >= n) return fail(RVH_EINVAL, "device index out of range");
+  RVH_CUDA(cudaSetDevice(device));
+  rvh_ctx* c = new rvh_ctx();
+  c->device = device;
+  c->budget = mem_budget_bytes ? mem_budget_bytes : ((size_t)4 << 30);
+  cudaDeviceGetAttribute(&c->sms, cudaDevAttrMultiProcessorCount, device);
+  if (cudaStreamCreateWithFlags(&c->stream, cudaStreamNonBlocking) != cudaSuccess ||
+      cudaEventCreateWithFlags(&c->last_done, cudaEventDisableTiming) != cudaSuccess ||
+      cudaEventCreate(&c->ev0) != cudaSuccess || cudaEventCreate(&c->ev1) != cudaSuccess) {
+    cudaGetLastError();
+    delete c;
+    return fail(RVH_ECUDA, "stream/event creation failed");
+  }
+  *out = c;
+  return RVH_OK;
+}
+
+void rvh_destroy(rvh_ctx* ctx) {
+  if (!ctx) return;
+  cudaSetDevice(ctx->device);
+  if (ctx->server) server_destroy(ctx->server);
+  cudaStreamSynchronize(ctx->stream);
+  if (ctx->scratch) ctx_free(ctx, ctx->scratch, ctx->scratch_bytes);
+  cudaEventDestroy(ctx->last_done);
+  cudaEventDestroy(ctx->ev0);
+  cudaEventDestroy(ctx->ev1);
+  cudaStreamDestroy(ctx->stream);
+  delete ctx;
+}
+
+const char* rvh_last_error(rvh_ctx*) { return g_err.c_str(); }
+
+int rvh_set_schedule(rvh_ctx* ctx, int32_t pw, int32_t hpl) {
+  if (!ctx) return fail(RVH_EINVAL, "ctx is NULL");
+  if (pw != 0 && pw != 1 && pw != 8 && pw != 32) return fail(RVH_EINVAL, "points_per_warp must be 0, 1, 8 or 32");
+  if (hpl != 0 && hpl != 4 && hpl != 8) return fail(RVH_EINVAL, "hyps_per_lane must be 0, 4 or 8");
+  ctx->pw_fixed = pw;
+  ctx->hpl_fixed = hpl;
+  return RVH_OK;
+}
+
+int rvh_get_stats(rvh_ctx* ctx, rvh_stats* out) {
+  if (!ctx || !out) return fail(RVH_EINVAL, "NULL argument");
+  std::lock_guard<std::mutex> lk(ctx->mu);
+  RVH_CUDA(cudaSetDevice(ctx->device));
+  if (ctx->have_launch) {
+    RVH_CUDA(cudaEventSynchronize(ctx->last_done));
+    unsigned long long h[4] = {0, 0, 0, 0};
+    RVH_CUDA(cudaMemcpy(h, ctx->stats_d, sizeof(h), cudaMemcpyDeviceToHost));
+    ctx->last.candidates = (int64_t)h[0];
+    ctx->last.band_points = (int64_t)h[1];
+    ctx->last.fp64_hypotheses = (int64_t)h[2];
+    float ms = 0.f;
+    if (cudaEventElapsedTime(&ms, ctx->ev0, ctx->ev1) == cudaSuccess) ctx->last.kernel_ms = ms;
+    else cudaGetLastError();
+  }
+  *out = ctx->last;
+  return RVH_OK;
+}
+
+// Shared front half of rvh_estimate / rvh_estimate_baseline: validation, pointer
+// kinds, scratch layout, host->device staging.  fused = false selects the
+// baseline's scratch (FP64 rows).
+struct Staged {
+  const float *az, *el, *dop;
+  const int32_t* off;
+  rvh_result dev_out;       // device pointers the kernel writes
+  bool host_out[8];
+  char* base;
+  int2* worklist;
+  int* counter;
+  unsigned long long* stats;
+  void* rows;               // float4[n_points] (fused) or double[4 n_points] (baseline)
+};
+
+static int stage(rvh_ctx* ctx, const rvh_frame* f, const rvh_params* p, rvh_result* r, cudaStream_t s,
+                 bool fused, Staged& st) {
+  const int64_t np = f->n_points;
+  const int32_t nc = f->n_clusters;
+  const bool dim3 = p->model_dim == 3;
+  const bool d_az = is_device_ptr(f->azimuth), d_dop = is_device_ptr(f->doppler);
+  const bool d_el = !dim3 || is_device_ptr(f->elevation);
+  const bool d_off = is_device_ptr(f->cluster_offsets);
+  if (!d_off) {
+    int rc = check_host_offsets(f->cluster_offsets, nc, np);
+    if (rc) return rc;
+  }
+  void* outs[8] = {r->vx, r->vy, r->vz, r->heading, r->inlier_count, r->best_hypothesis, r->status, r->inlier_mask};
+  const size_t osz[8] = {8, 8, 8, 8, 4, 4, 4, 1};
+  for (int i = 0; i < 8; ++i) st.host_out[i] = outs[i] && !is_device_ptr(outs[i]);
+  // layout
+  size_t off = 0;
+  auto take = [&](size_t bytes) {
+    size_t o = off;
+    off += align_up(bytes);
+    return o;
+  };
+  const size_t o_work = take(sizeof(int2) * (size_t)std::max(nc, 1));
+  const size_t o_ctr = take(64);
+  const size_t o_stats = take(64);
+  const size_t o_rows = take((fused ? sizeof(float4) : 4 * sizeof(double)) * (size_t)std::max<int64_t>(np, 1));
+  const size_t o_az = d_az ? 0 : take(4 * (size_t)np);
+  const size_t o_el = d_el ? 0 : take(4 * (size_t)np);
+  const size_t o_dop = d_dop ? 0 : take(4 * (size_t)np);
+  const size_t o_off = d_off ? 0 : take(4 * (size_t)(nc + 1));
+  size_t o_out[8];
+  for (int i = 0; i < 8; ++i) {
+    const size_t n = (i == 7) ? (size_t)np : (size_t)nc;
+    o_out[i] = st.host_out[i] ? take(osz[i] * std::max<size_t>(n, 1)) : 0;
+  }
+  if (off > ctx->scratch_bytes) {
+    // wait for earlier work that may still use the old scratch
+    RVH_CUDA(cudaEventSynchronize(ctx->last_done));
+    if (ctx->scratch) ctx_free(ctx, ctx->scratch, ctx->scratch_bytes);
+    ctx->scratch = nullptr;
+    ctx->scratch_bytes = 0;
+    const size_t want = off + off / 4;
+    int rc = ctx_alloc(ctx, &ctx->scratch, want);
+    if (rc) return rc;
+    ctx->scratch_bytes = want;
+  }
+  char* b = (char*)ctx->scratch;
+  st.base = b;
+  st.worklist = (int2*)(b + o_work);
+  st.counter = (int*)(b + o_ctr);
+  st.stats = (unsigned long long*)(b + o_stats);
+  st.rows = b + o_rows;
+  st.az = d_az ? f->azimuth : (const float*)(b + o_az);
+  st.el = dim3 ? (d_el ? f->elevation : (const float*)(b + o_el)) : nullptr;
+  st.dop = d_dop ? f->doppler : (const float*)(b + o_dop);
+  st.off = d_off ? f->cluster_offsets : (const int32_t*)(b + o_off);
+  if (np > 0) {
+    if (!d_az) RVH_CUDA(cudaMemcpyAsync((void*)st.az, f->azimuth, 4 * np, cudaMemcpyHostToDevice, s));
+    if (dim3 && !d_el) RVH_CUDA(cudaMemcpyAsync((void*)st.el, f->elevation, 4 * np, cudaMemcpyHostToDevice, s));
+    if (!d_dop) RVH_CUDA(cudaMemcpyAsync((void*)st.dop, f->doppler, 4 * np, cudaMemcpyHostToDevice, s));
+  }
+  if (!d_off) RVH_CUDA(cudaMemcpyAsync((void*)st.off, f->cluster_offsets, 4 * (size_t)(nc + 1), cudaMemcpyHostToDevice, s));
+  void* dev[8];
+  for (int i = 0; i < 8; ++i) dev[i] = st.host_out[i] ? (void*)(b + o_out[i]) : outs[i];
+  st.dev_out.vx = (double*)dev[0];
+  st.dev_out.vy = (double*)dev[1];
+  st.dev_out.vz = (double*)dev[2];
+  st.dev_out.heading = (double*)dev[3];
+  st.dev_out.inlier_count = (int32_t*)dev[4];
+  st.dev_out.best_hypothesis = (int32_t*)dev[5];
+  st.dev_out.status = (int32_t*)dev[6];
+  st.dev_out.inlier_mask = (uint8_t*)dev[7];
+  return RVH_OK;
+}
+
+static int unstage(const rvh_frame* f, rvh_result* r, const Staged& st, cudaStream_t s) {
+  void* outs[8] = {r->vx, r->vy, r->vz, r->heading, r->inlier_count, r->best_hypothesis, r->status, r->inlier_mask};
+  void* dev[8] = {st.dev_out.vx, st.dev_out.vy, st.dev_out.vz, st.dev_out.heading, st.dev_out.inlier_count,
+                  st.dev_out.best_hypothesis, st.dev_out.status, st.dev_out.inlier_mask};
+  const size_t osz[8] = {8, 8, 8, 8, 4, 4, 4, 1};
+  bool any = false;
+  for (int i = 0; i < 8; ++i) {
+    if (!st.host_out[i]) continue;
+    const size_t n = (i == 7) ? (size_t)f->n_points : (size_t)f->n_clusters;
+    if (n) RVH_CUDA(cudaMemcpyAsync(outs[i], dev[i], osz[i] * n, cudaMemcpyDeviceToHost, s));
+    any = true;
+  }
+  if (any) RVH_CUDA(cudaStreamSynchronize(s));
+  return RVH_OK;
+}
+
+int rvh_estimate(rvh_ctx* ctx, const rvh_frame* frame, const rvh_params* params, rvh_result* result,
+                 void* stream) {
+  if (!ctx) return fail(RVH_EINVAL, "ctx is NULL");
+  int rc = check_args(frame, params, result);
+  if (rc) return rc;
+  if (frame->n_clusters == 0) return RVH_OK;
+  std::lock_guard<std::mutex> lk(ctx->mu);
+  RVH_CUDA(cudaSetDevice(ctx->device));
+  cudaStream_t s = stream ? (cudaStream_t)stream : ctx->stream;
+  RVH_CUDA(cudaStreamWaitEvent(s, ctx->last_done, 0));
+  Staged st{};
+  rc = stage(ctx, frame, params, result, s, true, st);
+  if (rc) return rc;
+  ctx->stats_d = st.stats;
+  RVH_CUDA(cudaMemsetAsync(st.stats, 0, 32, s));
+  FusedArgs a;
+  memset(&a, 0, sizeof(a));
+  fill_desc(a.f[0], *frame, *params, st.az, st.el, st.dop, st.off, (float4*)st.rows, st.dev_out);
+  a.n_frames = 1;
+  a.n_items = frame->n_clusters;
+  a.worklist = st.worklist;
+  a.work_counter = st.counter;
+  a.stats = st.stats;
+  choose_schedule(ctx, params->num_hypotheses, &a.pw, &a.hpl);
+  rc = launch_batch(ctx, a, params->model_dim, s, ctx->ev0, ctx->ev1);
+  if (rc) return rc;
+  ctx->last.hypotheses = (int64_t)frame->n_clusters * params->num_hypotheses;
+  ctx->last.pair_evals = frame->n_points * (int64_t)params->num_hypotheses;
+  ctx->last.points_per_warp = a.pw;
+  ctx->last.hyps_per_lane = a.hpl;
+  ctx->have_launch = true;
+  rc = unstage(frame, result, st, s);
+  RVH_CUDA(cudaEventRecord(ctx->last_done, s));
+  return rc;
+}
+
+int rvh_estimate_baseline(rvh_ctx* ctx, const rvh_frame* frame, const rvh_params* params, rvh_result* result,
+                          void* stream) {
+  if (!ctx) return fail(RVH_EINVAL, "ctx is NULL");
+  int rc = check_args(frame, params, result);
+  if (rc) return rc;
+  if (frame->n_clusters == 0) return RVH_OK;
+  std::lock_guard<std::mutex> lk(ctx->mu);
+  RVH_CUDA(cudaSetDevice(ctx->device));
+  cudaStream_t s = stream ? (cudaStream_t)stream : ctx->stream;
+  RVH_CUDA(cudaStreamWaitEvent(s, ctx->last_done, 0));
+  Staged st{};
+  rc = stage(ctx, frame, params, result, s, false, st);
+  if (rc) return rc;
+  const int dim = params->model_dim;
+  const int nmax = 2048;
+  const size_t smem = baseline_smem_bytes(nmax);
+  RVH_CUDA(baseline_configure(dim, smem));
+  BaselineArgs b;
+  memset(&b, 0, sizeof(b));
+  FrameDesc d;
+  fill_desc(d, *frame, *params, st.az, st.el, st.dop, st.off, nullptr, st.dev_out);
+  b.az = d.az;
+  b.el = d.el;
+  b.dop = d.dop;
+  b.offsets = st.off;
+  b.n_points = frame->n_points;
+  b.rows64_g = (double*)st.rows;
+  b.H = d.H;
+  b.tau = d.tau;
+  b.eps = d.eps;
+  b.key = d.key;
+  b.vx = d.vx;
+  b.vy = d.vy;
+  b.vz = d.vz;
+  b.heading = d.heading;
+  b.inlier_count = d.inlier_count;
+  b.best = d.best;
+  b.status = d.status;
+  b.mask = d.mask;
+  b.nmax_smem = nmax;
+  RVH_CUDA(cudaEventRecord(ctx->ev0, s));
+  for (int i = 0; i < frame->n_clusters; ++i) RVH_CUDA(launch_baseline_cluster(dim, b, i, smem, s));
+  RVH_CUDA(cudaEventRecord(ctx->ev1, s));
+  ctx->have_launch = false;
+  rc = unstage(frame, result, st, s);
+  RVH_CUDA(cudaEventRecord(ctx->last_done, s));
+  return rc;
+}
+
+int rvh_submit(rvh_ctx* ctx, const rvh_frame* frame, const rvh_params* params, rvh_result* result,
+               uint64_t* ticket) {
+  if (!ctx || !ticket) return fail(RVH_EINVAL, "NULL argument");
+  int rc = check_args(frame, params, result);
+  if (rc) return rc;
+  {
+    std::lock_guard<std::mutex> lk(ctx->mu);
+    if (!ctx->server) {
+      rc = server_create(ctx, &ctx->server);
+      if (rc) return rc;
+    }
+  }
+  return server_submit(ctx->server, frame, params, result, ticket);
+}
+
+int rvh_poll(rvh_ctx* ctx, uint64_t ticket) {
+  if (!ctx || !ctx->server) return fail(RVH_EINVAL, "unknown ticket");
+  return server_poll(ctx->server, ticket);
+}
+
+int rvh_wait(rvh_ctx* ctx, uint64_t ticket, int64_t timeout_us) {
+  if (!ctx || !ctx->server) return fail(RVH_EINVAL, "unknown ticket");
+  return server_wait(ctx->server, ticket, timeout_us);
+}
+
+}  // extern "C"
+
+namespace rvh {
+int set_error(int code, const std::string& msg) { return fail(code, msg); }
+bool device_ptr(const void* p) { return is_device_ptr(p); }
+int validate_host_offsets(const int32_t* off, int32_t n, int64_t np) { return check_host_offsets(off, n, np); }
+}  // namespace rvh

@@ -1,0 +1,301 @@
+// Device building blocks shared by the rvh kernels: the counter-based draw of
+// minimal sets, FP32 point rows, the FP32 minimal-set solve with its rigorous
+// error bound, and the FP64 solve whose rounding sequence defines the exact
+// inlier decisions.
+//
+// The whole library is compiled with -fmad=false: every fused multiply-add is
+// an explicit fmaf()/fma() call, so the FP32 error bounds below describe the
+// operations that actually run.
+#pragma once
+
+#include <cstdint>
+#include <cuda_runtime.h>
+
+#include "rvh.h"
+#include "rvh_kernels.h"
+
+namespace rvh {
+
+// ---- counter-based random minimal sets (stand-in for Alg. 1's host-side index arrays) --
+
+// Philox4x32 with 10 rounds (Salmon, Moraes, Dror, Shaw, SC'11).
+__device__ __forceinline__ uint4 philox4x32_10(uint4 x, uint2 key) {
+#pragma unroll
+  for (int round = 0; round < 10; ++round) {
+    if (round) {
+      key.x += 0x9E3779B9u;
+      key.y += 0xBB67AE85u;
+    }
+    const uint32_t hi0 = __umulhi(0xD2511F53u, x.x), lo0 = 0xD2511F53u * x.x;
+    const uint32_t hi1 = __umulhi(0xCD9E8D57u, x.z), lo1 = 0xCD9E8D57u * x.z;
+    x = make_uint4(hi1 ^ x.y ^ key.x, lo1, hi0 ^ x.w ^ key.y, lo0);
+  }
+  return x;
+}
+
+// Minimal set of hypothesis h of cluster `cluster` (frame-local index) with n >= k points.
+template <int DIM>
+__device__ __forceinline__ void draw_minimal_set(uint2 key, int cluster, int h, int n, int q[3]) {
+  const uint4 w = philox4x32_10(make_uint4((uint32_t)h, (uint32_t)cluster, 0u, 0u), key);
+  uint32_t q0 = __umulhi(w.x, (uint32_t)n);
+  uint32_t q1 = __umulhi(w.y, (uint32_t)(n - 1));
+  q1 += (q1 >= q0);
+  q[0] = (int)q0;
+  q[1] = (int)q1;
+  if (DIM == 3) {
+    const uint32_t lo = min(q0, q1), hi = max(q0, q1);
+    uint32_t q2 = __umulhi(w.z, (uint32_t)(n - 2));
+    q2 += (q2 >= lo);
+    q2 += (q2 >= hi);
+    q[2] = (int)q2;
+  } else {
+    q[2] = 0;
+  }
+}
+
+// ---- FP64 arithmetic that fixes every decision --------------------------------------
+// Each formula is evaluated in this exact order: x*w - y*z as fma(x, w, -(y*z)),
+// the 3x3 determinant by cofactors along row 0, Cramer's rule for the solve.
+
+__device__ __forceinline__ double det2_f64(double x, double y, double z, double w) {
+  return fma(x, w, -(y * z));
+}
+
+__device__ __forceinline__ double det3_f64(const double* m0, const double* m1, const double* m2) {
+  const double k0 = det2_f64(m1[1], m1[2], m2[1], m2[2]);
+  const double k1 = det2_f64(m1[0], m1[2], m2[0], m2[2]);
+  const double k2 = det2_f64(m1[0], m1[1], m2[0], m2[1]);
+  return fma(m0[2], k2, fma(-m0[1], k1, m0[0] * k0));
+}
+
+// Rows of A_i (Eq. eq:LSQPerCluster) in FP64: (cos t, sin t) or
+// (cos t cos e, sin t cos e, sin e).
+template <int DIM>
+__device__ __forceinline__ void row_f64(float az, float el, double a[3]) {
+  double s, c;
+  sincos((double)az, &s, &c);
+  if (DIM == 2) {
+    a[0] = c;
+    a[1] = s;
+    a[2] = 0.0;
+  } else {
+    double se, ce;
+    sincos((double)el, &se, &ce);
+    a[0] = c * ce;
+    a[1] = s * ce;
+    a[2] = se;
+  }
+}
+
+// Solves the k x k system (rows a0, a1[, a2], right side w) by Cramer's rule.
+// Returns false (and leaves v) when !(|det| >= eps).
+template <int DIM>
+__device__ __forceinline__ bool solve_f64(const double* a0, const double* a1, const double* a2,
+                                          const double* w, double eps, double v[3], double* det_out) {
+  if (DIM == 2) {
+    const double det = det2_f64(a0[0], a0[1], a1[0], a1[1]);
+    if (det_out) *det_out = det;
+    if (!(fabs(det) >= eps)) return false;
+    v[0] = det2_f64(w[0], a0[1], w[1], a1[1]) / det;
+    v[1] = det2_f64(a0[0], w[0], a1[0], w[1]) / det;
+    v[2] = 0.0;
+    return true;
+  } else {
+    const double det = det3_f64(a0, a1, a2);
+    if (det_out) *det_out = det;
+    if (!(fabs(det) >= eps)) return false;
+#pragma unroll
+    for (int col = 0; col < 3; ++col) {
+      double r0[3] = {a0[0], a0[1], a0[2]};
+      double r1[3] = {a1[0], a1[1], a1[2]};
+      double r2[3] = {a2[0], a2[1], a2[2]};
+      r0[col] = w[0];
+      r1[col] = w[1];
+      r2[col] = w[2];
+      v[col] = det3_f64(r0, r1, r2) / det;
+    }
+    return true;
+  }
+}
+
+// Doppler residual r = w - a.v of Eq. LSQ_eq in FP64.
+template <int DIM>
+__device__ __forceinline__ double residual_f64(const double* a, double w, const double* v) {
+  if (DIM == 2) return w - fma(v[0], a[0], v[1] * a[1]);
+  return w - fma(v[0], a[0], fma(v[1], a[1], v[2] * a[2]));
+}
+
+// ---- FP32 rows and FP32 hypotheses with rigorous error bounds ------------------------
+
+// Relative accuracy assumed for sincosf on |t| <= pi (tests verify twice this
+// margin exhaustively over every float in the range); outside it the row is
+// the FP64 one rounded to nearest.
+constexpr float kRowRel = 0x1p-21f;          // rho: |c32 - c64| <= rho |c64|
+constexpr float kU = 0x1p-24f;               // FP32 unit roundoff
+constexpr float kRowRel3 = 2.0f * 0x1p-21f + 2.0f * 0x1p-24f;  // products cos*cos
+constexpr float kSafety = 1.0f + 0x1p-14f;   // covers second-order terms and bound roundings
+constexpr float kTiny = 0x1p-120f;           // absolute slack for underflow
+constexpr float kBandFloor = 1e-5f;          // minimum half-width of the FP64 band (m/s)
+// |det32 - det64| over unit rows: (2 rho + 2u)(1 + 1e-4) for 2D,
+// sqrt(3)(3 rho3 + 5u) for 3D, rounded up, plus the FP64 rounding of det64.
+constexpr float kDetErr2 = 1.081e-6f;
+constexpr float kDetErr3 = 6.20e-6f;
+
+// FP32 row of a point plus its Doppler: (c, s, w, 0) or (a0, a1, a2, w).
+template <int DIM>
+__device__ __forceinline__ float4 row_f32(float az, float el, float w) {
+  float s, c;
+  if (fabsf(az) <= 3.1415925f) {
+    sincosf(az, &s, &c);
+  } else {
+    double sd, cd;
+    sincos((double)az, &sd, &cd);
+    s = __double2float_rn(sd);
+    c = __double2float_rn(cd);
+  }
+  if (DIM == 2) return make_float4(c, s, w, 0.0f);
+  float se, ce;
+  if (fabsf(el) <= 3.1415925f) {
+    sincosf(el, &se, &ce);
+  } else {
+    double sd, cd;
+    sincos((double)el, &sd, &cd);
+    se = __double2float_rn(sd);
+    ce = __double2float_rn(cd);
+  }
+  return make_float4(c * ce, s * ce, se, w);
+}
+
+// Hypothesis record used by the scoring loops: negated velocity (so the
+// residual is fmaf(nx, c, fmaf(ny, s, w))), thresholds and a kind.
+enum HypKind : int { kHypNormal = 0, kHypRejected = 1, kHypExactOnly = 2, kHypUndecided = 3 };
+
+struct Hyp32 {
+  float nx, ny, nz;   // -X, -Y, -Z
+  float thi;          // |r32| >  thi  => certainly an outlier
+  float tlo;          // |r32| <= tlo  => certainly an inlier
+  int kind;
+};
+
+// FP32 minimal-set solve of the rows p, q[, r] (FP32 rows with Doppler in the
+// last used lane) and the half-width b of the band outside of which the FP32
+// residual decides exactly like the FP64 one.  wmax = max |w| over the cluster.
+// Conditioning: |det32| >= acc => FP64 accepts; |det32| < rej => FP64 rejects;
+// otherwise the kind is kHypUndecided and the caller decides in FP64.
+template <int DIM>
+__device__ __forceinline__ Hyp32 hyp_f32(float4 p, float4 q, float4 r, float wmax, float acc,
+                                         float rej, TauPair tau) {
+  Hyp32 h;
+  h.nx = h.ny = h.nz = 0.0f;
+  h.thi = __int_as_float(0x7fc00000);  // NaN: never counted
+  h.tlo = -1.0f;
+  if (DIM == 2) {
+    const float d = fmaf(p.x, q.y, -(p.y * q.x));
+    const float ad = fabsf(d);
+    if (!(ad >= acc)) {
+      h.kind = (ad < rej) ? kHypRejected : kHypUndecided;
+      return h;
+    }
+    const float w0 = p.z, w1 = q.z;
+    const float nxn = fmaf(w0, q.y, -(w1 * p.y));
+    const float nyn = fmaf(p.x, w1, -(w0 * q.x));
+    const float X = nxn / d, Y = nyn / d;
+    const float A = fabsf(w0) + fabsf(w1);
+    const float eD = kDetErr2;
+    const float inv = 1.0f / ad;
+    const float slack = 1.0f / (ad - eD);
+    const float eNX = (kRowRel + kU) * 1.0001f * A + kU * fabsf(nxn);
+    const float eNY = (kRowRel + kU) * 1.0001f * A + kU * fabsf(nyn);
+    const float eX = eNX * inv + (fabsf(nxn) + eNX) * slack * eD * inv + kU * fabsf(X);
+    const float eY = eNY * inv + (fabsf(nyn) + eNY) * slack * eD * inv + kU * fabsf(Y);
+    const float e64 = 0x1p-50f * (2.0f * A + fabsf(nxn) + fabsf(nyn) + 2.0f * (fabsf(X) + fabsf(Y))) * inv;
+    float b = (2.0f * kU + 0x1p-52f) * wmax + (kU + kRowRel + 0x1p-52f) * fabsf(X) +
+              (2.0f * kU + kRowRel + 0x1p-52f) * fabsf(Y) + eX + eY + e64;
+    b = b * kSafety + kTiny;
+    h.nx = -X;
+    h.ny = -Y;
+    if (!(b < 1e30f) || !(fabsf(X) < 1e30f) || !(fabsf(Y) < 1e30f) || !(ad > 2.0f * eD)) {
+      h.kind = kHypExactOnly;
+      h.thi = __int_as_float(0x7f800000);  // +inf: nothing certainly out
+      h.tlo = -1.0f;                        // nothing certainly in
+      return h;
+    }
+    b = fmaxf(b, kBandFloor);
+    h.thi = __fadd_ru(tau.hi, b);
+    h.tlo = __fsub_rd(tau.lo, b);
+    h.kind = kHypNormal;
+    return h;
+  } else {
+    // rows p, q, r = (a0, a1, a2, w)
+    const float k0 = fmaf(q.y, r.z, -(q.z * r.y));
+    const float k1 = fmaf(q.x, r.z, -(q.z * r.x));
+    const float k2 = fmaf(q.x, r.y, -(q.y * r.x));
+    const float d = fmaf(p.z, k2, fmaf(-p.y, k1, p.x * k0));
+    const float ad = fabsf(d);
+    if (!(ad >= acc)) {
+      h.kind = (ad < rej) ? kHypRejected : kHypUndecided;
+      return h;
+    }
+    const float wp = p.w, wq = q.w, wr = r.w;
+    // column 0 replaced by w
+    float n0, n1, n2;
+    {
+      const float c0 = fmaf(q.y, r.z, -(q.z * r.y));
+      const float c1 = fmaf(wq, r.z, -(q.z * wr));
+      const float c2 = fmaf(wq, r.y, -(q.y * wr));
+      n0 = fmaf(p.z, c2, fmaf(-p.y, c1, wp * c0));
+    }
+    {  // column 1 replaced by w
+      const float c0 = fmaf(wq, r.z, -(q.z * wr));
+      const float c1 = fmaf(q.x, r.z, -(q.z * r.x));
+      const float c2 = fmaf(q.x, wr, -(wq * r.x));
+      n1 = fmaf(p.z, c2, fmaf(-wp, c1, p.x * c0));
+    }
+    {  // column 2 replaced by w
+      const float c0 = fmaf(q.y, wr, -(wq * r.y));
+      const float c1 = fmaf(q.x, wr, -(wq * r.x));
+      const float c2 = fmaf(q.x, r.y, -(q.y * r.x));
+      n2 = fmaf(wp, c2, fmaf(-p.y, c1, p.x * c0));
+    }
+    const float X = n0 / d, Y = n1 / d, Z = n2 / d;
+    const float A = fabsf(wp) + fabsf(wq) + fabsf(wr);
+    const float eD = kDetErr3;
+    const float inv = 1.0f / ad;
+    const float slack = 1.0f / (ad - eD);
+    const float eNb = (4.0f * kRowRel3 + 8.0f * kU) * 1.0001f * A;
+    const float eN0 = eNb + kU * fabsf(n0), eN1 = eNb + kU * fabsf(n1), eN2 = eNb + kU * fabsf(n2);
+    const float eX = eN0 * inv + (fabsf(n0) + eN0) * slack * eD * inv + kU * fabsf(X);
+    const float eY = eN1 * inv + (fabsf(n1) + eN1) * slack * eD * inv + kU * fabsf(Y);
+    const float eZ = eN2 * inv + (fabsf(n2) + eN2) * slack * eD * inv + kU * fabsf(Z);
+    const float e64 = 0x1p-48f *
+                      (3.0f * A + fabsf(n0) + fabsf(n1) + fabsf(n2) + 3.0f * (fabsf(X) + fabsf(Y) + fabsf(Z))) * inv;
+    float b = (3.0f * kU + 0x1p-52f) * wmax + (kU + kRowRel3 + 0x1p-52f) * fabsf(X) +
+              (2.0f * kU + kRowRel3 + 0x1p-52f) * fabsf(Y) + (3.0f * kU + kRowRel + 0x1p-52f) * fabsf(Z) +
+              eX + eY + eZ + e64;
+    b = b * kSafety + kTiny;
+    h.nx = -X;
+    h.ny = -Y;
+    h.nz = -Z;
+    if (!(b < 1e30f) || !(fabsf(X) < 1e30f) || !(fabsf(Y) < 1e30f) || !(fabsf(Z) < 1e30f) ||
+        !(ad > 2.0f * eD)) {
+      h.kind = kHypExactOnly;
+      h.thi = __int_as_float(0x7f800000);
+      h.tlo = -1.0f;
+      return h;
+    }
+    b = fmaxf(b, kBandFloor);
+    h.thi = __fadd_ru(tau.hi, b);
+    h.tlo = __fsub_rd(tau.lo, b);
+    h.kind = kHypNormal;
+    return h;
+  }
+}
+
+// FP32 residual of a row under a hypothesis (negated velocity).
+template <int DIM>
+__device__ __forceinline__ float resid_f32(float4 row, float nx, float ny, float nz) {
+  if (DIM == 2) return fmaf(nx, row.x, fmaf(ny, row.y, row.z));
+  return fmaf(nx, row.x, fmaf(ny, row.y, fmaf(nz, row.z, row.w)));
+}
+
+}  // namespace rvh

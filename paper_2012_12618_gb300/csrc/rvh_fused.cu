@@ -1,0 +1,542 @@
+// Fused persistent kernel: per cluster, FP32 rows -> counter-RNG minimal sets
+// -> FP32 solve with error bound -> FP32 scoring pass (upper-bound counts) ->
+// exact re-scoring of the trials that can still win (FP64 only inside the
+// error band) -> lowest-index argmax -> FP64 inlier mask and normal-equation
+// refine -> heading.  Sec. III-A (Alg. 1, Eq. 4) and Sec. III-B (Eq. LSQ_eq,
+// Eq. eq:LSQPerCluster, Alg. 2) of arXiv 2012.12618.
+//
+// Parallel mapping (GB300-first, not the paper's thread-per-trial): clusters
+// are work items taken by persistent CTAs from an LPT-ordered list; inside a
+// cluster, trials map to warps/lanes and points to lanes, with the cluster's
+// FP32 rows staged in shared memory.
+#include <cstdint>
+#include <cuda_runtime.h>
+
+#include "rvh_device.cuh"
+#include "rvh_kernels.h"
+
+namespace rvh {
+
+constexpr int kThreads = 256;
+constexpr int kWarps = kThreads / 32;
+
+struct Smem {
+  float4* rows;       // [nmax_smem]
+  float4* hyp;        // [hchunk] (-X, -Y, -Z, thi)
+  float* tlo;         // [hchunk]
+  int* U;             // [hchunk] upper bounds of the exact counts (-1 = rejected)
+  int* cand;          // [hchunk] candidate list
+  int8_t* kind;       // [hchunk]
+};
+
+__device__ __forceinline__ unsigned long long best_key(int count, int h) {
+  return ((unsigned long long)(uint32_t)(count + 1) << 32) | (unsigned long long)(0xFFFFFFFFu - (uint32_t)h);
+}
+
+template <typename T>
+__device__ __forceinline__ T warp_sum(T v) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+  return v;
+}
+
+__device__ __forceinline__ int block_max_int(int v, int* red) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) v = max(v, __shfl_xor_sync(0xffffffffu, v, o));
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  __syncthreads();
+  if (lane == 0) red[warp] = v;
+  __syncthreads();
+  int r = red[0];
+#pragma unroll
+  for (int w = 1; w < kWarps; ++w) r = max(r, red[w]);
+  return r;
+}
+
+__device__ __forceinline__ float block_max_float(float v, float* red) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) v = fmaxf(v, __shfl_xor_sync(0xffffffffu, v, o));
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  __syncthreads();
+  if (lane == 0) red[warp] = v;
+  __syncthreads();
+  float r = red[0];
+#pragma unroll
+  for (int w = 1; w < kWarps; ++w) r = fmaxf(r, red[w]);
+  return r;
+}
+
+// ---- phase A: upper-bound counts U_h = #{|r32| <= thi_h} ---------------------------
+// Lane l handles trial sub-group l / PW and points l % PW, l % PW + PW, ...;
+// each lane keeps HPL trials in registers.  PW = 32 is warp-per-trial-group
+// with lanes over points; PW = 1 is lanes over trials with broadcast rows.
+template <int DIM, int PW, int HPL>
+__device__ __forceinline__ void phase_a(const float4* __restrict__ rows, int N, const Smem& S, int nh) {
+  constexpr int NHL = 32 / PW;
+  constexpr int G = NHL * HPL;
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int hl = lane / PW, pl = lane % PW;
+  const int ngroups = (nh + G - 1) / G;
+  for (int g = warp; g < ngroups; g += kWarps) {
+    const int base = g * G + hl * HPL;
+    float nx[HPL], ny[HPL], nz[HPL], th[HPL], cnt[HPL];
+#pragma unroll
+    for (int m = 0; m < HPL; ++m) {
+      const int h = base + m;
+      float4 v = (h < nh) ? S.hyp[h] : make_float4(0.f, 0.f, 0.f, __int_as_float(0x7fc00000));
+      nx[m] = v.x;
+      ny[m] = v.y;
+      nz[m] = v.z;
+      th[m] = v.w;
+      cnt[m] = 0.0f;
+    }
+    for (int j = pl; j < N; j += PW) {
+      const float4 p = rows[j];
+#pragma unroll
+      for (int m = 0; m < HPL; ++m) {
+        const float r = resid_f32<DIM>(p, nx[m], ny[m], nz[m]);
+        cnt[m] += (fabsf(r) <= th[m]) ? 1.0f : 0.0f;
+      }
+    }
+#pragma unroll
+    for (int m = 0; m < HPL; ++m) {
+#pragma unroll
+      for (int o = PW / 2; o > 0; o >>= 1) cnt[m] += __shfl_xor_sync(0xffffffffu, cnt[m], o);
+    }
+    if (pl == 0) {
+#pragma unroll
+      for (int m = 0; m < HPL; ++m) {
+        const int h = base + m;
+        if (h < nh && S.kind[h] == kHypNormal) S.U[h] = (int)cnt[m];
+      }
+    }
+  }
+}
+
+template <int DIM>
+__device__ void phase_a_dispatch(int pw, int hpl, const float4* rows, int N, const Smem& S, int nh) {
+  if (pw == 1) {
+    if (hpl == 8) phase_a<DIM, 1, 8>(rows, N, S, nh); else phase_a<DIM, 1, 4>(rows, N, S, nh);
+  } else if (pw == 8) {
+    if (hpl == 8) phase_a<DIM, 8, 8>(rows, N, S, nh); else phase_a<DIM, 8, 4>(rows, N, S, nh);
+  } else {
+    if (hpl == 8) phase_a<DIM, 32, 8>(rows, N, S, nh); else phase_a<DIM, 32, 4>(rows, N, S, nh);
+  }
+}
+
+// FP64 velocity of trial h (the oracle's exact rounding sequence).  Returns false if rejected.
+template <int DIM>
+__device__ bool hyp_f64(const FrameDesc& a, int64_t o, int ci, int h, int N, double v[3]) {
+  int q[3];
+  draw_minimal_set<DIM>(a.key, ci, h, N, q);
+  double r0[3], r1[3], r2[3] = {0.0, 0.0, 0.0};
+  row_f64<DIM>(a.az[o + q[0]], DIM == 3 ? a.el[o + q[0]] : 0.0f, r0);
+  row_f64<DIM>(a.az[o + q[1]], DIM == 3 ? a.el[o + q[1]] : 0.0f, r1);
+  if (DIM == 3) row_f64<DIM>(a.az[o + q[2]], a.el[o + q[2]], r2);
+  double w[3] = {(double)a.dop[o + q[0]], (double)a.dop[o + q[1]], DIM == 3 ? (double)a.dop[o + q[2]] : 0.0};
+  return solve_f64<DIM>(r0, r1, r2, w, a.eps, v, nullptr);
+}
+
+// Exact count of trial (record hy, thresholds) by one warp: FP32 certainties plus
+// FP64 re-decision of the band points.
+template <int DIM>
+__device__ int exact_count_warp(const FrameDesc& a, const float4* __restrict__ rows, int64_t o, int ci,
+                                int h, int N, float4 hy, float tlo, unsigned long long* band_ctr) {
+  const int lane = threadIdx.x & 31;
+  int L = 0, B = 0;
+  for (int j = lane; j < N; j += 32) {
+    const float r = fabsf(resid_f32<DIM>(rows[j], hy.x, hy.y, hy.z));
+    if (r <= tlo) ++L;
+    else if (!(r > hy.w)) ++B;
+  }
+  L = warp_sum(L);
+  B = warp_sum(B);
+  if (B == 0) return L;
+  double v[3] = {0.0, 0.0, 0.0};
+  if (lane == 0) hyp_f64<DIM>(a, o, ci, h, N, v);
+#pragma unroll
+  for (int i = 0; i < 3; ++i) v[i] = __shfl_sync(0xffffffffu, v[i], 0);
+  int Lb = 0;
+  for (int j = lane; j < N; j += 32) {
+    const float4 p = rows[j];
+    const float r = fabsf(resid_f32<DIM>(p, hy.x, hy.y, hy.z));
+    if (!(r <= tlo) && !(r > hy.w)) {
+      double a64[3];
+      row_f64<DIM>(a.az[o + j], DIM == 3 ? a.el[o + j] : 0.0f, a64);
+      const double w = (double)(DIM == 2 ? p.z : p.w);
+      if (fabs(residual_f64<DIM>(a64, w, v)) <= a.tau) ++Lb;
+    }
+  }
+  Lb = warp_sum(Lb);
+  if (lane == 0) atomicAdd(band_ctr, (unsigned long long)B);
+  return L + Lb;
+}
+
+struct ClusterShared {
+  unsigned long long best;
+  int ncand;
+  int nin;
+  float wmax;
+  float4 win;      // winner's FP32 record
+  float win_tlo;
+  double v64[3];
+  int win_ok;
+  int red_i[kWarps];
+  float red_f[kWarps];
+  double red_d[kWarps][10];
+  unsigned long long ctr[4];  // candidates, band points, fp64 hyps, pair evals
+};
+
+template <int DIM>
+__device__ void write_invalid(const FrameDesc& a, int ci, int st) {
+  a.vx[ci] = __longlong_as_double(0x7ff8000000000000LL);
+  a.vy[ci] = __longlong_as_double(0x7ff8000000000000LL);
+  if (a.vz) a.vz[ci] = __longlong_as_double(0x7ff8000000000000LL);
+  a.heading[ci] = __longlong_as_double(0x7ff8000000000000LL);
+  a.inlier_count[ci] = 0;
+  a.best[ci] = -1;
+  a.status[ci] = st;
+}
+
+template <int DIM, bool SMEM_ROWS>
+__device__ void process_cluster(const FrameDesc& a, const Smem& S, ClusterShared& cs, int ci, int hchunk,
+                                int pw, int hpl) {
+  const int tid = threadIdx.x;
+  const int64_t o = a.offsets[ci];
+  const int64_t e = a.offsets[ci + 1];
+  if (o < 0 || e < o || e > a.n_points || (e - o) > 0x7fffffff) {
+    if (tid == 0) write_invalid<DIM>(a, ci, RVH_STATUS_BAD_OFFSETS);
+    return;
+  }
+  const int N = (int)(e - o);
+  if (N < DIM) {
+    for (int j = tid; j < N; j += kThreads) a.mask[o + j] = 0;
+    if (tid == 0) write_invalid<DIM>(a, ci, RVH_STATUS_TOO_FEW_POINTS);
+    return;
+  }
+  float4* rows = SMEM_ROWS ? S.rows : (a.rows_g + o);
+
+  // a1: FP32 rows of the cluster (sincosf; FP64 fallback outside |t| <= pi)
+  float wm = 0.0f;
+  for (int j = tid; j < N; j += kThreads) {
+    const float w = a.dop[o + j];
+    rows[j] = row_f32<DIM>(a.az[o + j], DIM == 3 ? a.el[o + j] : 0.0f, w);
+    wm = fmaxf(wm, fabsf(w));
+  }
+  wm = block_max_float(wm, cs.red_f);  // includes a __syncthreads after the row writes
+  if (tid == 0) {
+    cs.best = 0ull;
+    cs.wmax = wm;
+  }
+  __syncthreads();
+  const float wmax = cs.wmax;
+  unsigned long long n_fp64 = 0, n_cand = 0;
+
+  for (int hc0 = 0; hc0 < a.H; hc0 += hchunk) {
+    const int nh = min(hchunk, a.H - hc0);
+    // a2 + a3: draw, FP32 solve, bound
+    for (int hl = tid; hl < nh; hl += kThreads) {
+      int q[3];
+      draw_minimal_set<DIM>(a.key, ci, hc0 + hl, N, q);
+      const float4 p0 = rows[q[0]], p1 = rows[q[1]];
+      const float4 p2 = DIM == 3 ? rows[q[2]] : p0;
+      Hyp32 hy = hyp_f32<DIM>(p0, p1, p2, wmax, a.acc, a.rej, a.tau32);
+      if (hy.kind == kHypUndecided) {
+        ++n_fp64;
+        double v[3];
+        if (hyp_f64<DIM>(a, o, ci, hc0 + hl, N, v)) {
+          hy = hyp_f32<DIM>(p0, p1, p2, wmax, 0.0f, 0.0f, a.tau32);
+          if (hy.kind != kHypNormal) hy.kind = kHypExactOnly;
+          if (hy.kind == kHypExactOnly) {
+            hy.thi = __int_as_float(0x7f800000);
+            hy.tlo = -1.0f;
+          }
+        } else {
+          hy.kind = kHypRejected;
+        }
+      }
+      if (hy.kind == kHypExactOnly) ++n_fp64;
+      S.hyp[hl] = make_float4(hy.nx, hy.ny, hy.nz, hy.kind == kHypRejected ? __int_as_float(0x7fc00000) : hy.thi);
+      S.tlo[hl] = hy.tlo;
+      S.kind[hl] = (int8_t)hy.kind;
+      S.U[hl] = hy.kind == kHypRejected ? -1 : (hy.kind == kHypExactOnly ? N : 0);
+    }
+    __syncthreads();
+
+    // a4: scoring pass (the hot loop)
+    phase_a_dispatch<DIM>(pw, hpl, rows, N, S, nh);
+    __syncthreads();
+
+    // a5 + a6: exact counts of the trials whose upper bound reaches the lead
+    int um = -1;
+    for (int hl = tid; hl < nh; hl += kThreads) um = max(um, S.U[hl]);
+    const int Umax = block_max_int(um, cs.red_i);  // syncs after phase A's writes
+    const int lead = (int)(cs.best >> 32) - 1;     // best exact count so far (-1 none)
+    // trials of earlier chunks have lower indices, so a later trial must beat
+    // the lead strictly
+    if (Umax >= 0 && Umax > lead) {
+      for (int round = 0; round < 2; ++round) {
+        if (tid == 0) cs.ncand = 0;
+        __syncthreads();
+        const int cur = (int)(cs.best >> 32) - 1;
+        for (int hl = tid; hl < nh; hl += kThreads) {
+          const int u = S.U[hl];
+          const bool pick = round == 0 ? (u == Umax) : (u >= cur && u >= 0 && u < Umax);
+          if (pick) S.cand[atomicAdd(&cs.ncand, 1)] = hl;
+        }
+        __syncthreads();
+        const int nc = cs.ncand;
+        n_cand += (tid == 0) ? (unsigned long long)nc : 0ull;
+        for (int c = tid >> 5; c < nc; c += kWarps) {
+          const int hl = S.cand[c];
+          const int C = exact_count_warp<DIM>(a, rows, o, ci, hc0 + hl, N, S.hyp[hl], S.tlo[hl], &cs.ctr[1]);
+          if ((tid & 31) == 0) atomicMax(&cs.best, best_key(C, hc0 + hl));
+        }
+        __syncthreads();
+      }
+    }
+    __syncthreads();
+  }
+
+  if (tid == 0) {
+    atomicAdd(&cs.ctr[0], n_cand);
+  }
+  if (n_fp64) atomicAdd(&cs.ctr[2], n_fp64);
+
+  const unsigned long long key = cs.best;
+  if (key == 0ull) {
+    for (int j = tid; j < N; j += kThreads) a.mask[o + j] = 0;
+    if (tid == 0) write_invalid<DIM>(a, ci, RVH_STATUS_ALL_DEGENERATE);
+    __syncthreads();
+    return;
+  }
+  const int hstar = (int)(0xFFFFFFFFu - (uint32_t)(key & 0xFFFFFFFFull));
+
+  // a7 + a8: winner in FP64, its mask, and the normal equations over its inliers
+  if (tid == 0) {
+    int q[3];
+    draw_minimal_set<DIM>(a.key, ci, hstar, N, q);
+    const float4 p0 = rows[q[0]], p1 = rows[q[1]];
+    const float4 p2 = DIM == 3 ? rows[q[2]] : p0;
+    Hyp32 hy = hyp_f32<DIM>(p0, p1, p2, wmax, 0.0f, 0.0f, a.tau32);
+    if (hy.kind != kHypNormal) {
+      hy.thi = __int_as_float(0x7f800000);
+      hy.tlo = -1.0f;
+    }
+    cs.win = make_float4(hy.nx, hy.ny, hy.nz, hy.thi);
+    cs.win_tlo = hy.tlo;
+    double v[3] = {0.0, 0.0, 0.0};
+    hyp_f64<DIM>(a, o, ci, hstar, N, v);
+    cs.v64[0] = v[0];
+    cs.v64[1] = v[1];
+    cs.v64[2] = v[2];
+  }
+  __syncthreads();
+  const float4 win = cs.win;
+  const float wtlo = cs.win_tlo;
+  const double v64[3] = {cs.v64[0], cs.v64[1], cs.v64[2]};
+  constexpr int NS = DIM == 2 ? 5 : 9;
+  double sums[NS];
+#pragma unroll
+  for (int i = 0; i < NS; ++i) sums[i] = 0.0;
+  int nin = 0;
+  for (int j = tid; j < N; j += kThreads) {
+    const float4 p = rows[j];
+    const float r = fabsf(resid_f32<DIM>(p, win.x, win.y, win.z));
+    bool in = r <= wtlo;
+    const bool band = !in && !(r > win.w);
+    if (in || band) {
+      double a64[3];
+      row_f64<DIM>(a.az[o + j], DIM == 3 ? a.el[o + j] : 0.0f, a64);
+      const double w = (double)(DIM == 2 ? p.z : p.w);
+      if (band) in = fabs(residual_f64<DIM>(a64, w, v64)) <= a.tau;
+      if (in) {
+        ++nin;
+        if (DIM == 2) {
+          sums[0] = fma(a64[0], a64[0], sums[0]);
+          sums[1] = fma(a64[0], a64[1], sums[1]);
+          sums[2] = fma(a64[1], a64[1], sums[2]);
+          sums[3] = fma(a64[0], w, sums[3]);
+          sums[4] = fma(a64[1], w, sums[4]);
+        } else {
+          sums[0] = fma(a64[0], a64[0], sums[0]);
+          sums[1] = fma(a64[0], a64[1], sums[1]);
+          sums[2] = fma(a64[0], a64[2], sums[2]);
+          sums[3] = fma(a64[1], a64[1], sums[3]);
+          sums[4] = fma(a64[1], a64[2], sums[4]);
+          sums[5] = fma(a64[2], a64[2], sums[5]);
+          sums[6] = fma(a64[0], w, sums[6]);
+          sums[7] = fma(a64[1], w, sums[7]);
+          sums[8] = fma(a64[2], w, sums[8]);
+        }
+      }
+    }
+    a.mask[o + j] = in ? 1 : 0;
+  }
+  const int warp = tid >> 5, lane = tid & 31;
+  nin = warp_sum(nin);
+#pragma unroll
+  for (int i = 0; i < NS; ++i) sums[i] = warp_sum(sums[i]);
+  if (lane == 0) {
+    cs.red_i[warp] = nin;
+#pragma unroll
+    for (int i = 0; i < NS; ++i) cs.red_d[warp][i] = sums[i];
+  }
+  __syncthreads();
+  if (tid == 0) {
+    int n_in = 0;
+    double t[NS];
+#pragma unroll
+    for (int i = 0; i < NS; ++i) t[i] = 0.0;
+    for (int w = 0; w < kWarps; ++w) {
+      n_in += cs.red_i[w];
+#pragma unroll
+      for (int i = 0; i < NS; ++i) t[i] += cs.red_d[w][i];
+    }
+    double vout[3] = {v64[0], v64[1], v64[2]};
+    int st = 0;
+    if (DIM == 2) {
+      const double tr = t[0] + t[2];
+      const double limit = 1e-12 * (tr * tr);
+      const double det = det2_f64(t[0], t[1], t[1], t[2]);
+      if (n_in >= 2 && fabs(det) > limit) {
+        const double G0[3] = {t[0], t[1], 0.0}, G1[3] = {t[1], t[2], 0.0}, g[3] = {t[3], t[4], 0.0};
+        double vs[3];
+        solve_f64<2>(G0, G1, nullptr, g, 0.0, vs, nullptr);
+        vout[0] = vs[0];
+        vout[1] = vs[1];
+        vout[2] = 0.0;
+      } else {
+        st |= RVH_STATUS_LSQ_FALLBACK;
+      }
+    } else {
+      const double tr = t[0] + t[3] + t[5];
+      const double limit = 1e-12 * (tr * tr * tr);
+      const double G0[3] = {t[0], t[1], t[2]}, G1[3] = {t[1], t[3], t[4]}, G2[3] = {t[2], t[4], t[5]};
+      const double det = det3_f64(G0, G1, G2);
+      if (n_in >= 3 && fabs(det) > limit) {
+        const double g[3] = {t[6], t[7], t[8]};
+        double vs[3];
+        solve_f64<3>(G0, G1, G2, g, 0.0, vs, nullptr);
+        vout[0] = vs[0];
+        vout[1] = vs[1];
+        vout[2] = vs[2];
+      } else {
+        st |= RVH_STATUS_LSQ_FALLBACK;
+      }
+    }
+    a.vx[ci] = vout[0];
+    a.vy[ci] = vout[1];
+    if (a.vz) a.vz[ci] = DIM == 3 ? vout[2] : 0.0;
+    a.heading[ci] = atan2(vout[1], vout[0]);
+    a.inlier_count[ci] = n_in;
+    a.best[ci] = hstar;
+    a.status[ci] = st;
+  }
+  __syncthreads();
+}
+
+template <int DIM>
+__global__ void __launch_bounds__(kThreads, 2) fused_kernel(FusedArgs a) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  __shared__ ClusterShared cs;
+  __shared__ int s_item;
+  Smem S;
+  unsigned char* p = smem_raw;
+  S.rows = reinterpret_cast<float4*>(p);
+  p += (size_t)a.nmax_smem * sizeof(float4);
+  S.hyp = reinterpret_cast<float4*>(p);
+  p += (size_t)a.hchunk * sizeof(float4);
+  S.tlo = reinterpret_cast<float*>(p);
+  p += (size_t)a.hchunk * sizeof(float);
+  S.U = reinterpret_cast<int*>(p);
+  p += (size_t)a.hchunk * sizeof(int);
+  S.cand = reinterpret_cast<int*>(p);
+  p += (size_t)a.hchunk * sizeof(int);
+  S.kind = reinterpret_cast<int8_t*>(p);
+
+  if (threadIdx.x < 4) cs.ctr[threadIdx.x] = 0ull;
+  for (;;) {
+    __syncthreads();
+    if (threadIdx.x == 0) s_item = atomicAdd(a.work_counter, 1);
+    __syncthreads();
+    const int item = s_item;
+    if (item >= a.n_items) break;
+    const int2 fc = a.worklist[item];
+    const FrameDesc& F = a.f[fc.x];
+    const int ci = fc.y;
+    const int64_t o = F.offsets[ci], e = F.offsets[ci + 1];
+    if (e - o <= (int64_t)a.nmax_smem || e < o) {
+      process_cluster<DIM, true>(F, S, cs, ci, a.hchunk, a.pw, a.hpl);
+    } else {
+      process_cluster<DIM, false>(F, S, cs, ci, a.hchunk, a.pw, a.hpl);
+    }
+  }
+  __syncthreads();
+  if (threadIdx.x < 4 && a.stats) {
+    unsigned long long v = cs.ctr[threadIdx.x];
+    if (v) atomicAdd(&a.stats[threadIdx.x], v);
+  }
+}
+
+// Orders the batch's (frame, cluster) items by decreasing floor(log2(N * H))
+// (longest-processing-time first) and resets the work counter.  One CTA.
+__device__ __forceinline__ int item_bucket(const FrameDesc& F, int ci) {
+  const int64_t n = (int64_t)F.offsets[ci + 1] - F.offsets[ci];
+  const int64_t cost = n > 0 ? n * (int64_t)F.H : 1;
+  return 63 - min(63 - __clzll(cost), 63);  // 0 = most expensive
+}
+
+__global__ void worklist_kernel(FusedArgs a) {
+  __shared__ int hist[64];
+  if (threadIdx.x < 64) hist[threadIdx.x] = 0;
+  __syncthreads();
+  for (int f = 0; f < a.n_frames; ++f) {
+    const FrameDesc& F = a.f[f];
+    for (int i = threadIdx.x; i < F.n_clusters; i += blockDim.x) atomicAdd(&hist[item_bucket(F, i)], 1);
+  }
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    int s = 0;
+    for (int b = 0; b < 64; ++b) {
+      const int c = hist[b];
+      hist[b] = s;
+      s += c;
+    }
+    *a.work_counter = 0;
+  }
+  __syncthreads();
+  for (int f = 0; f < a.n_frames; ++f) {
+    const FrameDesc& F = a.f[f];
+    for (int i = threadIdx.x; i < F.n_clusters; i += blockDim.x)
+      a.worklist[atomicAdd(&hist[item_bucket(F, i)], 1)] = make_int2(f, i);
+  }
+}
+
+size_t fused_smem_bytes(int nmax_smem, int hchunk) {
+  return (size_t)nmax_smem * sizeof(float4) + (size_t)hchunk * (sizeof(float4) + sizeof(float) + 2 * sizeof(int) + 1);
+}
+
+cudaError_t launch_worklist(const FusedArgs& a, cudaStream_t s) {
+  worklist_kernel<<<1, 1024, 0, s>>>(a);
+  return cudaGetLastError();
+}
+
+cudaError_t fused_configure(int dim, size_t smem) {
+  if (dim == 2) return cudaFuncSetAttribute(fused_kernel<2>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  return cudaFuncSetAttribute(fused_kernel<3>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+}
+
+cudaError_t fused_occupancy(int dim, size_t smem, int* blocks_per_sm) {
+  if (dim == 2)
+    return cudaOccupancyMaxActiveBlocksPerMultiprocessor(blocks_per_sm, fused_kernel<2>, kThreads, smem);
+  return cudaOccupancyMaxActiveBlocksPerMultiprocessor(blocks_per_sm, fused_kernel<3>, kThreads, smem);
+}
+
+cudaError_t launch_fused(int dim, const FusedArgs& a, int grid, size_t smem, cudaStream_t s) {
+  if (dim == 2) fused_kernel<2><<<grid, kThreads, smem, s>>>(a);
+  else fused_kernel<3><<<grid, kThreads, smem, s>>>(a);
+  return cudaGetLastError();
+}
+
+}  // namespace rvh

@@ -1,0 +1,87 @@
+// Launch interfaces of the rvh kernels (host side of the library).
+#pragma once
+
+#include <cstddef>
+#include <cstdint>
+#include <cuda_runtime.h>
+
+namespace rvh {
+
+// tau rounded outward to FP32: lo = largest float <= tau, hi = smallest float >= tau.
+struct TauPair {
+  float lo, hi;
+};
+
+// One frame of a batch: inputs, per-frame estimator settings, outputs.
+struct FrameDesc {
+  const float* az;
+  const float* el;
+  const float* dop;
+  const int32_t* offsets;
+  int32_t n_clusters;
+  int32_t H;
+  int64_t n_points;
+  float4* rows_g;            // [n_points] FP32 rows of clusters larger than nmax_smem
+  double tau;
+  double eps;
+  TauPair tau32;
+  float acc, rej;            // FP32 conditioning thresholds (certain accept / certain reject)
+  uint2 key;                 // Philox key = seed
+  double* vx;
+  double* vy;
+  double* vz;
+  double* heading;
+  int32_t* inlier_count;
+  int32_t* best;
+  int32_t* status;
+  uint8_t* mask;
+};
+
+constexpr int kMaxBatchFrames = 32;
+
+// A batch of frames of one model dimension, processed by one persistent launch.
+struct FusedArgs {
+  FrameDesc f[kMaxBatchFrames];
+  int n_frames;
+  int n_items;               // sum of n_clusters over the frames
+  int2* worklist;            // [n_items] (frame, cluster), written by the worklist kernel
+  int* work_counter;
+  unsigned long long* stats;  // [4]: candidates, band points, fp64 trials, reserved
+  int nmax_smem;
+  int hchunk;
+  int pw, hpl;
+};
+
+size_t fused_smem_bytes(int nmax_smem, int hchunk);
+cudaError_t fused_configure(int dim, size_t smem);
+cudaError_t fused_occupancy(int dim, size_t smem, int* blocks_per_sm);
+cudaError_t launch_worklist(const FusedArgs& a, cudaStream_t s);
+cudaError_t launch_fused(int dim, const FusedArgs& a, int grid, size_t smem, cudaStream_t s);
+
+struct BaselineArgs {
+  const float* az;
+  const float* el;
+  const float* dop;
+  const int32_t* offsets;
+  int64_t n_points;
+  double* rows64_g;          // [n_points * 4] FP64 rows of clusters larger than nmax_smem
+  int H;
+  double tau;
+  double eps;
+  uint2 key;
+  double* vx;
+  double* vy;
+  double* vz;
+  double* heading;
+  int32_t* inlier_count;
+  int32_t* best;
+  int32_t* status;
+  uint8_t* mask;
+  int nmax_smem;
+};
+
+size_t baseline_smem_bytes(int nmax_smem);
+cudaError_t baseline_configure(int dim, size_t smem);
+cudaError_t launch_baseline_cluster(int dim, const BaselineArgs& a, int cluster, size_t smem, cudaStream_t s);
+
+}  // namespace rvh

@@ -1,0 +1,93 @@
+"""Helpers for the GPU tests: run the library on a frame, compare with the oracle."""
+from __future__ import annotations
+
+import ctypes
+import math
+
+import numpy as np
+
+import oracle
+
+OUT_KEYS = ("vx", "vy", "vz", "heading", "inlier_count", "best_hypothesis", "status", "inlier_mask")
+
+
+def torch_mod():
+    import torch
+    return torch
+
+
+def alloc_outputs(n_clusters: int, n_points: int, device: str):
+    torch = torch_mod()
+    kw = dict(device=device)
+    return {
+        "vx": torch.empty(n_clusters, dtype=torch.float64, **kw),
+        "vy": torch.empty(n_clusters, dtype=torch.float64, **kw),
+        "vz": torch.empty(n_clusters, dtype=torch.float64, **kw),
+        "heading": torch.empty(n_clusters, dtype=torch.float64, **kw),
+        "inlier_count": torch.empty(n_clusters, dtype=torch.int32, **kw),
+        "best_hypothesis": torch.empty(n_clusters, dtype=torch.int32, **kw),
+        "status": torch.empty(n_clusters, dtype=torch.int32, **kw),
+        "inlier_mask": torch.empty(max(n_points, 1), dtype=torch.uint8, **kw),
+    }
+
+
+def run_rvh(ctx, az, dop, off, *, el=None, H: int, tau: float, seed: int, cond_eps: float = 0.0,
+            baseline: bool = False, device: str = "cuda", stream=None) -> dict:
+    """Runs rvh_estimate (or the baseline) through the C ABI and returns numpy outputs."""
+    torch = torch_mod()
+    from paper_2012_12618_gb300 import rvh
+
+    def t(a, dt):
+        return torch.as_tensor(np.ascontiguousarray(a), dtype=dt).to(device)
+
+    taz, tdop, toff = t(az, torch.float32), t(dop, torch.float32), t(off, torch.int32)
+    tel = None if el is None else t(el, torch.float32)
+    n_points = int(np.asarray(az).shape[0])
+    outs = alloc_outputs(int(np.asarray(off).shape[0]) - 1, n_points, device)
+    frame = rvh.make_frame(taz, tdop, toff, tel)
+    params = rvh.make_params(3 if el is not None else 2, H, tau, seed, cond_eps)
+    res = rvh.make_result(outs)
+    fn = rvh.rvh_estimate_baseline if baseline else rvh.rvh_estimate
+    rc = fn(ctx.handle, frame, params, res, stream)
+    if rc != rvh.RVH_OK:
+        raise RuntimeError(f"rvh returned {rc}: {rvh.rvh_last_error(None)}")
+    if device.startswith("cuda"):
+        torch.cuda.synchronize()
+    out = {k: v.cpu().numpy() for k, v in outs.items()}
+    out["inlier_mask"] = out["inlier_mask"][:n_points]
+    return out
+
+
+def run_oracle(az, dop, off, *, el=None, H: int, tau: float, seed: int, cond_eps=None, subset=None) -> dict:
+    return oracle.estimate(az, dop, off, elevation=el, num_hypotheses=H, tau=tau, seed=seed,
+                           cond_eps=cond_eps, subset=subset, want_fragile=True)
+
+
+def compare(gpu: dict, orc: dict, off, *, subset=None, vel_tol: float = 1e-6, head_tol: float = 1e-6) -> dict:
+    """Element-wise comparison.  Masks, counts, winners and status are bit-exact;
+    velocities within vel_tol m/s; headings (wrapped) within head_tol rad where
+    |v| >= 1e-3 m/s.  Clusters the oracle flags as fragile (a decision within
+    rounding distance of its threshold) are reported, not compared."""
+    off = np.asarray(off)
+    nc = off.shape[0] - 1
+    idx = np.arange(nc) if subset is None else np.asarray(subset)
+    frag = orc["fragile"]
+    report = {"clusters": int(idx.shape[0]), "fragile": int(frag.sum()), "mismatch": []}
+    for k_out, ci in enumerate(idx):
+        if frag[k_out]:
+            continue
+        s, e = off[ci], off[ci + 1]
+        for key in ("inlier_count", "best_hypothesis", "status"):
+            if gpu[key][ci] != orc[key][k_out]:
+                report["mismatch"].append((int(ci), key, int(gpu[key][ci]), int(orc[key][k_out])))
+        if not np.array_equal(gpu["inlier_mask"][s:e], orc["inlier_mask"][s:e]):
+            report["mismatch"].append((int(ci), "inlier_mask", None, None))
+        for key in ("vx", "vy", "vz"):
+            g, o = gpu[key][ci], orc[key][k_out]
+            if np.isnan(o) != np.isnan(g) or (not np.isnan(o) and abs(g - o) > vel_tol):
+                report["mismatch"].append((int(ci), key, float(g), float(o)))
+        if not np.isnan(orc["vx"][k_out]) and math.hypot(orc["vx"][k_out], orc["vy"][k_out]) >= 1e-3:
+            d = (gpu["heading"][ci] - orc["heading"][k_out] + math.pi) % (2 * math.pi) - math.pi
+            if abs(d) > head_tol:
+                report["mismatch"].append((int(ci), "heading", float(gpu["heading"][ci]), float(orc["heading"][k_out])))
+    return report

@@ -1,0 +1,52 @@
+"""The C ABI library builds, loads and exports every entry point that
+include/rvh.h declares; calls that need no GPU behave as documented."""
+import ctypes
+import os
+import re
+
+import pytest
+
+from paper_2012_12618_gb300 import build, rvh
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+def declared_functions():
+    text = open(os.path.join(ROOT, "include", "rvh.h")).read()
+    text = re.sub(r"/\*.*?\*/", "", text, flags=re.S)
+    return sorted(set(re.findall(r"\b(rvh_[a-z_]+)\s*\(", text)))
+
+
+def test_header_declares_the_boundary():
+    names = declared_functions()
+    for must in ("rvh_create", "rvh_destroy", "rvh_estimate", "rvh_submit", "rvh_poll", "rvh_wait",
+                 "rvh_last_error"):
+        assert must in names
+
+
+def test_library_exports_every_declared_symbol():
+    L = ctypes.CDLL(build.build())
+    for name in declared_functions():
+        assert hasattr(L, name), name
+    # the binding covers the same names
+    assert set(declared_functions()) == set(rvh.SIGNATURES)
+
+
+def test_null_context_is_rejected():
+    f = rvh.rvh_frame()
+    p = rvh.make_params(2, 8, 0.1, 1)
+    r = rvh.rvh_result()
+    assert rvh.rvh_estimate(None, f, p, r) == rvh.RVH_EINVAL
+    assert "ctx" in rvh.rvh_last_error(None)
+    assert rvh.rvh_poll(None, 1) == rvh.RVH_EINVAL
+    assert rvh.rvh_set_schedule(None, 1, 4) == rvh.RVH_EINVAL
+
+
+def test_create_without_gpu_reports_cuda_error():
+    torch = pytest.importorskip("torch")
+    if torch.cuda.is_available():
+        pytest.skip("a GPU is present")
+    h = ctypes.c_void_p()
+    rc = rvh.rvh_create(ctypes.byref(h), 0, 0)
+    assert rc == rvh.RVH_ECUDA and not h.value
+    assert rvh.rvh_last_error(None)

@@ -1,0 +1,162 @@
+"""GPU parity: the CUDA path (through the C ABI) against the FP64 oracle.
+
+Bar: inlier masks, inlier counts, winning hypothesis indices and status bits
+bit-exact; vx, vy, vz within 1e-6 m/s; heading within 1e-6 rad (where
+|v| >= 1e-3 m/s).  Full-size workloads are compared on sampled clusters the
+oracle computes one by one (the RNG is keyed per cluster, so any subset is
+well defined).
+"""
+import numpy as np
+import pytest
+
+from paper_2012_12618_gb300 import synth
+from tests import gpu_util as G
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def ctx():
+    torch = pytest.importorskip("torch")
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_2012_12618_gb300 import rvh
+    c = rvh.Context(0)
+    yield c
+    c.close()
+
+
+def _check(rep):
+    assert not rep["mismatch"], rep["mismatch"][:20]
+    assert rep["fragile"] <= max(1, rep["clusters"] // 1000), rep
+
+
+def _run_pair(ctx, f, w, *, H=None, seed=None, subset=None, baseline=False, tau=None):
+    H = H or w.num_hypotheses
+    seed = w.seed if seed is None else seed
+    tau = w.tau if tau is None else tau
+    g = G.run_rvh(ctx, f.azimuth, f.doppler, f.offsets, el=f.elevation, H=H, tau=tau, seed=seed,
+                  baseline=baseline)
+    o = G.run_oracle(f.azimuth, f.doppler, f.offsets, el=f.elevation, H=H, tau=tau, seed=seed, subset=subset)
+    return g, o
+
+
+def _sample(f, k, rng_seed=0):
+    n = np.diff(f.offsets)
+    rng = np.random.default_rng(rng_seed)
+    big = np.argsort(-n)[:k // 4]                      # the largest clusters (global-row path too)
+    rest = rng.choice(f.n_clusters, size=k - big.shape[0], replace=False)
+    return np.unique(np.concatenate([big, rest]))
+
+
+def test_frame64_full(ctx):
+    w = synth.WORKLOADS["frame64"]
+    f = synth.make_frame(w)
+    g, o = _run_pair(ctx, f, w)
+    _check(G.compare(g, o, f.offsets))
+
+
+@pytest.mark.parametrize("name,nc", [("dense2d", 192), ("stress2d", 256), ("dense3d", 96)])
+def test_small_full(ctx, name, nc):
+    w = synth.WORKLOADS[name]
+    f = synth.make_frame(w, n_clusters=nc, gen_seed=w.gen_seed + 100)
+    g, o = _run_pair(ctx, f, w)
+    _check(G.compare(g, o, f.offsets))
+
+
+@pytest.mark.parametrize("name,k", [("dense2d", 96), ("stress2d", 128), ("dense3d", 48)])
+def test_full_size_sampled(ctx, name, k):
+    w = synth.WORKLOADS[name]
+    f = synth.make_frame(w)
+    sub = _sample(f, k)
+    g, o = _run_pair(ctx, f, w, subset=sub)
+    _check(G.compare(g, o, f.offsets, subset=sub))
+
+
+def test_noise_free_band(ctx):
+    """Noise-free inliers plus band points at tau +- 2e-5: many points fall in
+    the FP32 error band and are decided in FP64."""
+    import dataclasses
+    w = dataclasses.replace(synth.WORKLOADS["stress2d"], noise_sigma=0.0)
+    f = synth.make_frame(w, n_clusters=256, gen_seed=77)
+    g, o = _run_pair(ctx, f, w)
+    _check(G.compare(g, o, f.offsets))
+
+
+def test_baseline_parity(ctx):
+    for name, nc in (("frame64", 64), ("dense3d", 24)):
+        w = synth.WORKLOADS[name]
+        f = synth.make_frame(w, n_clusters=nc, gen_seed=5)
+        H = 256
+        g, o = _run_pair(ctx, f, w, H=H, baseline=True)
+        _check(G.compare(g, o, f.offsets))
+
+
+@pytest.mark.parametrize("pw,hpl", [(1, 4), (1, 8), (8, 4), (8, 8), (32, 4), (32, 8)])
+def test_schedules_agree(ctx, pw, hpl):
+    from paper_2012_12618_gb300 import rvh
+    w = synth.WORKLOADS["dense2d"]
+    f = synth.make_frame(w, n_clusters=128, gen_seed=9)
+    assert rvh.rvh_set_schedule(ctx.handle, pw, hpl) == 0
+    try:
+        g, o = _run_pair(ctx, f, w, H=640)
+    finally:
+        rvh.rvh_set_schedule(ctx.handle, 0, 0)
+    _check(G.compare(g, o, f.offsets))
+
+
+def test_edge_cases(ctx):
+    rng = np.random.default_rng(3)
+    sizes = [0, 1, 2, 3, 5, 40, 2047, 2048, 2049, 5000, 17]
+    w = synth.WORKLOADS["dense2d"]
+    f = synth.make_frame(w, sizes=np.array(sizes), gen_seed=8)
+    az = f.azimuth.copy()
+    dop = f.doppler.copy()
+    off = f.offsets
+    # cluster 4 (5 points): every point at one azimuth -> all minimal sets singular
+    az[off[4]:off[5]] = np.float32(0.25)
+    # cluster 10: duplicated points and a NaN Doppler
+    s = off[10]
+    az[s + 1] = az[s]
+    dop[s + 1] = dop[s]
+    dop[s + 3] = np.nan
+    for H, tau in ((1, 0.1), (1500, 0.1), (64, 0.0), (300, 5.0)):
+        g = G.run_rvh(ctx, az, dop, off, H=H, tau=tau, seed=11)
+        o = G.run_oracle(az, dop, off, H=H, tau=tau, seed=11)
+        _check(G.compare(g, o, off))
+    st = g["status"]
+    assert st[0] & 1 and st[1] & 1 and st[2] == 0 or st[2] & 4
+
+
+def test_3d_edge_cases(ctx):
+    w = synth.WORKLOADS["dense3d"]
+    f = synth.make_frame(w, sizes=np.array([0, 2, 3, 4, 9, 1500, 2100, 100]), gen_seed=12)
+    for H in (1, 100, 1100):
+        g = G.run_rvh(ctx, f.azimuth, f.doppler, f.offsets, el=f.elevation, H=H, tau=0.1, seed=2)
+        o = G.run_oracle(f.azimuth, f.doppler, f.offsets, el=f.elevation, H=H, tau=0.1, seed=2)
+        _check(G.compare(g, o, f.offsets))
+
+
+def test_empty_frame(ctx):
+    g = G.run_rvh(ctx, np.zeros(0, np.float32), np.zeros(0, np.float32), np.zeros(1, np.int32), H=8, tau=0.1, seed=1)
+    assert g["vx"].shape == (0,)
+
+
+def test_host_and_device_pointers_agree(ctx):
+    w = synth.WORKLOADS["frame64"]
+    f = synth.make_frame(w, n_clusters=40, gen_seed=21)
+    a = G.run_rvh(ctx, f.azimuth, f.doppler, f.offsets, H=256, tau=0.1, seed=4, device="cuda")
+    b = G.run_rvh(ctx, f.azimuth, f.doppler, f.offsets, H=256, tau=0.1, seed=4, device="cpu")
+    for k in G.OUT_KEYS:
+        assert np.array_equal(a[k], b[k], equal_nan=True), k
+
+
+def test_seeds_change_draws(ctx):
+    w = synth.WORKLOADS["frame64"]
+    f = synth.make_frame(w, n_clusters=32, gen_seed=31)
+    bests = []
+    for seed in (1, 2, 0xFFFFFFFF00000001):
+        g, o = _run_pair(ctx, f, w, seed=seed)
+        _check(G.compare(g, o, f.offsets))
+        bests.append(g["best_hypothesis"])
+    assert not np.array_equal(bests[0], bests[1])
