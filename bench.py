@@ -1,0 +1,343 @@
+"""Throughput of the fused RANSAC + LSQ path on the dense 2D traffic frame.
+
+One step = one rvh_estimate over a whole frame: 4096 clusters with sizes
+log-uniform in 8..2048 (1.53 M points), 2D model, 1024 hypotheses per
+cluster, tau = 0.1 m/s.  Inputs are resident in device memory; between
+timed steps the L2 is flushed (a 256 MiB write), outside the step's events.
+
+Prints one JSON line (rank 0).  --impl reference times the FP64 CPU oracle on
+the host cores instead (each step: a bounded sample of the same workload).
+"""
+from __future__ import annotations
+
+import argparse
+import ctypes
+import hashlib
+import json
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+WORKLOAD = "dense2d"
+FP32_LANES_PER_SM = 128          # FP32 FMA lanes per SM (Blackwell)
+SM_MAX_MHZ_FALLBACK = 2070.0
+KERNEL_SOURCES = ["rvh_fused.cu", "rvh_device.cuh", "rvh_kernels.h"]
+
+
+def kernel_hash() -> str:
+    h = hashlib.sha256()
+    for f in KERNEL_SOURCES:
+        with open(os.path.join(ROOT, "paper_2012_12618_gb300", "csrc", f), "rb") as fh:
+            h.update(fh.read())
+    return h.hexdigest()[:16]
+
+
+def recorded_traffic():
+    """DRAM bytes per fused launch from the committed ncu summary, if it was
+    taken on the current kernel source (else None)."""
+    path = os.path.join(ROOT, "profiles", "fused_dense2d_traffic.json")
+    try:
+        rec = json.load(open(path))
+    except (OSError, ValueError):
+        return None
+    if rec.get("kernel_hash") != kernel_hash():
+        return None
+    return rec.get("dram_bytes_per_launch")
+
+
+class ClockSampler:
+    """nvidia-smi sampling of SM clocks and throttle reasons during the timed region."""
+
+    FIELDS = ("clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index: int):
+        self.index = index
+        self.samples = []
+        self._stop = threading.Event()
+        self._t = None
+
+    def _run(self):
+        while not self._stop.is_set():
+            try:
+                out = subprocess.run(["nvidia-smi", "-i", str(self.index), f"--query-gpu={self.FIELDS}",
+                                      "--format=csv,noheader,nounits"], capture_output=True, text=True,
+                                     timeout=5).stdout.strip()
+                if out:
+                    self.samples.append([x.strip() for x in out.split(",")])
+            except Exception:
+                pass
+            self._stop.wait(0.2)
+
+    def __enter__(self):
+        self._t = threading.Thread(target=self._run, daemon=True)
+        self._t.start()
+        return self
+
+    def __exit__(self, *exc):
+        self._stop.set()
+        self._t.join(timeout=10)
+
+    def summary(self):
+        if not self.samples:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["unsampled"]}
+        sm = [float(s[0]) for s in self.samples if s[0].replace(".", "").isdigit()]
+        mx = [float(s[1]) for s in self.samples if s[1].replace(".", "").isdigit()]
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({names[i] for s in self.samples for i in range(4)
+                          if len(s) > 4 + i and s[4 + i].lower().startswith("active")})
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": max(mx) if mx else None,
+                "reasons": reasons, "samples": len(self.samples)}
+
+
+def dist_env():
+    ws = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return ws, rank, local
+
+
+def reference_arm(args):
+    """The FP64 CPU oracle, as it stands, on the host cores: each step
+    estimates a bounded sample of the workload's clusters."""
+    ws, rank, _ = dist_env()
+    if rank != 0:
+        return 0
+    import oracle
+    from paper_2012_12618_gb300 import synth
+    w = synth.WORKLOADS[WORKLOAD]
+    f = synth.make_frame(w)
+    n_sample = 256
+    rng = np.random.default_rng(0)
+    times = []
+    for step in range(args.warmup + args.steps):
+        sub = np.sort(rng.choice(f.n_clusters, n_sample, replace=False))
+        t0 = time.perf_counter()
+        oracle.estimate(f.azimuth, f.doppler, f.offsets, num_hypotheses=w.num_hypotheses, tau=w.tau,
+                        seed=w.seed, subset=sub)
+        dt = time.perf_counter() - t0
+        if step >= args.warmup:
+            times.append(dt)
+    total = sum(times)
+    value = n_sample * len(times) / total
+    line = {
+        "impl": "reference", "metric": "clusters/s", "value": value, "unit": "clusters/s",
+        "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
+        "ms_per_step": 1e3 * total / len(times), "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "config": {"workload": f"{WORKLOAD}: {w.n_clusters} clusters, sizes log-uniform 8..2048, 2D, "
+                               f"H={w.num_hypotheses}, tau={w.tau}", "sample_clusters_per_step": n_sample},
+        "cpu_baseline": {"value": value, "unit": "clusters/s", "cores": 1, "kind": "oracle",
+                         "sample": f"{n_sample} random clusters of the {WORKLOAD} frame per step"},
+        "e2e": {"value": value, "unit": "clusters/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=100)
+    ap.add_argument("--warmup", type=int, default=5)
+    ap.add_argument("--impl", default="rvh", choices=["rvh", "reference"])
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-gpu-baseline", action="store_true")
+    args = ap.parse_args()
+    if args.impl == "reference":
+        return reference_arm(args)
+
+    import torch
+    ws, rank, local = dist_env()
+    if ws > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl" if torch.cuda.is_available() else "gloo")
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+
+    from paper_2012_12618_gb300 import rvh, synth
+    w = synth.WORKLOADS[WORKLOAD]
+    # weak scaling: every rank estimates its own frame (independent sensors)
+    f = synth.make_frame(w, gen_seed=w.gen_seed + 1000 * rank)
+    nc, npts = f.n_clusters, f.n_points
+    sizes = np.diff(f.offsets).astype(np.int64)
+    pairs = int(sizes.sum()) * w.num_hypotheses
+
+    ctx = rvh.Context(local)
+    d_az = torch.from_numpy(f.azimuth).to(dev)
+    d_dop = torch.from_numpy(f.doppler).to(dev)
+    d_off = torch.from_numpy(f.offsets).to(dev)
+    outs = rvh.alloc_outputs(nc, npts, dev)
+    frame = rvh.make_frame(d_az, d_dop, d_off)
+    params = rvh.make_params(2, w.num_hypotheses, w.tau, w.seed)
+    res = rvh.make_result(outs)
+    # a dedicated stream: the library and the timing events share it
+    stream = torch.cuda.Stream(dev)
+    torch.cuda.set_stream(stream)
+    sptr = ctypes.c_void_p(stream.cuda_stream)
+    flush = torch.empty(256 << 20, dtype=torch.uint8, device=dev)
+    stats = rvh.rvh_stats()
+
+    def step():
+        ctx.check(rvh.rvh_estimate(ctx.handle, frame, params, res, sptr), "rvh_estimate")
+
+    for _ in range(max(args.warmup, 3)):
+        flush.fill_(1)
+        step()
+    torch.cuda.synchronize()
+
+    step_ms, kern_ms = [], []
+    band = cand = fp64h = 0
+    phase = np.zeros(6)
+    if ws > 1:
+        torch.distributed.barrier()
+    torch.cuda.synchronize()
+    t_wall = time.perf_counter()
+    with ClockSampler(local) as clk:
+        for _ in range(args.steps):
+            flush.fill_(np.uint8(_ & 0xFF))
+            e0 = torch.cuda.Event(enable_timing=True)
+            e1 = torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            step()
+            e1.record(stream)
+            e1.synchronize()
+            step_ms.append(e0.elapsed_time(e1))
+            ctx.check(rvh.rvh_get_stats(ctx.handle, stats), "rvh_get_stats")
+            kern_ms.append(stats.kernel_ms)
+            band += stats.band_points
+            cand += stats.candidates
+            fp64h += stats.fp64_hypotheses
+            phase += np.array(list(stats.phase_cycles), dtype=np.float64)
+        torch.cuda.synchronize()
+    wall = time.perf_counter() - t_wall
+    if ws > 1:
+        torch.distributed.barrier()
+    t_step = float(np.mean(step_ms)) * 1e-3
+    t_max = t_step
+    if ws > 1:
+        tt = torch.tensor([t_step], device=dev, dtype=torch.float64)
+        torch.distributed.all_reduce(tt, op=torch.distributed.ReduceOp.MAX)
+        t_max = float(tt.item())
+    value = nc * ws / t_max
+    grid = stats.grid
+
+    # ---- roofline of the fused kernel (FP32 pipe; 2 FMA = 4 flop per trial x point pair)
+    kern_s = float(np.mean(kern_ms)) * 1e-3
+    flops = 4.0 * pairs
+    achieved = flops / kern_s / 1e12
+    props = torch.cuda.get_device_properties(dev)
+    sms = props.multi_processor_count
+    peaks = {}
+    try:
+        peaks = json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))
+    except (OSError, ValueError):
+        pass
+    clocks = clk.summary()
+    max_mhz = float(peaks.get("sm_max_mhz") or clocks.get("sm_max_mhz") or SM_MAX_MHZ_FALLBACK)
+    peak = sms * FP32_LANES_PER_SM * 2 * max_mhz * 1e6 / 1e12
+    roofline = {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
+                "frac": achieved / peak, "traffic": recorded_traffic(),
+                "kernel": "rvh::fused_kernel<2>",
+                "peak_basis": f"{sms} SMs x {FP32_LANES_PER_SM} FP32 FMA lanes x 2 flop x {max_mhz:.0f} MHz",
+                "frac_at_measured_clock": (achieved / (sms * FP32_LANES_PER_SM * 2 * clocks["sm_mhz"] * 1e6 / 1e12)
+                                           if clocks.get("sm_mhz") else None),
+                "algorithmic_flops_per_launch": flops, "kernel_ms": kern_s * 1e3}
+
+    # ---- end to end through the C ABI with pinned host buffers (copies inside the timed region)
+    h_az = torch.from_numpy(f.azimuth).pin_memory()
+    h_dop = torch.from_numpy(f.doppler).pin_memory()
+    h_off = torch.from_numpy(f.offsets).pin_memory()
+    h_outs = {k: v.cpu().pin_memory() for k, v in outs.items()}
+    h_frame = rvh.make_frame(h_az, h_dop, h_off)
+    h_res = rvh.make_result(h_outs)
+    for _ in range(2):
+        ctx.check(rvh.rvh_estimate(ctx.handle, h_frame, params, h_res, sptr), "rvh_estimate(host)")
+    e2e_t = []
+    for _ in range(max(3, args.steps // 2)):
+        flush.fill_(3)
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        ctx.check(rvh.rvh_estimate(ctx.handle, h_frame, params, h_res, sptr), "rvh_estimate(host)")
+        e2e_t.append(time.perf_counter() - t0)
+    h2d = npts * 8 + (nc + 1) * 4
+    d2h = nc * (4 * 8 + 3 * 4) + npts
+    e2e = {"value": nc / float(np.mean(e2e_t)), "unit": "clusters/s", "h2d_bytes_per_step": h2d,
+           "d2h_bytes_per_step": d2h, "ms_per_step": 1e3 * float(np.mean(e2e_t))}
+
+    # ---- plain all-FP64 one-launch-per-cluster GPU version (same frame)
+    gpu_base = None
+    if not args.no_gpu_baseline:
+        base_out = rvh.alloc_outputs(nc, npts, dev)
+        bres = rvh.make_result(base_out)
+        ctx.check(rvh.rvh_estimate_baseline(ctx.handle, frame, params, bres, sptr), "baseline")
+        torch.cuda.synchronize()
+        b0 = torch.cuda.Event(enable_timing=True)
+        b1 = torch.cuda.Event(enable_timing=True)
+        b0.record(stream)
+        ctx.check(rvh.rvh_estimate_baseline(ctx.handle, frame, params, bres, sptr), "baseline")
+        b1.record(stream)
+        b1.synchronize()
+        bms = b0.elapsed_time(b1)
+        same = bool(torch.equal(base_out["inlier_mask"], outs["inlier_mask"]) and
+                    torch.equal(base_out["best_hypothesis"], outs["best_hypothesis"]))
+        gpu_base = {"value": nc / (bms * 1e-3), "unit": "clusters/s", "kind": "plain all-FP64 GPU kernel, "
+                    "one launch per cluster", "ms_per_step": bms, "fused_speedup": value / ws / (nc / (bms * 1e-3)),
+                    "identical_masks_and_winners": same}
+
+    # ---- the FP64 oracle on this host (rank 0, N = 1 only)
+    cpu = None
+    if rank == 0 and ws == 1 and not args.no_cpu_baseline:
+        import oracle
+        sub = np.sort(np.random.default_rng(1).choice(nc, 1024, replace=False))
+        t0 = time.perf_counter()
+        oracle.estimate(f.azimuth, f.doppler, f.offsets, num_hypotheses=w.num_hypotheses, tau=w.tau,
+                        seed=w.seed, subset=sub)
+        dt = time.perf_counter() - t0
+        cpu = {"value": sub.shape[0] / dt, "unit": "clusters/s", "cores": 1, "kind": "oracle",
+               "sample": f"{sub.shape[0]} random clusters of the {WORKLOAD} frame, single-threaded FP64 C",
+               "seconds": dt}
+
+    if rank == 0:
+        line = {
+            "metric": "clusters/s", "value": value, "unit": "clusters/s", "n_gpus": ws, "steps": args.steps,
+            "warmup": max(args.warmup, 3), "ms_per_step": t_max * 1e3, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f32+f64", "data": "synthetic",
+            "config": {"workload": f"{WORKLOAD}: {nc} clusters, sizes log-uniform 8..2048, {npts} points, 2D, "
+                                   f"H={w.num_hypotheses}, tau={w.tau} m/s, seed={w.seed}",
+                       "l2": "flushed between timed steps (256 MiB write outside the step events)",
+                       "per_rank": "one independent frame per rank"},
+            "pair_evals_per_s": pairs * ws / t_max,
+            "roofline": roofline,
+            "cpu_baseline": cpu,
+            "gpu_baseline": gpu_base,
+            "e2e": e2e,
+            "clocks": clocks,
+            "gpu_launches": 2 * args.steps,
+            "band": {"fp64_band_decisions_per_step": band / args.steps, "candidates_per_step": cand / args.steps,
+                     "fp64_trials_per_step": fp64h / args.steps,
+                     "band_rate_per_pair": band / args.steps / pairs},
+            "schedule": {"grid": grid, "points_per_warp": stats.points_per_warp,
+                         "hyps_per_lane": stats.hyps_per_lane},
+            "stage_share": dict(zip(["rows", "hypotheses", "scoring", "exact_rescoring", "mask_refine", "other"],
+                                    [round(float(x), 4) for x in phase / max(phase.sum(), 1.0)])),
+            "wall_s": wall,
+        }
+        print(json.dumps(line), flush=True)
+    ctx.close()
+    if ws > 1:
+        torch.distributed.destroy_process_group()
+    return 0
+
+
+if __name__ == "__main__":
+    sys.exit(main())

@@ -169,6 +169,10 @@ typedef struct {
   int32_t grid;                /* persistent CTAs of the last launch */
   int32_t points_per_warp;     /* schedule of the last launch */
   int32_t hyps_per_lane;
+  /* SM cycles summed over CTAs, per stage of the fused kernel: rows,
+   * hypotheses (draw + solve + bound), scoring pass, exact re-scoring,
+   * winner mask + refine, scheduling/other. */
+  int64_t phase_cycles[6];
 } rvh_stats;
 
 /* Counters of the last rvh_estimate on this context (synchronises its stream). */

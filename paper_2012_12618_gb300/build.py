@@ -36,6 +36,8 @@ def _deps() -> list[str]:
 
 
 def up_to_date() -> bool:
+    if os.environ.get("RVH_NVCC_EXTRA"):
+        return False
     if not os.path.exists(LIB):
         return False
     t = os.path.getmtime(LIB)
@@ -51,7 +53,8 @@ def build(force: bool = False, verbose: bool = False) -> str:
 
     def compile_one(src: str) -> str:
         obj = os.path.join(BUILD_DIR, src.replace(".cu", ".o"))
-        cmd = [cc, *ARCH, *FLAGS, "-c", os.path.join(CSRC, src), "-o", obj]
+        extra = os.environ.get("RVH_NVCC_EXTRA", "").split()
+        cmd = [cc, *ARCH, *FLAGS, *extra, "-c", os.path.join(CSRC, src), "-o", obj]
         r = subprocess.run(cmd, capture_output=True, text=True)
         if r.returncode != 0:
             raise RuntimeError(f"nvcc failed on {src}:\n{r.stdout}\n{r.stderr}")

@@ -5,6 +5,7 @@
 #include <chrono>
 #include <cmath>
 #include <condition_variable>
+#include <cstdlib>
 #include <cstring>
 #include <deque>
 #include <map>
@@ -120,6 +121,7 @@ struct rvh_ctx {
   int occ[4] = {0, 0, 0, 0};
   std::mutex mu;  // serialises rvh_estimate calls on this context
   rvh::Server* server = nullptr;
+  double2* trig = nullptr;  // device table of (cos, sin)(k/128)
 };
 
 namespace rvh {
@@ -162,8 +164,9 @@ void choose_schedule(rvh_ctx* ctx, int H, int* pw, int* hpl) {
 }
 
 // Fills the per-frame descriptor; the pointers must already be device pointers.
-void fill_desc(FrameDesc& d, const rvh_frame& f, const rvh_params& p, const float* az, const float* el,
-               const float* dop, const int32_t* off, float4* rows_g, const rvh_result& out) {
+void fill_desc(rvh_ctx* ctx, FrameDesc& d, const rvh_frame& f, const rvh_params& p, const float* az,
+               const float* el, const float* dop, const int32_t* off, float4* rows_g, const rvh_result& out) {
+  d.trig = ctx->trig;
   const int dim = p.model_dim;
   const double eps = p.cond_eps > 0 ? p.cond_eps : default_eps(dim);
   const double eD = (dim == 2 ? 1.081e-6 : 6.20e-6) + 0x1p-50;
@@ -239,12 +242,33 @@ int rvh_create(rvh_ctx** out, int device, size_t mem_budget_bytes) {
   c->device = device;
   c->budget = mem_budget_bytes ? mem_budget_bytes : ((size_t)4 << 30);
   cudaDeviceGetAttribute(&c->sms, cudaDevAttrMultiProcessorCount, device);
+  // tuning knobs for experiments: shared-memory row capacity and trial chunk
+  if (const char* e = getenv("RVH_NMAX_SMEM")) c->nmax_smem = std::max(64, atoi(e));
+  if (const char* e = getenv("RVH_HCHUNK")) c->hchunk = std::max(64, atoi(e));
   if (cudaStreamCreateWithFlags(&c->stream, cudaStreamNonBlocking) != cudaSuccess ||
       cudaEventCreateWithFlags(&c->last_done, cudaEventDisableTiming) != cudaSuccess ||
       cudaEventCreate(&c->ev0) != cudaSuccess || cudaEventCreate(&c->ev1) != cudaSuccess) {
     cudaGetLastError();
     delete c;
     return fail(RVH_ECUDA, "stream/event creation failed");
+  }
+  {
+    // (cos, sin)(k/128), k = -420..420, from the host's libm
+    std::vector<double2> tab(kTrigSize);
+    for (int k = -kTrigHalf; k <= kTrigHalf; ++k) {
+      const double t = k / 128.0;
+      tab[k + kTrigHalf] = make_double2(std::cos(t), std::sin(t));
+    }
+    void* p = nullptr;
+    int rc = ctx_alloc(c, &p, sizeof(double2) * kTrigSize);
+    if (rc == RVH_OK && cudaMemcpy(p, tab.data(), sizeof(double2) * kTrigSize, cudaMemcpyHostToDevice) != cudaSuccess)
+      rc = fail(RVH_ECUDA, "trig table upload failed");
+    if (rc != RVH_OK) {
+      cudaGetLastError();
+      rvh_destroy(c);
+      return rc;
+    }
+    c->trig = (double2*)p;
   }
   *out = c;
   return RVH_OK;
@@ -256,6 +280,7 @@ void rvh_destroy(rvh_ctx* ctx) {
   if (ctx->server) server_destroy(ctx->server);
   cudaStreamSynchronize(ctx->stream);
   if (ctx->scratch) ctx_free(ctx, ctx->scratch, ctx->scratch_bytes);
+  if (ctx->trig) ctx_free(ctx, ctx->trig, sizeof(double2) * kTrigSize);
   cudaEventDestroy(ctx->last_done);
   cudaEventDestroy(ctx->ev0);
   cudaEventDestroy(ctx->ev1);
@@ -280,8 +305,9 @@ int rvh_get_stats(rvh_ctx* ctx, rvh_stats* out) {
   RVH_CUDA(cudaSetDevice(ctx->device));
   if (ctx->have_launch) {
     RVH_CUDA(cudaEventSynchronize(ctx->last_done));
-    unsigned long long h[4] = {0, 0, 0, 0};
+    unsigned long long h[10] = {0, 0, 0, 0, 0, 0, 0, 0, 0, 0};
     RVH_CUDA(cudaMemcpy(h, ctx->stats_d, sizeof(h), cudaMemcpyDeviceToHost));
+    for (int k = 0; k < 6; ++k) ctx->last.phase_cycles[k] = (int64_t)h[4 + k];
     ctx->last.candidates = (int64_t)h[0];
     ctx->last.band_points = (int64_t)h[1];
     ctx->last.fp64_hypotheses = (int64_t)h[2];
@@ -332,7 +358,7 @@ static int stage(rvh_ctx* ctx, const rvh_frame* f, const rvh_params* p, rvh_resu
   };
   const size_t o_work = take(sizeof(int2) * (size_t)std::max(nc, 1));
   const size_t o_ctr = take(64);
-  const size_t o_stats = take(64);
+  const size_t o_stats = take(128);
   const size_t o_rows = take((fused ? sizeof(float4) : 4 * sizeof(double)) * (size_t)std::max<int64_t>(np, 1));
   const size_t o_az = d_az ? 0 : take(4 * (size_t)np);
   const size_t o_el = d_el ? 0 : take(4 * (size_t)np);
@@ -413,10 +439,10 @@ int rvh_estimate(rvh_ctx* ctx, const rvh_frame* frame, const rvh_params* params,
   rc = stage(ctx, frame, params, result, s, true, st);
   if (rc) return rc;
   ctx->stats_d = st.stats;
-  RVH_CUDA(cudaMemsetAsync(st.stats, 0, 32, s));
+  RVH_CUDA(cudaMemsetAsync(st.stats, 0, 80, s));
   FusedArgs a;
   memset(&a, 0, sizeof(a));
-  fill_desc(a.f[0], *frame, *params, st.az, st.el, st.dop, st.off, (float4*)st.rows, st.dev_out);
+  fill_desc(ctx, a.f[0], *frame, *params, st.az, st.el, st.dop, st.off, (float4*)st.rows, st.dev_out);
   a.n_frames = 1;
   a.n_items = frame->n_clusters;
   a.worklist = st.worklist;
@@ -455,7 +481,7 @@ int rvh_estimate_baseline(rvh_ctx* ctx, const rvh_frame* frame, const rvh_params
   BaselineArgs b;
   memset(&b, 0, sizeof(b));
   FrameDesc d;
-  fill_desc(d, *frame, *params, st.az, st.el, st.dop, st.off, nullptr, st.dev_out);
+  fill_desc(ctx, d, *frame, *params, st.az, st.el, st.dop, st.off, nullptr, st.dev_out);
   b.az = d.az;
   b.el = d.el;
   b.dop = d.dop;
@@ -475,6 +501,7 @@ int rvh_estimate_baseline(rvh_ctx* ctx, const rvh_frame* frame, const rvh_params
   b.status = d.status;
   b.mask = d.mask;
   b.nmax_smem = nmax;
+  b.trig = ctx->trig;
   RVH_CUDA(cudaEventRecord(ctx->ev0, s));
   for (int i = 0; i < frame->n_clusters; ++i) RVH_CUDA(launch_baseline_cluster(dim, b, i, smem, s));
   RVH_CUDA(cudaEventRecord(ctx->ev1, s));

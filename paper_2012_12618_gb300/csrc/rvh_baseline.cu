@@ -49,7 +49,7 @@ __global__ void __launch_bounds__(kBaseThreads) baseline_kernel(BaselineArgs a, 
   double* rows = N <= a.nmax_smem ? reinterpret_cast<double*>(smem_raw) : a.rows64_g + 4 * o;
   for (int j = tid; j < N; j += kBaseThreads) {
     double r[3];
-    row_f64<DIM>(a.az[o + j], DIM == 3 ? a.el[o + j] : 0.0f, r);
+    row_f64<DIM>(a.trig, a.az[o + j], DIM == 3 ? a.el[o + j] : 0.0f, r);
     rows[4 * j + 0] = r[0];
     rows[4 * j + 1] = r[1];
     rows[4 * j + 2] = r[2];

@@ -68,19 +68,43 @@ __device__ __forceinline__ double det3_f64(const double* m0, const double* m1, c
   return fma(m0[2], k2, fma(-m0[1], k1, m0[0] * k0));
 }
 
+// FP64 cos/sin of an FP32 angle by angle addition: t = k/128 + x with
+// |x| <= 1/256 exactly (FP32 arithmetic), (cos, sin)(k/128) from a table of
+// correctly rounded values built on the host, and cos x - 1, sin x from their
+// Taylor series (truncation below 5e-18 absolute).  Absolute error within a
+// few 2^-53 (tests bound it against the library sincos over every float in
+// [-pi, pi]), at a third of the library's FP64 instruction count; near the
+// zeros of cos and sin the relative error grows, which no formula here
+// depends on.  Angles beyond the table fall back to the library sincos.
+__device__ __forceinline__ void sincos_f64(const double2* __restrict__ trig, float t, double* s, double* c) {
+  const float kf = rintf(t * 128.0f);
+  if (!(fabsf(kf) <= (float)kTrigHalf)) {
+    sincos((double)t, s, c);
+    return;
+  }
+  const float xf = fmaf(kf, -0.0078125f, t);  // exact
+  const double x = (double)xf;
+  const double x2 = x * x;
+  const double cm1 = x2 * fma(x2, 1.0 / 24.0, -0.5);
+  const double sx = fma(x * x2, fma(x2, 1.0 / 120.0, -1.0 / 6.0), x);
+  const double2 cs = __ldg(&trig[(int)kf + kTrigHalf]);  // (cos, sin)(k/128)
+  *c = fma(cs.x, cm1, fma(-cs.y, sx, cs.x));
+  *s = fma(cs.y, cm1, fma(cs.x, sx, cs.y));
+}
+
 // Rows of A_i (Eq. eq:LSQPerCluster) in FP64: (cos t, sin t) or
 // (cos t cos e, sin t cos e, sin e).
 template <int DIM>
-__device__ __forceinline__ void row_f64(float az, float el, double a[3]) {
+__device__ __forceinline__ void row_f64(const double2* __restrict__ trig, float az, float el, double a[3]) {
   double s, c;
-  sincos((double)az, &s, &c);
+  sincos_f64(trig, az, &s, &c);
   if (DIM == 2) {
     a[0] = c;
     a[1] = s;
     a[2] = 0.0;
   } else {
     double se, ce;
-    sincos((double)el, &se, &ce);
+    sincos_f64(trig, el, &se, &ce);
     a[0] = c * ce;
     a[1] = s * ce;
     a[2] = se;

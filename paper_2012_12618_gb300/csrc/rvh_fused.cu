@@ -19,6 +19,9 @@ namespace rvh {
 
 constexpr int kThreads = 256;
 constexpr int kWarps = kThreads / 32;
+#ifndef RVH_MIN_BLOCKS
+#define RVH_MIN_BLOCKS 3
+#endif
 
 struct Smem {
   float4* rows;       // [nmax_smem]
@@ -50,6 +53,32 @@ __device__ __forceinline__ int block_max_int(int v, int* red) {
   int r = red[0];
 #pragma unroll
   for (int w = 1; w < kWarps; ++w) r = max(r, red[w]);
+  return r;
+}
+
+__device__ __forceinline__ int block_min_int(int v, int* red) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) v = min(v, __shfl_xor_sync(0xffffffffu, v, o));
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  __syncthreads();
+  if (lane == 0) red[warp] = v;
+  __syncthreads();
+  int r = red[0];
+#pragma unroll
+  for (int w = 1; w < kWarps; ++w) r = min(r, red[w]);
+  return r;
+}
+
+__device__ __forceinline__ unsigned long long block_sum_u64(unsigned long long v, unsigned long long* red) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  __syncthreads();
+  if (lane == 0) red[warp] = v;
+  __syncthreads();
+  unsigned long long r = 0;
+#pragma unroll
+  for (int w = 0; w < kWarps; ++w) r += red[w];
   return r;
 }
 
@@ -130,46 +159,11 @@ __device__ bool hyp_f64(const FrameDesc& a, int64_t o, int ci, int h, int N, dou
   int q[3];
   draw_minimal_set<DIM>(a.key, ci, h, N, q);
   double r0[3], r1[3], r2[3] = {0.0, 0.0, 0.0};
-  row_f64<DIM>(a.az[o + q[0]], DIM == 3 ? a.el[o + q[0]] : 0.0f, r0);
-  row_f64<DIM>(a.az[o + q[1]], DIM == 3 ? a.el[o + q[1]] : 0.0f, r1);
-  if (DIM == 3) row_f64<DIM>(a.az[o + q[2]], a.el[o + q[2]], r2);
+  row_f64<DIM>(a.trig, a.az[o + q[0]], DIM == 3 ? a.el[o + q[0]] : 0.0f, r0);
+  row_f64<DIM>(a.trig, a.az[o + q[1]], DIM == 3 ? a.el[o + q[1]] : 0.0f, r1);
+  if (DIM == 3) row_f64<DIM>(a.trig, a.az[o + q[2]], a.el[o + q[2]], r2);
   double w[3] = {(double)a.dop[o + q[0]], (double)a.dop[o + q[1]], DIM == 3 ? (double)a.dop[o + q[2]] : 0.0};
   return solve_f64<DIM>(r0, r1, r2, w, a.eps, v, nullptr);
-}
-
-// Exact count of trial (record hy, thresholds) by one warp: FP32 certainties plus
-// FP64 re-decision of the band points.
-template <int DIM>
-__device__ int exact_count_warp(const FrameDesc& a, const float4* __restrict__ rows, int64_t o, int ci,
-                                int h, int N, float4 hy, float tlo, unsigned long long* band_ctr) {
-  const int lane = threadIdx.x & 31;
-  int L = 0, B = 0;
-  for (int j = lane; j < N; j += 32) {
-    const float r = fabsf(resid_f32<DIM>(rows[j], hy.x, hy.y, hy.z));
-    if (r <= tlo) ++L;
-    else if (!(r > hy.w)) ++B;
-  }
-  L = warp_sum(L);
-  B = warp_sum(B);
-  if (B == 0) return L;
-  double v[3] = {0.0, 0.0, 0.0};
-  if (lane == 0) hyp_f64<DIM>(a, o, ci, h, N, v);
-#pragma unroll
-  for (int i = 0; i < 3; ++i) v[i] = __shfl_sync(0xffffffffu, v[i], 0);
-  int Lb = 0;
-  for (int j = lane; j < N; j += 32) {
-    const float4 p = rows[j];
-    const float r = fabsf(resid_f32<DIM>(p, hy.x, hy.y, hy.z));
-    if (!(r <= tlo) && !(r > hy.w)) {
-      double a64[3];
-      row_f64<DIM>(a.az[o + j], DIM == 3 ? a.el[o + j] : 0.0f, a64);
-      const double w = (double)(DIM == 2 ? p.z : p.w);
-      if (fabs(residual_f64<DIM>(a64, w, v)) <= a.tau) ++Lb;
-    }
-  }
-  Lb = warp_sum(Lb);
-  if (lane == 0) atomicAdd(band_ctr, (unsigned long long)B);
-  return L + Lb;
 }
 
 struct ClusterShared {
@@ -184,8 +178,56 @@ struct ClusterShared {
   int red_i[kWarps];
   float red_f[kWarps];
   double red_d[kWarps][10];
-  unsigned long long ctr[4];  // candidates, band points, fp64 hyps, pair evals
+  unsigned long long ctr[4];  // candidates, band points, fp64 hyps, reserved
+  unsigned long long clk[6];  // cycles per stage (thread 0's view of the CTA)
+  unsigned long long red_u[kWarps];
+  double cv64[3];             // FP64 velocity of the trial being counted (when it has band points)
+  double win_v64[3];          // FP64 velocity of the current winner (valid if win_has_v64)
+  int win_has_v64;
 };
+
+// Exact count of one trial by the whole CTA: FP32 certainties, then an FP64
+// re-decision of the points inside the trial's error band.  When there are
+// band points the trial's FP64 velocity is left in cs.cv64 and *band > 0.
+template <int DIM>
+__device__ int exact_count_block(const FrameDesc& a, const float4* __restrict__ rows, int64_t o, int ci,
+                                 int h, int N, float4 hy, float tlo, ClusterShared& cs, int* band) {
+  const int tid = threadIdx.x;
+  unsigned long long lb = 0;  // L in the low word, B in the high word
+  for (int j = tid; j < N; j += kThreads) {
+    const float r = fabsf(resid_f32<DIM>(rows[j], hy.x, hy.y, hy.z));
+    if (r <= tlo) lb += 1ull;
+    else if (!(r > hy.w)) lb += 1ull << 32;
+  }
+  lb = block_sum_u64(lb, cs.red_u);
+  const int L = (int)(lb & 0xFFFFFFFFull), B = (int)(lb >> 32);
+  *band = B;
+  if (B == 0) return L;
+  __syncthreads();
+  if (tid == 0) {
+    double v[3] = {0.0, 0.0, 0.0};
+    hyp_f64<DIM>(a, o, ci, h, N, v);
+    cs.cv64[0] = v[0];
+    cs.cv64[1] = v[1];
+    cs.cv64[2] = v[2];
+    cs.ctr[1] += (unsigned long long)B;
+  }
+  __syncthreads();
+  const double v[3] = {cs.cv64[0], cs.cv64[1], cs.cv64[2]};
+  unsigned long long lbin = 0;
+  for (int j = tid; j < N; j += kThreads) {
+    const float4 p = rows[j];
+    const float r = fabsf(resid_f32<DIM>(p, hy.x, hy.y, hy.z));
+    if (!(r <= tlo) && !(r > hy.w)) {
+      double a64[3];
+      row_f64<DIM>(a.trig, a.az[o + j], DIM == 3 ? a.el[o + j] : 0.0f, a64);
+      const double w = (double)(DIM == 2 ? p.z : p.w);
+      if (fabs(residual_f64<DIM>(a64, w, v)) <= a.tau) ++lbin;
+    }
+  }
+  lbin = block_sum_u64(lbin, cs.red_u);
+  return L + (int)lbin;
+}
 
 template <int DIM>
 __device__ void write_invalid(const FrameDesc& a, int ci, int st) {
@@ -215,6 +257,14 @@ __device__ void process_cluster(const FrameDesc& a, const Smem& S, ClusterShared
     return;
   }
   float4* rows = SMEM_ROWS ? S.rows : (a.rows_g + o);
+  long long t_stage = clock64();
+  auto stage_done = [&](int k) {
+    if (tid == 0) {
+      const long long t = clock64();
+      cs.clk[k] += (unsigned long long)(t - t_stage);
+      t_stage = t;
+    }
+  };
 
   // a1: FP32 rows of the cluster (sincosf; FP64 fallback outside |t| <= pi)
   float wm = 0.0f;
@@ -231,6 +281,7 @@ __device__ void process_cluster(const FrameDesc& a, const Smem& S, ClusterShared
   __syncthreads();
   const float wmax = cs.wmax;
   unsigned long long n_fp64 = 0, n_cand = 0;
+  stage_done(0);
 
   for (int hc0 = 0; hc0 < a.H; hc0 += hchunk) {
     const int nh = min(hchunk, a.H - hc0);
@@ -262,45 +313,68 @@ __device__ void process_cluster(const FrameDesc& a, const Smem& S, ClusterShared
       S.U[hl] = hy.kind == kHypRejected ? -1 : (hy.kind == kHypExactOnly ? N : 0);
     }
     __syncthreads();
+    stage_done(1);
 
     // a4: scoring pass (the hot loop)
     phase_a_dispatch<DIM>(pw, hpl, rows, N, S, nh);
     __syncthreads();
+    stage_done(2);
 
-    // a5 + a6: exact counts of the trials whose upper bound reaches the lead
+    // a5 + a6: exact counts, in index order, of the trials whose upper bound
+    // can still win.  C_h <= U_h <= Umax, so the first trial (lowest index)
+    // whose exact count reaches Umax is the winner of the chunk; trials of
+    // earlier chunks have lower indices, so this chunk must beat the lead
+    // strictly.
     int um = -1;
     for (int hl = tid; hl < nh; hl += kThreads) um = max(um, S.U[hl]);
     const int Umax = block_max_int(um, cs.red_i);  // syncs after phase A's writes
     const int lead = (int)(cs.best >> 32) - 1;     // best exact count so far (-1 none)
-    // trials of earlier chunks have lower indices, so a later trial must beat
-    // the lead strictly
     if (Umax >= 0 && Umax > lead) {
-      for (int round = 0; round < 2; ++round) {
-        if (tid == 0) cs.ncand = 0;
-        __syncthreads();
-        const int cur = (int)(cs.best >> 32) - 1;
-        for (int hl = tid; hl < nh; hl += kThreads) {
-          const int u = S.U[hl];
-          const bool pick = round == 0 ? (u == Umax) : (u >= cur && u >= 0 && u < Umax);
-          if (pick) S.cand[atomicAdd(&cs.ncand, 1)] = hl;
+      for (int pass = 0; pass < 2; ++pass) {
+        int prev = -1;
+        bool done = false;
+        for (;;) {
+          const int cur = (int)(cs.best >> 32) - 1;
+          int c = 0x7fffffff;
+          for (int hl = tid; hl < nh; hl += kThreads) {
+            const int u = S.U[hl];
+            const bool pick = pass == 0 ? (u == Umax) : (u >= cur && u >= 0 && u < Umax);
+            if (hl > prev && pick) c = min(c, hl);
+          }
+          c = block_min_int(c, cs.red_i);
+          if (c == 0x7fffffff) break;
+          const float4 hy = S.hyp[c];
+          const float htlo = S.tlo[c];
+          int B = 0;
+          const int C = exact_count_block<DIM>(a, rows, o, ci, hc0 + c, N, hy, htlo, cs, &B);
+          ++n_cand;
+          if (tid == 0) {
+            const unsigned long long k = best_key(C, hc0 + c);
+            if (k > cs.best) {
+              cs.best = k;
+              cs.win = hy;
+              cs.win_tlo = htlo;
+              cs.win_has_v64 = B > 0;
+              cs.win_v64[0] = cs.cv64[0];
+              cs.win_v64[1] = cs.cv64[1];
+              cs.win_v64[2] = cs.cv64[2];
+            }
+          }
+          __syncthreads();
+          if (pass == 0 && C == Umax) {
+            done = true;
+            break;
+          }
+          prev = c;
         }
-        __syncthreads();
-        const int nc = cs.ncand;
-        n_cand += (tid == 0) ? (unsigned long long)nc : 0ull;
-        for (int c = tid >> 5; c < nc; c += kWarps) {
-          const int hl = S.cand[c];
-          const int C = exact_count_warp<DIM>(a, rows, o, ci, hc0 + hl, N, S.hyp[hl], S.tlo[hl], &cs.ctr[1]);
-          if ((tid & 31) == 0) atomicMax(&cs.best, best_key(C, hc0 + hl));
-        }
-        __syncthreads();
+        if (done) break;
       }
     }
     __syncthreads();
+    stage_done(3);
   }
 
-  if (tid == 0) {
-    atomicAdd(&cs.ctr[0], n_cand);
-  }
+  if (tid == 0) cs.ctr[0] += n_cand;
   if (n_fp64) atomicAdd(&cs.ctr[2], n_fp64);
 
   const unsigned long long key = cs.best;
@@ -312,29 +386,12 @@ __device__ void process_cluster(const FrameDesc& a, const Smem& S, ClusterShared
   }
   const int hstar = (int)(0xFFFFFFFFu - (uint32_t)(key & 0xFFFFFFFFull));
 
-  // a7 + a8: winner in FP64, its mask, and the normal equations over its inliers
-  if (tid == 0) {
-    int q[3];
-    draw_minimal_set<DIM>(a.key, ci, hstar, N, q);
-    const float4 p0 = rows[q[0]], p1 = rows[q[1]];
-    const float4 p2 = DIM == 3 ? rows[q[2]] : p0;
-    Hyp32 hy = hyp_f32<DIM>(p0, p1, p2, wmax, 0.0f, 0.0f, a.tau32);
-    if (hy.kind != kHypNormal) {
-      hy.thi = __int_as_float(0x7f800000);
-      hy.tlo = -1.0f;
-    }
-    cs.win = make_float4(hy.nx, hy.ny, hy.nz, hy.thi);
-    cs.win_tlo = hy.tlo;
-    double v[3] = {0.0, 0.0, 0.0};
-    hyp_f64<DIM>(a, o, ci, hstar, N, v);
-    cs.v64[0] = v[0];
-    cs.v64[1] = v[1];
-    cs.v64[2] = v[2];
-  }
-  __syncthreads();
+  // a7 + a8: the winner's mask (FP32 certainties; FP64 for its band points,
+  // whose FP64 velocity was computed when it was counted) and the normal
+  // equations over its inliers.
   const float4 win = cs.win;
   const float wtlo = cs.win_tlo;
-  const double v64[3] = {cs.v64[0], cs.v64[1], cs.v64[2]};
+  const double v64[3] = {cs.win_v64[0], cs.win_v64[1], cs.win_v64[2]};
   constexpr int NS = DIM == 2 ? 5 : 9;
   double sums[NS];
 #pragma unroll
@@ -347,7 +404,7 @@ __device__ void process_cluster(const FrameDesc& a, const Smem& S, ClusterShared
     const bool band = !in && !(r > win.w);
     if (in || band) {
       double a64[3];
-      row_f64<DIM>(a.az[o + j], DIM == 3 ? a.el[o + j] : 0.0f, a64);
+      row_f64<DIM>(a.trig, a.az[o + j], DIM == 3 ? a.el[o + j] : 0.0f, a64);
       const double w = (double)(DIM == 2 ? p.z : p.w);
       if (band) in = fabs(residual_f64<DIM>(a64, w, v64)) <= a.tau;
       if (in) {
@@ -394,6 +451,9 @@ __device__ void process_cluster(const FrameDesc& a, const Smem& S, ClusterShared
       for (int i = 0; i < NS; ++i) t[i] += cs.red_d[w][i];
     }
     double vout[3] = {v64[0], v64[1], v64[2]};
+    auto minimal_velocity = [&]() {
+      if (!cs.win_has_v64) hyp_f64<DIM>(a, o, ci, hstar, N, vout);
+    };
     int st = 0;
     if (DIM == 2) {
       const double tr = t[0] + t[2];
@@ -408,6 +468,7 @@ __device__ void process_cluster(const FrameDesc& a, const Smem& S, ClusterShared
         vout[2] = 0.0;
       } else {
         st |= RVH_STATUS_LSQ_FALLBACK;
+        minimal_velocity();
       }
     } else {
       const double tr = t[0] + t[3] + t[5];
@@ -423,6 +484,7 @@ __device__ void process_cluster(const FrameDesc& a, const Smem& S, ClusterShared
         vout[2] = vs[2];
       } else {
         st |= RVH_STATUS_LSQ_FALLBACK;
+        minimal_velocity();
       }
     }
     a.vx[ci] = vout[0];
@@ -434,10 +496,11 @@ __device__ void process_cluster(const FrameDesc& a, const Smem& S, ClusterShared
     a.status[ci] = st;
   }
   __syncthreads();
+  stage_done(4);
 }
 
 template <int DIM>
-__global__ void __launch_bounds__(kThreads, 2) fused_kernel(FusedArgs a) {
+__global__ void __launch_bounds__(kThreads, RVH_MIN_BLOCKS) fused_kernel(FusedArgs a) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   __shared__ ClusterShared cs;
   __shared__ int s_item;
@@ -456,6 +519,8 @@ __global__ void __launch_bounds__(kThreads, 2) fused_kernel(FusedArgs a) {
   S.kind = reinterpret_cast<int8_t*>(p);
 
   if (threadIdx.x < 4) cs.ctr[threadIdx.x] = 0ull;
+  if (threadIdx.x < 6) cs.clk[threadIdx.x] = 0ull;
+  const long long t_kernel = clock64();
   for (;;) {
     __syncthreads();
     if (threadIdx.x == 0) s_item = atomicAdd(a.work_counter, 1);
@@ -473,10 +538,18 @@ __global__ void __launch_bounds__(kThreads, 2) fused_kernel(FusedArgs a) {
     }
   }
   __syncthreads();
+  if (threadIdx.x == 0) {
+    unsigned long long staged = 0;
+    for (int k = 0; k < 5; ++k) staged += cs.clk[k];
+    const unsigned long long total = (unsigned long long)(clock64() - t_kernel);
+    cs.clk[5] = total > staged ? total - staged : 0ull;
+  }
+  __syncthreads();
   if (threadIdx.x < 4 && a.stats) {
     unsigned long long v = cs.ctr[threadIdx.x];
     if (v) atomicAdd(&a.stats[threadIdx.x], v);
   }
+  if (threadIdx.x < 6 && a.stats) atomicAdd(&a.stats[4 + threadIdx.x], cs.clk[threadIdx.x]);
 }
 
 // Orders the batch's (frame, cluster) items by decreasing floor(log2(N * H))

@@ -7,6 +7,11 @@
 
 namespace rvh {
 
+// Table of (cos, sin)(k/128) for the FP64 rows: k = -kTrigHalf..kTrigHalf
+// covers |t| <= 3.28 rad (beyond pi).
+constexpr int kTrigHalf = 420;
+constexpr int kTrigSize = 2 * kTrigHalf + 1;
+
 // tau rounded outward to FP32: lo = largest float <= tau, hi = smallest float >= tau.
 struct TauPair {
   float lo, hi;
@@ -22,6 +27,7 @@ struct FrameDesc {
   int32_t H;
   int64_t n_points;
   float4* rows_g;            // [n_points] FP32 rows of clusters larger than nmax_smem
+  const double2* trig;       // (cos, sin)(k/128), k = -420..420
   double tau;
   double eps;
   TauPair tau32;
@@ -46,7 +52,7 @@ struct FusedArgs {
   int n_items;               // sum of n_clusters over the frames
   int2* worklist;            // [n_items] (frame, cluster), written by the worklist kernel
   int* work_counter;
-  unsigned long long* stats;  // [4]: candidates, band points, fp64 trials, reserved
+  unsigned long long* stats;  // [4 + 6]: candidates, band points, fp64 trials, reserved, phase cycles
   int nmax_smem;
   int hchunk;
   int pw, hpl;
@@ -65,6 +71,7 @@ struct BaselineArgs {
   const int32_t* offsets;
   int64_t n_points;
   double* rows64_g;          // [n_points * 4] FP64 rows of clusters larger than nmax_smem
+  const double2* trig;
   int H;
   double tau;
   double eps;

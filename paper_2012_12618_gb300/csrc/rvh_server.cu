@@ -384,7 +384,7 @@ void Server::loop() {
     // scratch for the launch: worklist + counter + stats
     int n_items = 0;
     for (uint64_t id : take) n_items += reqs[id]->frame.n_clusters;
-    const size_t sbytes = gran(sizeof(int2) * (size_t)std::max(n_items, 1)) + 256;
+    const size_t sbytes = gran(sizeof(int2) * (size_t)std::max(n_items, 1)) + 256;  // counter + stats[10]
     size_t soff = 0;
     if (!dev_arena.alloc(sbytes, &soff)) {
       // pool exhausted by admitted frames: retry once a step completes
@@ -399,7 +399,7 @@ void Server::loop() {
     for (uint64_t id : take) {
       Req& q = *reqs[id];
       char* b = (char*)pool + q.dev_off;
-      fill_desc(a.f[nf], q.frame, q.params, q.frame.azimuth, q.frame.elevation, q.frame.doppler,
+      fill_desc(ctx, a.f[nf], q.frame, q.params, q.frame.azimuth, q.frame.elevation, q.frame.doppler,
                 q.frame.cluster_offsets, (float4*)b, q.dev);
       cudaStreamWaitEvent(slot->stream, q.copied, 0);
       ++nf;
@@ -408,7 +408,7 @@ void Server::loop() {
     a.n_items = n_items;
     a.worklist = (int2*)sb;
     a.work_counter = (int*)(sb + gran(sizeof(int2) * (size_t)std::max(n_items, 1)));
-    a.stats = (unsigned long long*)(sb + gran(sizeof(int2) * (size_t)std::max(n_items, 1)) + 64);
+    a.stats = nullptr;
     int Hmax = 1;
     for (int i = 0; i < nf; ++i) Hmax = std::max(Hmax, a.f[i].H);
     choose_schedule(ctx, Hmax, &a.pw, &a.hpl);

@@ -49,7 +49,7 @@ class rvh_stats(ctypes.Structure):
     _fields_ = [("hypotheses", ctypes.c_int64), ("pair_evals", ctypes.c_int64), ("candidates", ctypes.c_int64),
                 ("band_points", ctypes.c_int64), ("fp64_hypotheses", ctypes.c_int64),
                 ("kernel_ms", ctypes.c_float), ("grid", ctypes.c_int32), ("points_per_warp", ctypes.c_int32),
-                ("hyps_per_lane", ctypes.c_int32)]
+                ("hyps_per_lane", ctypes.c_int32), ("phase_cycles", ctypes.c_int64 * 6)]
 
 
 # exported symbols and their ctypes signatures (restype, argtypes)
@@ -161,6 +161,22 @@ def make_result(out: dict) -> rvh_result:
     return rvh_result(ptr(out["vx"]), ptr(out["vy"]), ptr(out.get("vz")), ptr(out["heading"]),
                       ptr(out["inlier_count"]), ptr(out["best_hypothesis"]), ptr(out["status"]),
                       ptr(out["inlier_mask"]))
+
+
+def alloc_outputs(n_clusters: int, n_points: int, device="cuda") -> dict:
+    """Result buffers as torch tensors on `device` ("cpu" gives host memory)."""
+    import torch
+    kw = dict(device=device)
+    return {
+        "vx": torch.empty(n_clusters, dtype=torch.float64, **kw),
+        "vy": torch.empty(n_clusters, dtype=torch.float64, **kw),
+        "vz": torch.empty(n_clusters, dtype=torch.float64, **kw),
+        "heading": torch.empty(n_clusters, dtype=torch.float64, **kw),
+        "inlier_count": torch.empty(n_clusters, dtype=torch.int32, **kw),
+        "best_hypothesis": torch.empty(n_clusters, dtype=torch.int32, **kw),
+        "status": torch.empty(n_clusters, dtype=torch.int32, **kw),
+        "inlier_mask": torch.empty(max(n_points, 1), dtype=torch.uint8, **kw),
+    }
 
 
 class Context:

@@ -26,9 +26,12 @@ def ctx():
     c.close()
 
 
-def _check(rep):
+def _check(rep, ties_allowed=False):
     assert not rep["mismatch"], rep["mismatch"][:20]
-    assert rep["fragile"] <= max(1, rep["clusters"] // 1000), rep
+    # rounding ties (oracle-flagged fragile clusters that disagree) stay rare,
+    # except with tau = 0, where every decision is decided by rounding alone
+    if not ties_allowed:
+        assert len({t[0] for t in rep["ties"]}) <= max(1, rep["clusters"] // 100), rep["ties"][:20]
 
 
 def _run_pair(ctx, f, w, *, H=None, seed=None, subset=None, baseline=False, tau=None):
@@ -123,7 +126,7 @@ def test_edge_cases(ctx):
     for H, tau in ((1, 0.1), (1500, 0.1), (64, 0.0), (300, 5.0)):
         g = G.run_rvh(ctx, az, dop, off, H=H, tau=tau, seed=11)
         o = G.run_oracle(az, dop, off, H=H, tau=tau, seed=11)
-        _check(G.compare(g, o, off))
+        _check(G.compare(g, o, off), ties_allowed=(tau == 0.0))
     st = g["status"]
     assert st[0] & 1 and st[1] & 1 and st[2] == 0 or st[2] & 4
 
