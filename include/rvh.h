@@ -136,6 +136,32 @@ int rvh_estimate(rvh_ctx* ctx, const rvh_frame* frame, const rvh_params* params,
 int rvh_estimate_baseline(rvh_ctx* ctx, const rvh_frame* frame, const rvh_params* params,
                           rvh_result* result, void* stream);
 
+/* ---- allocation-free estimate ----------------------------------------------------- */
+/* The paper has no counterpart to this entry point.  It is rvh_estimate for
+ * callers that may not allocate device memory once they are running: for
+ * example real-time perception stacks that forbid any allocation after
+ * start-up, or plugins whose host framework owns all device memory.  It needs
+ * no context and calls no cudaMalloc, cudaFree or other allocating routine.
+ *
+ * Its scratch (work list, work counter, FP32 rows of large clusters) and the
+ * FP64 row table live in file-scope device arrays of fixed size:
+ * RVH_NOALLOC_MAX_CLUSTERS clusters and RVH_NOALLOC_MAX_POINTS points, about
+ * 32.5 MiB, which every GPU that loads the library holds until the process
+ * exits.  Larger frames are rejected with RVH_EINVAL and a message.
+ *
+ * The first call on a device sets that device up (device addresses of the
+ * arrays, the row table upload, the kernels' shared-memory opt-in), with the
+ * device current; make this first call before any stream capture.
+ * All inputs and outputs must be device memory; the call is stream-ordered on
+ * `stream` (a cudaStream_t, NULL = the legacy default stream) and returns once
+ * the work is enqueued.  Every call shares the arrays, which keep the last
+ * call's contents (each call resets the work counter it needs zeroed), so
+ * calls that overlap on the GPU race: order them on one stream or with events.
+ * Results equal rvh_estimate's. */
+#define RVH_NOALLOC_MAX_POINTS 2097152
+#define RVH_NOALLOC_MAX_CLUSTERS 65536
+int rvh_estimate_noalloc(const rvh_frame* frame, const rvh_params* params, rvh_result* result, void* stream);
+
 /* ---- streaming (serving) -------------------------------------------------------- */
 /* Queues a frame for continuous batching.  Host inputs are copied into the
  * context's device pool before the call returns; device inputs must stay

@@ -26,6 +26,9 @@ RVH_STATUS_ALL_DEGENERATE = 2
 RVH_STATUS_LSQ_FALLBACK = 4
 RVH_STATUS_BAD_OFFSETS = 8
 
+RVH_NOALLOC_MAX_POINTS = 2097152
+RVH_NOALLOC_MAX_CLUSTERS = 65536
+
 
 class rvh_frame(ctypes.Structure):
     _fields_ = [("azimuth", ctypes.c_void_p), ("elevation", ctypes.c_void_p), ("doppler", ctypes.c_void_p),
@@ -61,6 +64,8 @@ SIGNATURES = {
                                     ctypes.POINTER(rvh_result), _P]),
     "rvh_estimate_baseline": (ctypes.c_int, [_P, ctypes.POINTER(rvh_frame), ctypes.POINTER(rvh_params),
                                              ctypes.POINTER(rvh_result), _P]),
+    "rvh_estimate_noalloc": (ctypes.c_int, [ctypes.POINTER(rvh_frame), ctypes.POINTER(rvh_params),
+                                            ctypes.POINTER(rvh_result), _P]),
     "rvh_submit": (ctypes.c_int, [_P, ctypes.POINTER(rvh_frame), ctypes.POINTER(rvh_params),
                                   ctypes.POINTER(rvh_result), ctypes.POINTER(ctypes.c_uint64)]),
     "rvh_poll": (ctypes.c_int, [_P, ctypes.c_uint64]),
@@ -107,6 +112,10 @@ def rvh_estimate(ctx, frame, params, result, stream=None) -> int:
 def rvh_estimate_baseline(ctx, frame, params, result, stream=None) -> int:
     return load().rvh_estimate_baseline(ctx, ctypes.byref(frame), ctypes.byref(params), ctypes.byref(result),
                                         stream)
+
+
+def rvh_estimate_noalloc(frame, params, result, stream=None) -> int:
+    return load().rvh_estimate_noalloc(ctypes.byref(frame), ctypes.byref(params), ctypes.byref(result), stream)
 
 
 def rvh_submit(ctx, frame, params, result, ticket) -> int:

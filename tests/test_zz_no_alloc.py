@@ -1,0 +1,66 @@
+"""rvh_estimate_noalloc against rvh_estimate (GPU).
+
+Some callers may not allocate device memory once they are running (real-time
+stacks that forbid allocation after start-up, plugins whose framework owns all
+device memory); rvh_estimate_noalloc serves them from fixed file-scope device
+arrays.  This file is named to be collected last.  The test runs the new entry
+point twice in a row through the C ABI on the same frame and checks each
+result against the context-based rvh_estimate: masks, counts, winners and
+status bit-exact, velocities and heading within 1e-6.  It passes on its own in
+a fresh process and after the other tests.
+"""
+import ctypes
+
+import numpy as np
+import pytest
+
+from paper_2012_12618_gb300 import rvh, synth
+
+pytestmark = pytest.mark.gpu
+
+
+def _to_np(outs, n_points):
+    out = {k: v.cpu().numpy() for k, v in outs.items()}
+    out["inlier_mask"] = out["inlier_mask"][:n_points]
+    return out
+
+
+def test_noalloc_matches_estimate_twice():
+    torch = pytest.importorskip("torch")
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    w = synth.WORKLOADS["dense2d"]
+    f = synth.make_frame(w, n_clusters=384, gen_seed=404)
+    dev = torch.device("cuda", 0)
+    az = torch.from_numpy(f.azimuth).to(dev)
+    dop = torch.from_numpy(f.doppler).to(dev)
+    off = torch.from_numpy(f.offsets).to(dev)
+    frame = rvh.make_frame(az, dop, off)
+    params = rvh.make_params(2, w.num_hypotheses, w.tau, 7)
+
+    ctx = rvh.Context(0)
+    try:
+        ref_outs = rvh.alloc_outputs(f.n_clusters, f.n_points, dev)
+        assert rvh.rvh_estimate(ctx.handle, frame, params, rvh.make_result(ref_outs), None) == rvh.RVH_OK
+        torch.cuda.synchronize()
+        ref = _to_np(ref_outs, f.n_points)
+    finally:
+        ctx.close()
+
+    for call in range(2):
+        outs = rvh.alloc_outputs(f.n_clusters, f.n_points, dev)
+        for t in outs.values():
+            t.fill_(0x5A if t.dtype == torch.uint8 else 7)
+        rc = rvh.rvh_estimate_noalloc(frame, params, rvh.make_result(outs), None)
+        assert rc == rvh.RVH_OK, rvh.rvh_last_error(None)
+        torch.cuda.synchronize()
+        got = _to_np(outs, f.n_points)
+        for k in ("inlier_mask", "inlier_count", "best_hypothesis", "status"):
+            assert np.array_equal(got[k], ref[k]), (call, k)
+        for k in ("vx", "vy", "vz", "heading"):
+            assert np.allclose(got[k], ref[k], rtol=0, atol=1e-6, equal_nan=True), (call, k)
+
+    # frames beyond the fixed limits are refused before any launch
+    big = rvh.rvh_frame(None, None, None, None, 1, rvh.RVH_NOALLOC_MAX_POINTS + 1)
+    assert rvh.rvh_estimate_noalloc(big, params, rvh.make_result(outs), None) == rvh.RVH_EINVAL
+    assert "limits" in rvh.rvh_last_error(None)
