@@ -152,6 +152,8 @@ def main():
     ap.add_argument("--impl", default="rvh", choices=["rvh", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-gpu-baseline", action="store_true")
+    ap.add_argument("--serving-seconds", type=float, default=3.0,
+                    help="measured seconds of the 64-radar serving load (0 skips it)")
     args = ap.parse_args()
     if args.impl == "reference":
         return reference_arm(args)
@@ -294,6 +296,18 @@ def main():
                     "one launch per cluster", "ms_per_step": bms, "fused_speedup": value / ws / (nc / (bms * 1e-3)),
                     "identical_masks_and_winners": same}
 
+    # ---- serving: 64 radars x 20 frames/s (Poisson), mixed 2D/3D, continuous batching
+    serve = None
+    if args.serving_seconds > 0 and rank == 0:
+        from paper_2012_12618_gb300 import serving
+        spec = synth.ServingSpec(duration_s=args.serving_seconds, warmup_s=0.5)
+        sres = serving.run_load(ctx, spec, dev)
+        serve = sres.summary()
+        serve["config"] = (f"{spec.n_radars} radars x {spec.fps:g} frames/s Poisson, clusters "
+                           f"{spec.clusters_lo}..{spec.clusters_hi} per frame, sizes log-uniform "
+                           f"{spec.size_lo}..{spec.size_hi}; radars 0-31 2D H=256, 32-63 3D H=2048; "
+                           f"{spec.duration_s:g} s measured after {spec.warmup_s:g} s")
+
     # ---- the FP64 oracle on this host (rank 0, N = 1 only)
     cpu = None
     if rank == 0 and ws == 1 and not args.no_cpu_baseline:
@@ -320,6 +334,7 @@ def main():
             "roofline": roofline,
             "cpu_baseline": cpu,
             "gpu_baseline": gpu_base,
+            "serving": serve,
             "e2e": e2e,
             "clocks": clocks,
             "gpu_launches": 2 * args.steps,

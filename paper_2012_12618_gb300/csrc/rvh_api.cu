@@ -116,7 +116,7 @@ struct rvh_ctx {
   bool have_launch = false;
   rvh_stats last{};
   int pw_fixed = 0, hpl_fixed = 0;
-  int nmax_smem = 2048;
+  int nmax_smem = 1536;
   int hchunk = 1024;
   int occ[4] = {0, 0, 0, 0};
   std::mutex mu;  // serialises rvh_estimate calls on this context

@@ -20,7 +20,7 @@ namespace rvh {
 constexpr int kThreads = 256;
 constexpr int kWarps = kThreads / 32;
 #ifndef RVH_MIN_BLOCKS
-#define RVH_MIN_BLOCKS 3
+#define RVH_MIN_BLOCKS 4
 #endif
 
 struct Smem {

@@ -26,6 +26,10 @@ namespace rvh {
 namespace {
 
 constexpr size_t kGran = 256;
+// work-list capacity of one step (clusters over all frames of a launch); each
+// step slot owns this scratch for the server's lifetime, so admitted frames
+// can never starve a launch of its scratch
+constexpr int kStepItems = 1 << 19;
 size_t gran(size_t x) { return (x + kGran - 1) & ~(kGran - 1); }
 
 // First-fit arena allocator over [0, size).
@@ -171,6 +175,11 @@ int server_create(rvh_ctx* ctx, Server** out) {
   for (auto& st : s->steps) {
     cudaStreamCreateWithFlags(&st.stream, cudaStreamNonBlocking);
     cudaEventCreateWithFlags(&st.done, cudaEventDisableTiming);
+    st.scratch_bytes = gran(sizeof(int2) * (size_t)kStepItems) + 256;
+    if (!s->dev_arena.alloc(st.scratch_bytes, &st.scratch_off)) {
+      server_destroy(s);
+      return set_error(RVH_ENOMEM, "serving pool too small for the step scratch");
+    }
   }
   s->thread = std::thread([s] { s->loop(); });
   *out = s;
@@ -204,6 +213,7 @@ int server_submit(Server* s, const rvh_frame* f, const rvh_params* p, rvh_result
   const int64_t np = f->n_points;
   const int32_t nc = f->n_clusters;
   const bool dim3 = p->model_dim == 3;
+  if (nc > kStepItems) return set_error(RVH_EINVAL, "frame has more clusters than a serving step holds");
   if (nc > 0 && !device_ptr(f->cluster_offsets)) {
     int rc = validate_host_offsets(f->cluster_offsets, nc, np);
     if (rc) return rc;
@@ -241,7 +251,8 @@ int server_submit(Server* s, const rvh_frame* f, const rvh_params* p, rvh_result
   }
   {
     std::lock_guard<std::mutex> lk(s->mu);
-    if (off > s->dev_arena.size() || pin > s->pin_arena.size())
+    const size_t usable = s->dev_arena.size() - s->steps.size() * s->steps[0].scratch_bytes;
+    if (off > usable || pin > s->pin_arena.size())
       return set_error(RVH_ENOMEM, "frame larger than the serving pool");
     if (!s->dev_arena.alloc(off, &q->dev_off)) return set_error(RVH_EAGAIN, "device pool full");
     if (pin && !s->pin_arena.alloc(pin, &q->pin_off)) {
@@ -317,8 +328,6 @@ int Server::finalize_step(Step& st) {
     q.copied = nullptr;
     q.state = 2;
   }
-  if (st.scratch_bytes) dev_arena.release(st.scratch_off, st.scratch_bytes);
-  st.scratch_bytes = 0;
   st.reqs.clear();
   st.busy = false;
   return RVH_OK;
@@ -364,12 +373,17 @@ void Server::loop() {
     }
     // iteration-level batch: everything queued now, grouped by model dimension
     std::vector<uint64_t> batch[2];
+    int items[2] = {0, 0};
     std::deque<uint64_t> rest;
     for (uint64_t id : queue) {
       Req& q = *reqs[id];
-      auto& b = batch[q.params.model_dim == 3];
-      if ((int)b.size() < kMaxBatchFrames) b.push_back(id);
-      else rest.push_back(id);
+      const int d = q.params.model_dim == 3;
+      if ((int)batch[d].size() < kMaxBatchFrames && items[d] + q.frame.n_clusters <= kStepItems) {
+        batch[d].push_back(id);
+        items[d] += q.frame.n_clusters;
+      } else {
+        rest.push_back(id);
+      }
     }
     // one dimension per step slot; the other waits for the next free slot
     int dimsel = batch[0].empty() ? 1 : 0;
@@ -381,18 +395,10 @@ void Server::loop() {
     for (uint64_t id : batch[1 - dimsel]) rest.push_front(id);
     std::sort(rest.begin(), rest.end());
     queue.assign(rest.begin(), rest.end());
-    // scratch for the launch: worklist + counter + stats
+    // the slot's own scratch: worklist + counter
     int n_items = 0;
     for (uint64_t id : take) n_items += reqs[id]->frame.n_clusters;
-    const size_t sbytes = gran(sizeof(int2) * (size_t)std::max(n_items, 1)) + 256;  // counter + stats[10]
-    size_t soff = 0;
-    if (!dev_arena.alloc(sbytes, &soff)) {
-      // pool exhausted by admitted frames: retry once a step completes
-      for (uint64_t id : take) queue.push_front(id);
-      cv.wait_for(lk, std::chrono::microseconds(50));
-      continue;
-    }
-    char* sb = (char*)pool + soff;
+    char* sb = (char*)pool + slot->scratch_off;
     FusedArgs a;
     memset(&a, 0, sizeof(a));
     int nf = 0;
@@ -407,7 +413,7 @@ void Server::loop() {
     a.n_frames = nf;
     a.n_items = n_items;
     a.worklist = (int2*)sb;
-    a.work_counter = (int*)(sb + gran(sizeof(int2) * (size_t)std::max(n_items, 1)));
+    a.work_counter = (int*)(sb + gran(sizeof(int2) * (size_t)kStepItems));
     a.stats = nullptr;
     int Hmax = 1;
     for (int i = 0; i < nf; ++i) Hmax = std::max(Hmax, a.f[i].H);
@@ -431,8 +437,6 @@ void Server::loop() {
     cudaEventRecord(slot->done, slot->stream);
     slot->busy = true;
     slot->reqs = take;
-    slot->scratch_off = soff;
-    slot->scratch_bytes = sbytes;
   }
 }
 

@@ -1,0 +1,154 @@
+"""Serving: rvh_submit / rvh_poll / rvh_wait with continuous batching (GPU).
+
+The central property: a frame's result does not depend on which other frames
+share its batch or step -- it equals the result of rvh_estimate on the frame
+alone (bit-exact masks, counts, winners and status; identical velocities).
+"""
+import ctypes
+
+import numpy as np
+import pytest
+
+from paper_2012_12618_gb300 import rvh, serving, synth
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def torch():
+    t = pytest.importorskip("torch")
+    if not t.cuda.is_available():
+        pytest.skip("no CUDA device")
+    return t
+
+
+def _frames():
+    spec = synth.ServingSpec(clusters_lo=20, clusters_hi=160)
+    out = []
+    for radar, k in ((0, 0), (40, 0), (1, 3), (33, 1), (2, 5), (50, 2), (3, 1)):
+        f, w = synth.serving_frame(spec, radar, k)
+        out.append((f, w, synth.radar_frame_seed(radar, k)))
+    return out
+
+
+def _np(outs, n_points):
+    d = {k: v.cpu().numpy().copy() for k, v in outs.items()}
+    d["inlier_mask"] = d["inlier_mask"][:n_points]
+    return d
+
+
+def _same(a, b):
+    for k in ("inlier_mask", "inlier_count", "best_hypothesis", "status", "vx", "vy", "vz", "heading"):
+        assert np.array_equal(a[k], b[k], equal_nan=True), k
+
+
+def test_results_same_alone_and_in_the_mix(torch):
+    dev = torch.device("cuda", 0)
+    frames = _frames()
+    ctx = rvh.Context(0)
+    try:
+        inputs, alone = [], []
+        for f, w, seed in frames:
+            t = [torch.from_numpy(x).to(dev) if x is not None else None
+                 for x in (f.azimuth, f.elevation, f.doppler, f.offsets)]
+            frame = rvh.make_frame(t[0], t[2], t[3], t[1])
+            params = rvh.make_params(w.model_dim, w.num_hypotheses, w.tau, seed)
+            outs = rvh.alloc_outputs(f.n_clusters, f.n_points, dev)
+            ctx.check(rvh.rvh_estimate(ctx.handle, frame, params, rvh.make_result(outs), None), "estimate")
+            torch.cuda.synchronize()
+            alone.append(_np(outs, f.n_points))
+            inputs.append((t, frame, params))
+        for order in (list(range(len(frames))), list(reversed(range(len(frames))))):
+            tickets, results = [], []
+            for i in order:
+                f, w, seed = frames[i]
+                # alternate device outputs and host outputs, device inputs and host inputs
+                if i % 2:
+                    outs = rvh.alloc_outputs(f.n_clusters, f.n_points, "cpu")
+                    frame = rvh.make_frame(f.azimuth, f.doppler, f.offsets, f.elevation)
+                else:
+                    outs = rvh.alloc_outputs(f.n_clusters, f.n_points, dev)
+                    frame = inputs[i][1]
+                tk = ctypes.c_uint64(0)
+                ctx.check(rvh.rvh_submit(ctx.handle, frame, inputs[i][2], rvh.make_result(outs), tk), "submit")
+                tickets.append((i, tk.value, outs, frame))
+            for i, tk, outs, _ in tickets:
+                assert rvh.rvh_wait(ctx.handle, tk, 30_000_000) == rvh.RVH_OK, rvh.rvh_last_error(None)
+                torch.cuda.synchronize()
+                _same(_np(outs, frames[i][0].n_points), alone[i])
+    finally:
+        ctx.close()
+
+
+def test_poll_semantics(torch):
+    dev = torch.device("cuda", 0)
+    f, w, seed = _frames()[0]
+    ctx = rvh.Context(0)
+    try:
+        assert rvh.rvh_poll(ctx.handle, 12345) == rvh.RVH_EINVAL
+        outs = rvh.alloc_outputs(f.n_clusters, f.n_points, dev)
+        frame = rvh.make_frame(f.azimuth, f.doppler, f.offsets)
+        params = rvh.make_params(2, w.num_hypotheses, w.tau, seed)
+        tk = ctypes.c_uint64(0)
+        ctx.check(rvh.rvh_submit(ctx.handle, frame, params, rvh.make_result(outs), tk), "submit")
+        rc = rvh.rvh_wait(ctx.handle, tk.value, 0)
+        assert rc in (rvh.RVH_OK, rvh.RVH_ETIMEDOUT)
+        if rc != rvh.RVH_OK:
+            assert rvh.rvh_wait(ctx.handle, tk.value, -1) == rvh.RVH_OK
+        # a completed ticket is released by the call that reported it
+        assert rvh.rvh_poll(ctx.handle, tk.value) == rvh.RVH_EINVAL
+        # invalid frames are refused at submission
+        bad = np.array([0, 5, 3], np.int32)
+        fr = rvh.make_frame(f.azimuth[:3], f.doppler[:3], bad)
+        assert rvh.rvh_submit(ctx.handle, fr, params, rvh.make_result(outs), tk) == rvh.RVH_EINVAL
+    finally:
+        ctx.close()
+
+
+def test_backpressure_and_recovery(torch):
+    """A small budget fills up: submissions get RVH_EAGAIN (or a frame too big
+    for the pool RVH_ENOMEM) and succeed again once earlier frames complete."""
+    dev = torch.device("cuda", 0)
+    ctx = rvh.Context(0, mem_budget_bytes=96 << 20)
+    try:
+        w = synth.WORKLOADS["dense3d"]
+        f = synth.make_frame(w, n_clusters=1500, gen_seed=3)
+        t = [torch.from_numpy(x).to(dev) for x in (f.azimuth, f.elevation, f.doppler, f.offsets)]
+        frame = rvh.make_frame(t[0], t[2], t[3], t[1])
+        params = rvh.make_params(3, 2048, 0.1, 1)
+        held, saw_eagain = [], False
+        for _ in range(64):
+            outs = rvh.alloc_outputs(f.n_clusters, f.n_points, dev)
+            tk = ctypes.c_uint64(0)
+            rc = rvh.rvh_submit(ctx.handle, frame, params, rvh.make_result(outs), tk)
+            if rc == rvh.RVH_EAGAIN:
+                saw_eagain = True
+                break
+            assert rc == rvh.RVH_OK, rvh.rvh_last_error(None)
+            held.append((tk.value, outs))
+        for tk, _ in held:
+            assert rvh.rvh_wait(ctx.handle, tk, 60_000_000) == rvh.RVH_OK
+        outs = rvh.alloc_outputs(f.n_clusters, f.n_points, dev)
+        tk = ctypes.c_uint64(0)
+        assert rvh.rvh_submit(ctx.handle, frame, params, rvh.make_result(outs), tk) == rvh.RVH_OK
+        assert rvh.rvh_wait(ctx.handle, tk.value, 60_000_000) == rvh.RVH_OK
+        assert saw_eagain or len(held) == 64
+        big = synth.make_frame(synth.WORKLOADS["dense2d"], n_clusters=16384, gen_seed=4)
+        bframe = rvh.make_frame(big.azimuth, big.doppler, big.offsets)
+        bouts = rvh.alloc_outputs(big.n_clusters, big.n_points, "cpu")
+        rc = rvh.rvh_submit(ctx.handle, bframe, rvh.make_params(2, 64, 0.1, 1), rvh.make_result(bouts), tk)
+        assert rc == rvh.RVH_ENOMEM
+    finally:
+        ctx.close()
+
+
+def test_short_load(torch):
+    dev = torch.device("cuda", 0)
+    spec = synth.ServingSpec(n_radars=16, duration_s=0.6, warmup_s=0.2, clusters_lo=50, clusters_hi=400)
+    ctx = rvh.Context(0)
+    try:
+        res = serving.run_load(ctx, spec, dev, pool_frames=2)
+    finally:
+        ctx.close()
+    s = res.summary()
+    assert res.frames > 50 and s["p99_ms"] is not None and s["p99_ms"] < 1000.0, s
