@@ -150,6 +150,8 @@ def main():
     ap.add_argument("--steps", type=int, default=100)
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", default="rvh", choices=["rvh", "reference"])
+    ap.add_argument("--workload", default=WORKLOAD, choices=["frame64", "dense2d", "stress2d", "dense3d"],
+                    help="dense2d is the headline workload; the others are the precision, 3D and small-frame cases")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-gpu-baseline", action="store_true")
     ap.add_argument("--serving-seconds", type=float, default=3.0,
@@ -167,7 +169,9 @@ def main():
     dev = torch.device("cuda", local)
 
     from paper_2012_12618_gb300 import rvh, synth
-    w = synth.WORKLOADS[WORKLOAD]
+    wname = args.workload
+    w = synth.WORKLOADS[wname]
+    dim = w.model_dim
     # weak scaling: every rank estimates its own frame (independent sensors)
     f = synth.make_frame(w, gen_seed=w.gen_seed + 1000 * rank)
     nc, npts = f.n_clusters, f.n_points
@@ -176,11 +180,12 @@ def main():
 
     ctx = rvh.Context(local)
     d_az = torch.from_numpy(f.azimuth).to(dev)
+    d_el = None if f.elevation is None else torch.from_numpy(f.elevation).to(dev)
     d_dop = torch.from_numpy(f.doppler).to(dev)
     d_off = torch.from_numpy(f.offsets).to(dev)
     outs = rvh.alloc_outputs(nc, npts, dev)
-    frame = rvh.make_frame(d_az, d_dop, d_off)
-    params = rvh.make_params(2, w.num_hypotheses, w.tau, w.seed)
+    frame = rvh.make_frame(d_az, d_dop, d_off, d_el)
+    params = rvh.make_params(dim, w.num_hypotheses, w.tau, w.seed)
     res = rvh.make_result(outs)
     # a dedicated stream: the library and the timing events share it
     stream = torch.cuda.Stream(dev)
@@ -198,7 +203,7 @@ def main():
     torch.cuda.synchronize()
 
     step_ms, kern_ms = [], []
-    band = cand = fp64h = 0
+    band = cand = fp64h = refined = 0
     phase = np.zeros(6)
     if ws > 1:
         torch.distributed.barrier()
@@ -219,6 +224,7 @@ def main():
             band += stats.band_points
             cand += stats.candidates
             fp64h += stats.fp64_hypotheses
+            refined += stats.refined_hypotheses
             phase += np.array(list(stats.phase_cycles), dtype=np.float64)
         torch.cuda.synchronize()
     wall = time.perf_counter() - t_wall
@@ -233,9 +239,9 @@ def main():
     value = nc * ws / t_max
     grid = stats.grid
 
-    # ---- roofline of the fused kernel (FP32 pipe; 2 FMA = 4 flop per trial x point pair)
+    # ---- roofline of the fused kernel (FP32 pipe; k FMA = 2k flop per trial x point pair)
     kern_s = float(np.mean(kern_ms)) * 1e-3
-    flops = 4.0 * pairs
+    flops = 2.0 * dim * pairs
     achieved = flops / kern_s / 1e12
     props = torch.cuda.get_device_properties(dev)
     sms = props.multi_processor_count
@@ -249,7 +255,7 @@ def main():
     peak = sms * FP32_LANES_PER_SM * 2 * max_mhz * 1e6 / 1e12
     roofline = {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
                 "frac": achieved / peak, "traffic": recorded_traffic(),
-                "kernel": "rvh::fused_kernel<2>",
+                "kernel": f"rvh::fused_kernel<{dim}>",
                 "peak_basis": f"{sms} SMs x {FP32_LANES_PER_SM} FP32 FMA lanes x 2 flop x {max_mhz:.0f} MHz",
                 "frac_at_measured_clock": (achieved / (sms * FP32_LANES_PER_SM * 2 * clocks["sm_mhz"] * 1e6 / 1e12)
                                            if clocks.get("sm_mhz") else None),
@@ -257,10 +263,11 @@ def main():
 
     # ---- end to end through the C ABI with pinned host buffers (copies inside the timed region)
     h_az = torch.from_numpy(f.azimuth).pin_memory()
+    h_el = None if f.elevation is None else torch.from_numpy(f.elevation).pin_memory()
     h_dop = torch.from_numpy(f.doppler).pin_memory()
     h_off = torch.from_numpy(f.offsets).pin_memory()
     h_outs = {k: v.cpu().pin_memory() for k, v in outs.items()}
-    h_frame = rvh.make_frame(h_az, h_dop, h_off)
+    h_frame = rvh.make_frame(h_az, h_dop, h_off, h_el)
     h_res = rvh.make_result(h_outs)
     for _ in range(2):
         ctx.check(rvh.rvh_estimate(ctx.handle, h_frame, params, h_res, sptr), "rvh_estimate(host)")
@@ -271,7 +278,7 @@ def main():
         t0 = time.perf_counter()
         ctx.check(rvh.rvh_estimate(ctx.handle, h_frame, params, h_res, sptr), "rvh_estimate(host)")
         e2e_t.append(time.perf_counter() - t0)
-    h2d = npts * 8 + (nc + 1) * 4
+    h2d = npts * 4 * (dim + 1) + (nc + 1) * 4
     d2h = nc * (4 * 8 + 3 * 4) + npts
     e2e = {"value": nc / float(np.mean(e2e_t)), "unit": "clusters/s", "h2d_bytes_per_step": h2d,
            "d2h_bytes_per_step": d2h, "ms_per_step": 1e3 * float(np.mean(e2e_t))}
@@ -312,13 +319,13 @@ def main():
     cpu = None
     if rank == 0 and ws == 1 and not args.no_cpu_baseline:
         import oracle
-        sub = np.sort(np.random.default_rng(1).choice(nc, 1024, replace=False))
+        sub = np.sort(np.random.default_rng(1).choice(nc, min(nc, 1024 if dim == 2 else 256), replace=False))
         t0 = time.perf_counter()
-        oracle.estimate(f.azimuth, f.doppler, f.offsets, num_hypotheses=w.num_hypotheses, tau=w.tau,
-                        seed=w.seed, subset=sub)
+        oracle.estimate(f.azimuth, f.doppler, f.offsets, elevation=f.elevation, num_hypotheses=w.num_hypotheses,
+                        tau=w.tau, seed=w.seed, subset=sub)
         dt = time.perf_counter() - t0
         cpu = {"value": sub.shape[0] / dt, "unit": "clusters/s", "cores": 1, "kind": "oracle",
-               "sample": f"{sub.shape[0]} random clusters of the {WORKLOAD} frame, single-threaded FP64 C",
+               "sample": f"{sub.shape[0]} random clusters of the {wname} frame, single-threaded FP64 C",
                "seconds": dt}
 
     if rank == 0:
@@ -326,8 +333,9 @@ def main():
             "metric": "clusters/s", "value": value, "unit": "clusters/s", "n_gpus": ws, "steps": args.steps,
             "warmup": max(args.warmup, 3), "ms_per_step": t_max * 1e3, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "f32+f64", "data": "synthetic",
-            "config": {"workload": f"{WORKLOAD}: {nc} clusters, sizes log-uniform 8..2048, {npts} points, 2D, "
-                                   f"H={w.num_hypotheses}, tau={w.tau} m/s, seed={w.seed}",
+            "config": {"workload": f"{wname}: {nc} clusters, sizes {w.size_law} {w.size_lo}..{w.size_hi}, "
+                                   f"{npts} points, {dim}D, H={w.num_hypotheses}, tau={w.tau} m/s, "
+                                   f"outliers {w.outlier_frac:g}, noise {w.noise_sigma:g} m/s, seed={w.seed}",
                        "l2": "flushed between timed steps (256 MiB write outside the step events)",
                        "per_rank": "one independent frame per rank"},
             "pair_evals_per_s": pairs * ws / t_max,
@@ -340,6 +348,7 @@ def main():
             "gpu_launches": 2 * args.steps,
             "band": {"fp64_band_decisions_per_step": band / args.steps, "candidates_per_step": cand / args.steps,
                      "fp64_trials_per_step": fp64h / args.steps,
+                     "refined_trials_per_step": refined / args.steps,
                      "band_rate_per_pair": band / args.steps / pairs},
             "schedule": {"grid": grid, "points_per_warp": stats.points_per_warp,
                          "hyps_per_lane": stats.hyps_per_lane},

@@ -143,10 +143,10 @@ int rvh_estimate_baseline(rvh_ctx* ctx, const rvh_frame* frame, const rvh_params
  * start-up, or plugins whose host framework owns all device memory.  It needs
  * no context and calls no cudaMalloc, cudaFree or other allocating routine.
  *
- * Its scratch (work list, work counter, FP32 rows of large clusters) and the
+ * Its scratch (work list, work counter, FP32 and FP64 point rows) and the
  * FP64 row table live in file-scope device arrays of fixed size:
  * RVH_NOALLOC_MAX_CLUSTERS clusters and RVH_NOALLOC_MAX_POINTS points, about
- * 32.5 MiB, which every GPU that loads the library holds until the process
+ * 48.5 MiB, which every GPU that loads the library holds until the process
  * exits.  Larger frames are rejected with RVH_EINVAL and a message.
  *
  * The first call on a device sets that device up (device addresses of the
@@ -158,7 +158,7 @@ int rvh_estimate_baseline(rvh_ctx* ctx, const rvh_frame* frame, const rvh_params
  * call's contents (each call resets the work counter it needs zeroed), so
  * calls that overlap on the GPU race: order them on one stream or with events.
  * Results equal rvh_estimate's. */
-#define RVH_NOALLOC_MAX_POINTS 2097152
+#define RVH_NOALLOC_MAX_POINTS 1048576
 #define RVH_NOALLOC_MAX_CLUSTERS 65536
 int rvh_estimate_noalloc(const rvh_frame* frame, const rvh_params* params, rvh_result* result, void* stream);
 
@@ -199,6 +199,7 @@ typedef struct {
    * hypotheses (draw + solve + bound), scoring pass, exact re-scoring,
    * winner mask + refine, scheduling/other. */
   int64_t phase_cycles[6];
+  int64_t refined_hypotheses;  /* trials whose FP32 solve took one refinement step */
 } rvh_stats;
 
 /* Counters of the last rvh_estimate on this context (synchronises its stream). */

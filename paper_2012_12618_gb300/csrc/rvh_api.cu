@@ -165,11 +165,13 @@ void choose_schedule(rvh_ctx* ctx, int H, int* pw, int* hpl) {
 
 // Fills the per-frame descriptor; the pointers must already be device pointers.
 void fill_desc(rvh_ctx* ctx, FrameDesc& d, const rvh_frame& f, const rvh_params& p, const float* az,
-               const float* el, const float* dop, const int32_t* off, float4* rows_g, const rvh_result& out) {
+               const float* el, const float* dop, const int32_t* off, float4* rows_g, double4_32a* rows64_g,
+               const rvh_result& out) {
   d.trig = ctx->trig;
+  d.rows64_g = rows64_g;
   const int dim = p.model_dim;
   const double eps = p.cond_eps > 0 ? p.cond_eps : default_eps(dim);
-  const double eD = (dim == 2 ? 1.081e-6 : 6.20e-6) + 0x1p-50;
+  const double eD = (dim == 2 ? 5.98e-7 : 3.65e-6) + 0x1p-50;
   d.az = az;
   d.el = el;
   d.dop = dop;
@@ -308,6 +310,7 @@ int rvh_get_stats(rvh_ctx* ctx, rvh_stats* out) {
     unsigned long long h[10] = {0, 0, 0, 0, 0, 0, 0, 0, 0, 0};
     RVH_CUDA(cudaMemcpy(h, ctx->stats_d, sizeof(h), cudaMemcpyDeviceToHost));
     for (int k = 0; k < 6; ++k) ctx->last.phase_cycles[k] = (int64_t)h[4 + k];
+    ctx->last.refined_hypotheses = (int64_t)h[3];
     ctx->last.candidates = (int64_t)h[0];
     ctx->last.band_points = (int64_t)h[1];
     ctx->last.fp64_hypotheses = (int64_t)h[2];
@@ -332,6 +335,7 @@ struct Staged {
   int* counter;
   unsigned long long* stats;
   void* rows;               // float4[n_points] (fused) or double[4 n_points] (baseline)
+  double4_32a* rows64;          // double4_32a[n_points] (fused)
 };
 
 static int stage(rvh_ctx* ctx, const rvh_frame* f, const rvh_params* p, rvh_result* r, cudaStream_t s,
@@ -360,6 +364,7 @@ static int stage(rvh_ctx* ctx, const rvh_frame* f, const rvh_params* p, rvh_resu
   const size_t o_ctr = take(64);
   const size_t o_stats = take(128);
   const size_t o_rows = take((fused ? sizeof(float4) : 4 * sizeof(double)) * (size_t)std::max<int64_t>(np, 1));
+  const size_t o_rows64 = fused ? take(sizeof(double4_32a) * (size_t)std::max<int64_t>(np, 1)) : 0;
   const size_t o_az = d_az ? 0 : take(4 * (size_t)np);
   const size_t o_el = d_el ? 0 : take(4 * (size_t)np);
   const size_t o_dop = d_dop ? 0 : take(4 * (size_t)np);
@@ -386,6 +391,7 @@ static int stage(rvh_ctx* ctx, const rvh_frame* f, const rvh_params* p, rvh_resu
   st.counter = (int*)(b + o_ctr);
   st.stats = (unsigned long long*)(b + o_stats);
   st.rows = b + o_rows;
+  st.rows64 = fused ? (double4_32a*)(b + o_rows64) : nullptr;
   st.az = d_az ? f->azimuth : (const float*)(b + o_az);
   st.el = dim3 ? (d_el ? f->elevation : (const float*)(b + o_el)) : nullptr;
   st.dop = d_dop ? f->doppler : (const float*)(b + o_dop);
@@ -442,7 +448,7 @@ int rvh_estimate(rvh_ctx* ctx, const rvh_frame* frame, const rvh_params* params,
   RVH_CUDA(cudaMemsetAsync(st.stats, 0, 80, s));
   FusedArgs a;
   memset(&a, 0, sizeof(a));
-  fill_desc(ctx, a.f[0], *frame, *params, st.az, st.el, st.dop, st.off, (float4*)st.rows, st.dev_out);
+  fill_desc(ctx, a.f[0], *frame, *params, st.az, st.el, st.dop, st.off, (float4*)st.rows, st.rows64, st.dev_out);
   a.n_frames = 1;
   a.n_items = frame->n_clusters;
   a.worklist = st.worklist;
@@ -481,7 +487,7 @@ int rvh_estimate_baseline(rvh_ctx* ctx, const rvh_frame* frame, const rvh_params
   BaselineArgs b;
   memset(&b, 0, sizeof(b));
   FrameDesc d;
-  fill_desc(ctx, d, *frame, *params, st.az, st.el, st.dop, st.off, nullptr, st.dev_out);
+  fill_desc(ctx, d, *frame, *params, st.az, st.el, st.dop, st.off, nullptr, nullptr, st.dev_out);
   b.az = d.az;
   b.el = d.el;
   b.dop = d.dop;

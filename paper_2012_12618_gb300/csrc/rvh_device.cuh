@@ -151,19 +151,23 @@ __device__ __forceinline__ double residual_f64(const double* a, double w, const 
 
 // ---- FP32 rows and FP32 hypotheses with rigorous error bounds ------------------------
 
-// Relative accuracy assumed for sincosf on |t| <= pi (tests verify twice this
-// margin exhaustively over every float in the range); outside it the row is
-// the FP64 one rounded to nearest.
-constexpr float kRowRel = 0x1p-21f;          // rho: |c32 - c64| <= rho |c64|
-constexpr float kU = 0x1p-24f;               // FP32 unit roundoff
-constexpr float kRowRel3 = 2.0f * 0x1p-21f + 2.0f * 0x1p-24f;  // products cos*cos
+// Relative accuracy assumed for sincosf on |t| <= pi: |c32 - c64| <= rho |c64|.
+// Tests check every float in that range against twice this margin; outside it
+// the row is the FP64 one rounded to nearest.
+constexpr float kRowRel = 0x1p-22f;
+constexpr float kU = 0x1p-24f;                                 // FP32 unit roundoff
+constexpr float kRowRel3 = 2.0f * 0x1p-22f + 2.0f * 0x1p-24f;  // products cos t * cos e
 constexpr float kSafety = 1.0f + 0x1p-14f;   // covers second-order terms and bound roundings
 constexpr float kTiny = 0x1p-120f;           // absolute slack for underflow
 constexpr float kBandFloor = 1e-5f;          // minimum half-width of the FP64 band (m/s)
 // |det32 - det64| over unit rows: (2 rho + 2u)(1 + 1e-4) for 2D,
 // sqrt(3)(3 rho3 + 5u) for 3D, rounded up, plus the FP64 rounding of det64.
-constexpr float kDetErr2 = 1.081e-6f;
-constexpr float kDetErr3 = 6.20e-6f;
+constexpr float kDetErr2 = 5.98e-7f;
+constexpr float kDetErr3 = 3.65e-6f;
+// Trials (of callers that allow refinement) whose band would be wider than
+// this get one refinement step; 3D minimal sets are ill-conditioned in the
+// vertical direction, so most 3D trials do.
+constexpr float kRefineBand = 1e-4f;
 
 // FP32 row of a point plus its Doppler: (c, s, w, 0) or (a0, a1, a2, w).
 template <int DIM>
@@ -199,120 +203,159 @@ struct Hyp32 {
   float thi;          // |r32| >  thi  => certainly an outlier
   float tlo;          // |r32| <= tlo  => certainly an inlier
   int kind;
+  int refined;
 };
 
-// FP32 minimal-set solve of the rows p, q[, r] (FP32 rows with Doppler in the
-// last used lane) and the half-width b of the band outside of which the FP32
-// residual decides exactly like the FP64 one.  wmax = max |w| over the cluster.
-// Conditioning: |det32| >= acc => FP64 accepts; |det32| < rej => FP64 rejects;
-// otherwise the kind is kHypUndecided and the caller decides in FP64.
+// FP32 Cramer solve of the rows p, q[, r] with right side b (exact floats),
+// determinant d already formed.  X receives the solution, e a bound on
+// |X - A64^-1 b| per component, where A64 holds the FP64 rows: the bound
+// covers the FP32 rows' error (rho per entry), every FP32 rounding, and the
+// error of d (eD).
 template <int DIM>
-__device__ __forceinline__ Hyp32 hyp_f32(float4 p, float4 q, float4 r, float wmax, float acc,
-                                         float rej, TauPair tau) {
+__device__ __forceinline__ void cramer_f32(float4 p, float4 q, float4 r, const float* b, float d, float eD,
+                                           float* X, float* e) {
+  const float ad = fabsf(d);
+  const float inv = 1.0f / ad;
+  const float slack = eD / (ad - eD);
+  if (DIM == 2) {
+    const float n0 = fmaf(b[0], q.y, -(b[1] * p.y));
+    const float n1 = fmaf(p.x, b[1], -(b[0] * q.x));
+    X[0] = n0 / d;
+    X[1] = n1 / d;
+    X[2] = 0.0f;
+    const float A = (kRowRel + kU) * 1.0001f * (fabsf(b[0]) + fabsf(b[1]));
+    const float e0 = A + kU * fabsf(n0), e1 = A + kU * fabsf(n1);
+    e[0] = (e0 + (fabsf(n0) + e0) * slack) * inv + kU * fabsf(X[0]);
+    e[1] = (e1 + (fabsf(n1) + e1) * slack) * inv + kU * fabsf(X[1]);
+    e[2] = 0.0f;
+  } else {
+    float n[3];
+    {  // column 0 replaced by b
+      const float c0 = fmaf(q.y, r.z, -(q.z * r.y));
+      const float c1 = fmaf(b[1], r.z, -(q.z * b[2]));
+      const float c2 = fmaf(b[1], r.y, -(q.y * b[2]));
+      n[0] = fmaf(p.z, c2, fmaf(-p.y, c1, b[0] * c0));
+    }
+    {  // column 1 replaced by b
+      const float c0 = fmaf(b[1], r.z, -(q.z * b[2]));
+      const float c1 = fmaf(q.x, r.z, -(q.z * r.x));
+      const float c2 = fmaf(q.x, b[2], -(b[1] * r.x));
+      n[1] = fmaf(p.z, c2, fmaf(-b[0], c1, p.x * c0));
+    }
+    {  // column 2 replaced by b
+      const float c0 = fmaf(q.y, b[2], -(b[1] * r.y));
+      const float c1 = fmaf(q.x, b[2], -(b[1] * r.x));
+      const float c2 = fmaf(q.x, r.y, -(q.y * r.x));
+      n[2] = fmaf(b[0], c2, fmaf(-p.y, c1, p.x * c0));
+    }
+    const float A = (4.0f * kRowRel3 + 8.0f * kU) * 1.0001f * (fabsf(b[0]) + fabsf(b[1]) + fabsf(b[2]));
+#pragma unroll
+    for (int k = 0; k < 3; ++k) {
+      X[k] = n[k] / d;
+      const float ek = A + kU * fabsf(n[k]);
+      e[k] = (ek + (fabsf(n[k]) + ek) * slack) * inv + kU * fabsf(X[k]);
+    }
+  }
+}
+
+// Half-width of the band around tau outside of which the FP32 residual of any
+// point decides like the FP64 residual, for a trial X with |X - X64| <= e.
+template <int DIM>
+__device__ __forceinline__ float band_f32(float wmax, const float* X, const float* e) {
+  float b;
+  if (DIM == 2) {
+    b = (2.0f * kU + 0x1p-52f) * wmax + (kU + kRowRel + 0x1p-52f) * fabsf(X[0]) +
+        (2.0f * kU + kRowRel + 0x1p-52f) * fabsf(X[1]) + e[0] + e[1];
+  } else {
+    b = (3.0f * kU + 0x1p-52f) * wmax + (kU + kRowRel3 + 0x1p-52f) * fabsf(X[0]) +
+        (2.0f * kU + kRowRel3 + 0x1p-52f) * fabsf(X[1]) + (3.0f * kU + kRowRel + 0x1p-52f) * fabsf(X[2]) +
+        e[0] + e[1] + e[2];
+  }
+  return b * kSafety + kTiny;
+}
+
+// The trial's FP32 hypothesis and band.  p, q[, r]: FP32 rows (with Doppler);
+// seed64(i) returns the FP64 row (a0, a1, a2, w) of seed point i, called only
+// by the refinement step; refine = false disables it.  wmax = max |w| over
+// the cluster.  Conditioning: |det32| >= acc => FP64 accepts; |det32| < rej =>
+// FP64 rejects; otherwise kHypUndecided (the caller decides in FP64).
+//
+// Refinement (when the band would exceed kRefineBand): the seed residuals
+// r = w - A64 X are formed in FP64, the correction A^-1 r is solved in FP32
+// and added.  Since X64 - X = A64^-1 (w - A64 X) exactly, the corrected
+// error is the correction's own error (tiny: r is tiny) plus
+// ||A64^-1||_inf (|fl(r) - r| + FP64 rounding) plus the FP32 rounding of X+dX.
+template <int DIM, typename Seed64>
+__device__ __forceinline__ Hyp32 hyp_f32(float4 p, float4 q, float4 r, const Seed64& seed64, bool refine, float wmax,
+                                         float acc, float rej, TauPair tau) {
   Hyp32 h;
   h.nx = h.ny = h.nz = 0.0f;
   h.thi = __int_as_float(0x7fc00000);  // NaN: never counted
   h.tlo = -1.0f;
+  h.refined = 0;
+  float d;
   if (DIM == 2) {
-    const float d = fmaf(p.x, q.y, -(p.y * q.x));
-    const float ad = fabsf(d);
-    if (!(ad >= acc)) {
-      h.kind = (ad < rej) ? kHypRejected : kHypUndecided;
-      return h;
-    }
-    const float w0 = p.z, w1 = q.z;
-    const float nxn = fmaf(w0, q.y, -(w1 * p.y));
-    const float nyn = fmaf(p.x, w1, -(w0 * q.x));
-    const float X = nxn / d, Y = nyn / d;
-    const float A = fabsf(w0) + fabsf(w1);
-    const float eD = kDetErr2;
-    const float inv = 1.0f / ad;
-    const float slack = 1.0f / (ad - eD);
-    const float eNX = (kRowRel + kU) * 1.0001f * A + kU * fabsf(nxn);
-    const float eNY = (kRowRel + kU) * 1.0001f * A + kU * fabsf(nyn);
-    const float eX = eNX * inv + (fabsf(nxn) + eNX) * slack * eD * inv + kU * fabsf(X);
-    const float eY = eNY * inv + (fabsf(nyn) + eNY) * slack * eD * inv + kU * fabsf(Y);
-    const float e64 = 0x1p-50f * (2.0f * A + fabsf(nxn) + fabsf(nyn) + 2.0f * (fabsf(X) + fabsf(Y))) * inv;
-    float b = (2.0f * kU + 0x1p-52f) * wmax + (kU + kRowRel + 0x1p-52f) * fabsf(X) +
-              (2.0f * kU + kRowRel + 0x1p-52f) * fabsf(Y) + eX + eY + e64;
-    b = b * kSafety + kTiny;
-    h.nx = -X;
-    h.ny = -Y;
-    if (!(b < 1e30f) || !(fabsf(X) < 1e30f) || !(fabsf(Y) < 1e30f) || !(ad > 2.0f * eD)) {
-      h.kind = kHypExactOnly;
-      h.thi = __int_as_float(0x7f800000);  // +inf: nothing certainly out
-      h.tlo = -1.0f;                        // nothing certainly in
-      return h;
-    }
-    b = fmaxf(b, kBandFloor);
-    h.thi = __fadd_ru(tau.hi, b);
-    h.tlo = __fsub_rd(tau.lo, b);
-    h.kind = kHypNormal;
-    return h;
+    d = fmaf(p.x, q.y, -(p.y * q.x));
   } else {
-    // rows p, q, r = (a0, a1, a2, w)
     const float k0 = fmaf(q.y, r.z, -(q.z * r.y));
     const float k1 = fmaf(q.x, r.z, -(q.z * r.x));
     const float k2 = fmaf(q.x, r.y, -(q.y * r.x));
-    const float d = fmaf(p.z, k2, fmaf(-p.y, k1, p.x * k0));
-    const float ad = fabsf(d);
-    if (!(ad >= acc)) {
-      h.kind = (ad < rej) ? kHypRejected : kHypUndecided;
-      return h;
-    }
-    const float wp = p.w, wq = q.w, wr = r.w;
-    // column 0 replaced by w
-    float n0, n1, n2;
-    {
-      const float c0 = fmaf(q.y, r.z, -(q.z * r.y));
-      const float c1 = fmaf(wq, r.z, -(q.z * wr));
-      const float c2 = fmaf(wq, r.y, -(q.y * wr));
-      n0 = fmaf(p.z, c2, fmaf(-p.y, c1, wp * c0));
-    }
-    {  // column 1 replaced by w
-      const float c0 = fmaf(wq, r.z, -(q.z * wr));
-      const float c1 = fmaf(q.x, r.z, -(q.z * r.x));
-      const float c2 = fmaf(q.x, wr, -(wq * r.x));
-      n1 = fmaf(p.z, c2, fmaf(-wp, c1, p.x * c0));
-    }
-    {  // column 2 replaced by w
-      const float c0 = fmaf(q.y, wr, -(wq * r.y));
-      const float c1 = fmaf(q.x, wr, -(wq * r.x));
-      const float c2 = fmaf(q.x, r.y, -(q.y * r.x));
-      n2 = fmaf(wp, c2, fmaf(-p.y, c1, p.x * c0));
-    }
-    const float X = n0 / d, Y = n1 / d, Z = n2 / d;
-    const float A = fabsf(wp) + fabsf(wq) + fabsf(wr);
-    const float eD = kDetErr3;
-    const float inv = 1.0f / ad;
-    const float slack = 1.0f / (ad - eD);
-    const float eNb = (4.0f * kRowRel3 + 8.0f * kU) * 1.0001f * A;
-    const float eN0 = eNb + kU * fabsf(n0), eN1 = eNb + kU * fabsf(n1), eN2 = eNb + kU * fabsf(n2);
-    const float eX = eN0 * inv + (fabsf(n0) + eN0) * slack * eD * inv + kU * fabsf(X);
-    const float eY = eN1 * inv + (fabsf(n1) + eN1) * slack * eD * inv + kU * fabsf(Y);
-    const float eZ = eN2 * inv + (fabsf(n2) + eN2) * slack * eD * inv + kU * fabsf(Z);
-    const float e64 = 0x1p-48f *
-                      (3.0f * A + fabsf(n0) + fabsf(n1) + fabsf(n2) + 3.0f * (fabsf(X) + fabsf(Y) + fabsf(Z))) * inv;
-    float b = (3.0f * kU + 0x1p-52f) * wmax + (kU + kRowRel3 + 0x1p-52f) * fabsf(X) +
-              (2.0f * kU + kRowRel3 + 0x1p-52f) * fabsf(Y) + (3.0f * kU + kRowRel + 0x1p-52f) * fabsf(Z) +
-              eX + eY + eZ + e64;
-    b = b * kSafety + kTiny;
-    h.nx = -X;
-    h.ny = -Y;
-    h.nz = -Z;
-    if (!(b < 1e30f) || !(fabsf(X) < 1e30f) || !(fabsf(Y) < 1e30f) || !(fabsf(Z) < 1e30f) ||
-        !(ad > 2.0f * eD)) {
-      h.kind = kHypExactOnly;
-      h.thi = __int_as_float(0x7f800000);
-      h.tlo = -1.0f;
-      return h;
-    }
-    b = fmaxf(b, kBandFloor);
-    h.thi = __fadd_ru(tau.hi, b);
-    h.tlo = __fsub_rd(tau.lo, b);
-    h.kind = kHypNormal;
+    d = fmaf(p.z, k2, fmaf(-p.y, k1, p.x * k0));
+  }
+  const float ad = fabsf(d);
+  if (!(ad >= acc)) {
+    h.kind = (ad < rej) ? kHypRejected : kHypUndecided;
     return h;
   }
+  const float eD = DIM == 2 ? kDetErr2 : kDetErr3;
+  const float w[3] = {DIM == 2 ? p.z : p.w, DIM == 2 ? q.z : q.w, DIM == 2 ? 0.0f : r.w};
+  float X[3], e[3];
+  cramer_f32<DIM>(p, q, r, w, d, eD, X, e);
+  // error of the FP64 solve (the oracle's X64) against the exact solution with FP64 rows
+  const float sw = fabsf(w[0]) + fabsf(w[1]) + fabsf(w[2]);
+  const float sx = fabsf(X[0]) + fabsf(X[1]) + fabsf(X[2]);
+  const float e64 = (DIM == 2 ? 0x1p-50f : 0x1p-48f) * (2.0f * sw + 2.0f * sx) / ad;
+#pragma unroll
+  for (int k = 0; k < DIM; ++k) e[k] += e64;
+  float b = band_f32<DIM>(wmax, X, e);
+  if (refine && b > kRefineBand && ad > 2.0f * eD && b < 1e30f) {
+    float rf[3] = {0.0f, 0.0f, 0.0f};
+    float rerr = 0.0f;
+    const double X0 = X[0], X1 = X[1], X2 = X[2];
+#pragma unroll
+    for (int i = 0; i < DIM; ++i) {
+      const double4_32a a = seed64(i);
+      const double ri = DIM == 2 ? a.w - fma(X0, a.x, X1 * a.y) : a.w - fma(X0, a.x, fma(X1, a.y, X2 * a.z));
+      rf[i] = __double2float_rn(ri);
+      // |fl32(r) - r| + FP64 rounding of r
+      rerr = fmaxf(rerr, kU * fabsf(rf[i]) + 0x1p-51f * (fabsf(w[i]) + sx));
+    }
+    float dX[3], de[3];
+    cramer_f32<DIM>(p, q, r, rf, d, eD, dX, de);
+    const float inv_norm = (float)DIM / (ad - eD);  // ||A64^-1||_inf (adjugate entries <= 1)
+#pragma unroll
+    for (int k = 0; k < DIM; ++k) {
+      X[k] = X[k] + dX[k];
+      e[k] = de[k] + inv_norm * rerr + kU * fabsf(X[k]) + e64;
+    }
+    b = band_f32<DIM>(wmax, X, e);
+    h.refined = 1;
+  }
+  h.nx = -X[0];
+  h.ny = -X[1];
+  h.nz = -X[2];
+  if (!(b < 1e30f) || !(fabsf(X[0]) < 1e30f) || !(fabsf(X[1]) < 1e30f) || !(fabsf(X[2]) < 1e30f) ||
+      !(ad > 2.0f * eD)) {
+    h.kind = kHypExactOnly;
+    h.thi = __int_as_float(0x7f800000);  // +inf: nothing certainly out
+    h.tlo = -1.0f;                        // nothing certainly in
+    return h;
+  }
+  b = fmaxf(b, kBandFloor);
+  h.thi = __fadd_ru(tau.hi, b);
+  h.tlo = __fsub_rd(tau.lo, b);
+  h.kind = kHypNormal;
+  return h;
 }
 
 // FP32 residual of a row under a hypothesis (negated velocity).

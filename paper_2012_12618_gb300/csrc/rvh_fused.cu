@@ -1,6 +1,7 @@
-// Fused persistent kernel: per cluster, FP32 rows -> counter-RNG minimal sets
-// -> FP32 solve with error bound -> FP32 scoring pass (upper-bound counts) ->
-// exact re-scoring of the trials that can still win (FP64 only inside the
+// Fused persistent kernel: per cluster, FP32 and FP64 rows -> counter-RNG
+// minimal sets -> FP32 solve with error bound (refined in FP64 residuals when
+// ill-conditioned) -> FP32 scoring pass (upper-bound counts) -> exact counts,
+// in index order, of the trials that can still win (FP64 only inside the
 // error band) -> lowest-index argmax -> FP64 inlier mask and normal-equation
 // refine -> heading.  Sec. III-A (Alg. 1, Eq. 4) and Sec. III-B (Eq. LSQ_eq,
 // Eq. eq:LSQPerCluster, Alg. 2) of arXiv 2012.12618.
@@ -8,7 +9,8 @@
 // Parallel mapping (GB300-first, not the paper's thread-per-trial): clusters
 // are work items taken by persistent CTAs from an LPT-ordered list; inside a
 // cluster, trials map to warps/lanes and points to lanes, with the cluster's
-// FP32 rows staged in shared memory.
+// FP32 rows staged in shared memory and its FP64 rows in L1/L2-resident
+// global scratch.
 #include <cstdint>
 #include <cuda_runtime.h>
 
@@ -28,7 +30,6 @@ struct Smem {
   float4* hyp;        // [hchunk] (-X, -Y, -Z, thi)
   float* tlo;         // [hchunk]
   int* U;             // [hchunk] upper bounds of the exact counts (-1 = rejected)
-  int* cand;          // [hchunk] candidate list
   int8_t* kind;       // [hchunk]
 };
 
@@ -95,7 +96,7 @@ __device__ __forceinline__ float block_max_float(float v, float* red) {
   return r;
 }
 
-// ---- phase A: upper-bound counts U_h = #{|r32| <= thi_h} ---------------------------
+// ---- a4: upper-bound counts U_h = #{|r32| <= thi_h} (the hot loop) -----------------
 // Lane l handles trial sub-group l / PW and points l % PW, l % PW + PW, ...;
 // each lane keeps HPL trials in registers.  PW = 32 is warp-per-trial-group
 // with lanes over points; PW = 1 is lanes over trials with broadcast rows.
@@ -153,32 +154,44 @@ __device__ void phase_a_dispatch(int pw, int hpl, const float4* rows, int N, con
   }
 }
 
-// FP64 velocity of trial h (the oracle's exact rounding sequence).  Returns false if rejected.
+// FP64 rows (a0, a1, a2, w) of a cluster's points.  The 3D model keeps them
+// in global scratch, written once when the cluster is loaded (every 3D trial
+// refines its solve with them); the 2D model computes them when asked (only
+// the winner's inliers, band points and rare refinements need them).
 template <int DIM>
-__device__ bool hyp_f64(const FrameDesc& a, int64_t o, int ci, int h, int N, double v[3]) {
+struct Rows64 {
+  const FrameDesc* a;
+  int64_t o;
+  double4_32a* pre;
+  __device__ __forceinline__ double4_32a at(int j) const {
+    if (DIM == 3) return pre[j];
+    double t[3];
+    row_f64<2>(a->trig, a->az[o + j], 0.0f, t);
+    return make_double4_32a(t[0], t[1], 0.0, (double)a->dop[o + j]);
+  }
+};
+
+// FP64 velocity of trial h in the oracle's exact rounding sequence.  Returns
+// false if rejected.
+template <int DIM>
+__device__ bool hyp_f64(const FrameDesc& a, const Rows64<DIM>& R, int ci, int h, int N, double v[3]) {
   int q[3];
   draw_minimal_set<DIM>(a.key, ci, h, N, q);
-  double r0[3], r1[3], r2[3] = {0.0, 0.0, 0.0};
-  row_f64<DIM>(a.trig, a.az[o + q[0]], DIM == 3 ? a.el[o + q[0]] : 0.0f, r0);
-  row_f64<DIM>(a.trig, a.az[o + q[1]], DIM == 3 ? a.el[o + q[1]] : 0.0f, r1);
-  if (DIM == 3) row_f64<DIM>(a.trig, a.az[o + q[2]], a.el[o + q[2]], r2);
-  double w[3] = {(double)a.dop[o + q[0]], (double)a.dop[o + q[1]], DIM == 3 ? (double)a.dop[o + q[2]] : 0.0};
+  const double4_32a s0 = R.at(q[0]), s1 = R.at(q[1]), s2 = R.at(DIM == 3 ? q[2] : q[0]);
+  const double r0[3] = {s0.x, s0.y, s0.z}, r1[3] = {s1.x, s1.y, s1.z}, r2[3] = {s2.x, s2.y, s2.z};
+  const double w[3] = {s0.w, s1.w, DIM == 3 ? s2.w : 0.0};
   return solve_f64<DIM>(r0, r1, r2, w, a.eps, v, nullptr);
 }
 
 struct ClusterShared {
   unsigned long long best;
-  int ncand;
-  int nin;
   float wmax;
   float4 win;      // winner's FP32 record
   float win_tlo;
-  double v64[3];
-  int win_ok;
   int red_i[kWarps];
   float red_f[kWarps];
   double red_d[kWarps][10];
-  unsigned long long ctr[4];  // candidates, band points, fp64 hyps, reserved
+  unsigned long long ctr[4];  // exact counts, band points, fp64 trials, refined trials
   unsigned long long clk[6];  // cycles per stage (thread 0's view of the CTA)
   unsigned long long red_u[kWarps];
   double cv64[3];             // FP64 velocity of the trial being counted (when it has band points)
@@ -190,8 +203,8 @@ struct ClusterShared {
 // re-decision of the points inside the trial's error band.  When there are
 // band points the trial's FP64 velocity is left in cs.cv64 and *band > 0.
 template <int DIM>
-__device__ int exact_count_block(const FrameDesc& a, const float4* __restrict__ rows, int64_t o, int ci,
-                                 int h, int N, float4 hy, float tlo, ClusterShared& cs, int* band) {
+__device__ int exact_count_block(const FrameDesc& a, const float4* __restrict__ rows, const Rows64<DIM>& R,
+                                 int ci, int h, int N, float4 hy, float tlo, ClusterShared& cs, int* band) {
   const int tid = threadIdx.x;
   unsigned long long lb = 0;  // L in the low word, B in the high word
   for (int j = tid; j < N; j += kThreads) {
@@ -206,7 +219,7 @@ __device__ int exact_count_block(const FrameDesc& a, const float4* __restrict__ 
   __syncthreads();
   if (tid == 0) {
     double v[3] = {0.0, 0.0, 0.0};
-    hyp_f64<DIM>(a, o, ci, h, N, v);
+    hyp_f64<DIM>(a, R, ci, h, N, v);
     cs.cv64[0] = v[0];
     cs.cv64[1] = v[1];
     cs.cv64[2] = v[2];
@@ -216,13 +229,11 @@ __device__ int exact_count_block(const FrameDesc& a, const float4* __restrict__ 
   const double v[3] = {cs.cv64[0], cs.cv64[1], cs.cv64[2]};
   unsigned long long lbin = 0;
   for (int j = tid; j < N; j += kThreads) {
-    const float4 p = rows[j];
-    const float r = fabsf(resid_f32<DIM>(p, hy.x, hy.y, hy.z));
+    const float r = fabsf(resid_f32<DIM>(rows[j], hy.x, hy.y, hy.z));
     if (!(r <= tlo) && !(r > hy.w)) {
-      double a64[3];
-      row_f64<DIM>(a.trig, a.az[o + j], DIM == 3 ? a.el[o + j] : 0.0f, a64);
-      const double w = (double)(DIM == 2 ? p.z : p.w);
-      if (fabs(residual_f64<DIM>(a64, w, v)) <= a.tau) ++lbin;
+      const double4_32a s = R.at(j);
+      const double a64[3] = {s.x, s.y, s.z};
+      if (fabs(residual_f64<DIM>(a64, s.w, v)) <= a.tau) ++lbin;
     }
   }
   lbin = block_sum_u64(lbin, cs.red_u);
@@ -238,6 +249,78 @@ __device__ void write_invalid(const FrameDesc& a, int ci, int st) {
   a.inlier_count[ci] = 0;
   a.best[ci] = -1;
   a.status[ci] = st;
+}
+
+// a8: normal equations G v = g over the inliers (sums t: 2D Scc, Scs, Sss,
+// Scv, Ssv; 3D the six entries of G then g), Cramer's rule, fallback to the
+// winning minimal-set velocity, heading atan2(vy, vx).  One thread.
+template <int DIM>
+__device__ void finish_cluster(const FrameDesc& a, const Rows64<DIM>& R, int ci, int N, int hstar, int n_in,
+                               const double* t, const double* v64, bool has_v64) {
+  double vout[3] = {v64[0], v64[1], v64[2]};
+  int st = 0;
+  bool ok = false;
+  if (DIM == 2) {
+    const double tr = t[0] + t[2];
+    const double limit = 1e-12 * (tr * tr);
+    const double det = det2_f64(t[0], t[1], t[1], t[2]);
+    if (n_in >= 2 && fabs(det) > limit) {
+      const double G0[3] = {t[0], t[1], 0.0}, G1[3] = {t[1], t[2], 0.0}, g[3] = {t[3], t[4], 0.0};
+      double vs[3];
+      solve_f64<2>(G0, G1, nullptr, g, 0.0, vs, nullptr);
+      vout[0] = vs[0];
+      vout[1] = vs[1];
+      vout[2] = 0.0;
+      ok = true;
+    }
+  } else {
+    const double tr = t[0] + t[3] + t[5];
+    const double limit = 1e-12 * (tr * tr * tr);
+    const double G0[3] = {t[0], t[1], t[2]}, G1[3] = {t[1], t[3], t[4]}, G2[3] = {t[2], t[4], t[5]};
+    const double det = det3_f64(G0, G1, G2);
+    if (n_in >= 3 && fabs(det) > limit) {
+      const double g[3] = {t[6], t[7], t[8]};
+      double vs[3];
+      solve_f64<3>(G0, G1, G2, g, 0.0, vs, nullptr);
+      vout[0] = vs[0];
+      vout[1] = vs[1];
+      vout[2] = vs[2];
+      ok = true;
+    }
+  }
+  if (!ok) {
+    st |= RVH_STATUS_LSQ_FALLBACK;
+    if (!has_v64) hyp_f64<DIM>(a, R, ci, hstar, N, vout);
+  }
+  a.vx[ci] = vout[0];
+  a.vy[ci] = vout[1];
+  if (a.vz) a.vz[ci] = DIM == 3 ? vout[2] : 0.0;
+  a.heading[ci] = atan2(vout[1], vout[0]);
+  a.inlier_count[ci] = n_in;
+  a.best[ci] = hstar;
+  a.status[ci] = st;
+}
+
+// Accumulates the normal-equation sums of one inlier row (a0, a1, a2, w).
+template <int DIM>
+__device__ __forceinline__ void accumulate_row(double* sums, const double4_32a& s) {
+  if (DIM == 2) {
+    sums[0] = fma(s.x, s.x, sums[0]);
+    sums[1] = fma(s.x, s.y, sums[1]);
+    sums[2] = fma(s.y, s.y, sums[2]);
+    sums[3] = fma(s.x, s.w, sums[3]);
+    sums[4] = fma(s.y, s.w, sums[4]);
+  } else {
+    sums[0] = fma(s.x, s.x, sums[0]);
+    sums[1] = fma(s.x, s.y, sums[1]);
+    sums[2] = fma(s.x, s.z, sums[2]);
+    sums[3] = fma(s.y, s.y, sums[3]);
+    sums[4] = fma(s.y, s.z, sums[4]);
+    sums[5] = fma(s.z, s.z, sums[5]);
+    sums[6] = fma(s.x, s.w, sums[6]);
+    sums[7] = fma(s.y, s.w, sums[7]);
+    sums[8] = fma(s.z, s.w, sums[8]);
+  }
 }
 
 template <int DIM, bool SMEM_ROWS>
@@ -257,6 +340,7 @@ __device__ void process_cluster(const FrameDesc& a, const Smem& S, ClusterShared
     return;
   }
   float4* rows = SMEM_ROWS ? S.rows : (a.rows_g + o);
+  const Rows64<DIM> R = {&a, o, a.rows64_g + o};
   long long t_stage = clock64();
   auto stage_done = [&](int k) {
     if (tid == 0) {
@@ -266,11 +350,18 @@ __device__ void process_cluster(const FrameDesc& a, const Smem& S, ClusterShared
     }
   };
 
-  // a1: FP32 rows of the cluster (sincosf; FP64 fallback outside |t| <= pi)
+  // a1: FP32 rows in shared memory (sincosf), FP64 rows in global scratch
   float wm = 0.0f;
   for (int j = tid; j < N; j += kThreads) {
     const float w = a.dop[o + j];
-    rows[j] = row_f32<DIM>(a.az[o + j], DIM == 3 ? a.el[o + j] : 0.0f, w);
+    const float az = a.az[o + j];
+    const float el = DIM == 3 ? a.el[o + j] : 0.0f;
+    rows[j] = row_f32<DIM>(az, el, w);
+    if (DIM == 3) {
+      double a64[3];
+      row_f64<DIM>(a.trig, az, el, a64);
+      R.pre[j] = make_double4_32a(a64[0], a64[1], a64[2], (double)w);
+    }
     wm = fmaxf(wm, fabsf(w));
   }
   wm = block_max_float(wm, cs.red_f);  // includes a __syncthreads after the row writes
@@ -280,25 +371,29 @@ __device__ void process_cluster(const FrameDesc& a, const Smem& S, ClusterShared
   }
   __syncthreads();
   const float wmax = cs.wmax;
-  unsigned long long n_fp64 = 0, n_cand = 0;
+  unsigned long long n_fp64 = 0, n_cand = 0, n_ref = 0;
   stage_done(0);
 
   for (int hc0 = 0; hc0 < a.H; hc0 += hchunk) {
     const int nh = min(hchunk, a.H - hc0);
-    // a2 + a3: draw, FP32 solve, bound
+    // a2 + a3: draw, FP32 solve (refined when ill-conditioned), bound
     for (int hl = tid; hl < nh; hl += kThreads) {
       int q[3];
       draw_minimal_set<DIM>(a.key, ci, hc0 + hl, N, q);
-      const float4 p0 = rows[q[0]], p1 = rows[q[1]];
-      const float4 p2 = DIM == 3 ? rows[q[2]] : p0;
-      Hyp32 hy = hyp_f32<DIM>(p0, p1, p2, wmax, a.acc, a.rej, a.tau32);
+      const int q2 = DIM == 3 ? q[2] : q[0];
+      const float4 p0 = rows[q[0]], p1 = rows[q[1]], p2 = rows[q2];
+      const int qs[3] = {q[0], q[1], q2};
+      auto seed64 = [&](int i) { return R.at(qs[i]); };
+      // 2D minimal sets are mildly conditioned (|det| = |sin(t1 - t0)|): their
+      // wide bands are rare and cheaper than refining; 3D trials refine
+      Hyp32 hy = hyp_f32<DIM>(p0, p1, p2, seed64, DIM == 3, wmax, a.acc, a.rej, a.tau32);
       if (hy.kind == kHypUndecided) {
         ++n_fp64;
         double v[3];
-        if (hyp_f64<DIM>(a, o, ci, hc0 + hl, N, v)) {
-          hy = hyp_f32<DIM>(p0, p1, p2, wmax, 0.0f, 0.0f, a.tau32);
-          if (hy.kind != kHypNormal) hy.kind = kHypExactOnly;
-          if (hy.kind == kHypExactOnly) {
+        if (hyp_f64<DIM>(a, R, ci, hc0 + hl, N, v)) {
+          hy = hyp_f32<DIM>(p0, p1, p2, seed64, DIM == 3, wmax, 0.0f, 0.0f, a.tau32);
+          if (hy.kind != kHypNormal) {
+            hy.kind = kHypExactOnly;
             hy.thi = __int_as_float(0x7f800000);
             hy.tlo = -1.0f;
           }
@@ -307,6 +402,7 @@ __device__ void process_cluster(const FrameDesc& a, const Smem& S, ClusterShared
         }
       }
       if (hy.kind == kHypExactOnly) ++n_fp64;
+      n_ref += hy.refined;
       S.hyp[hl] = make_float4(hy.nx, hy.ny, hy.nz, hy.kind == kHypRejected ? __int_as_float(0x7fc00000) : hy.thi);
       S.tlo[hl] = hy.tlo;
       S.kind[hl] = (int8_t)hy.kind;
@@ -327,8 +423,8 @@ __device__ void process_cluster(const FrameDesc& a, const Smem& S, ClusterShared
     // strictly.
     int um = -1;
     for (int hl = tid; hl < nh; hl += kThreads) um = max(um, S.U[hl]);
-    const int Umax = block_max_int(um, cs.red_i);  // syncs after phase A's writes
-    const int lead = (int)(cs.best >> 32) - 1;     // best exact count so far (-1 none)
+    const int Umax = block_max_int(um, cs.red_i);
+    const int lead = (int)(cs.best >> 32) - 1;  // best exact count so far (-1 none)
     if (Umax >= 0 && Umax > lead) {
       for (int pass = 0; pass < 2; ++pass) {
         int prev = -1;
@@ -346,7 +442,7 @@ __device__ void process_cluster(const FrameDesc& a, const Smem& S, ClusterShared
           const float4 hy = S.hyp[c];
           const float htlo = S.tlo[c];
           int B = 0;
-          const int C = exact_count_block<DIM>(a, rows, o, ci, hc0 + c, N, hy, htlo, cs, &B);
+          const int C = exact_count_block<DIM>(a, rows, R, ci, hc0 + c, N, hy, htlo, cs, &B);
           ++n_cand;
           if (tid == 0) {
             const unsigned long long k = best_key(C, hc0 + c);
@@ -376,6 +472,7 @@ __device__ void process_cluster(const FrameDesc& a, const Smem& S, ClusterShared
 
   if (tid == 0) cs.ctr[0] += n_cand;
   if (n_fp64) atomicAdd(&cs.ctr[2], n_fp64);
+  if (n_ref) atomicAdd(&cs.ctr[3], n_ref);
 
   const unsigned long long key = cs.best;
   if (key == 0ull) {
@@ -398,34 +495,18 @@ __device__ void process_cluster(const FrameDesc& a, const Smem& S, ClusterShared
   for (int i = 0; i < NS; ++i) sums[i] = 0.0;
   int nin = 0;
   for (int j = tid; j < N; j += kThreads) {
-    const float4 p = rows[j];
-    const float r = fabsf(resid_f32<DIM>(p, win.x, win.y, win.z));
+    const float r = fabsf(resid_f32<DIM>(rows[j], win.x, win.y, win.z));
     bool in = r <= wtlo;
     const bool band = !in && !(r > win.w);
     if (in || band) {
-      double a64[3];
-      row_f64<DIM>(a.trig, a.az[o + j], DIM == 3 ? a.el[o + j] : 0.0f, a64);
-      const double w = (double)(DIM == 2 ? p.z : p.w);
-      if (band) in = fabs(residual_f64<DIM>(a64, w, v64)) <= a.tau;
+      const double4_32a s = R.at(j);
+      if (band) {
+        const double a64[3] = {s.x, s.y, s.z};
+        in = fabs(residual_f64<DIM>(a64, s.w, v64)) <= a.tau;
+      }
       if (in) {
         ++nin;
-        if (DIM == 2) {
-          sums[0] = fma(a64[0], a64[0], sums[0]);
-          sums[1] = fma(a64[0], a64[1], sums[1]);
-          sums[2] = fma(a64[1], a64[1], sums[2]);
-          sums[3] = fma(a64[0], w, sums[3]);
-          sums[4] = fma(a64[1], w, sums[4]);
-        } else {
-          sums[0] = fma(a64[0], a64[0], sums[0]);
-          sums[1] = fma(a64[0], a64[1], sums[1]);
-          sums[2] = fma(a64[0], a64[2], sums[2]);
-          sums[3] = fma(a64[1], a64[1], sums[3]);
-          sums[4] = fma(a64[1], a64[2], sums[4]);
-          sums[5] = fma(a64[2], a64[2], sums[5]);
-          sums[6] = fma(a64[0], w, sums[6]);
-          sums[7] = fma(a64[1], w, sums[7]);
-          sums[8] = fma(a64[2], w, sums[8]);
-        }
+        accumulate_row<DIM>(sums, s);
       }
     }
     a.mask[o + j] = in ? 1 : 0;
@@ -450,50 +531,7 @@ __device__ void process_cluster(const FrameDesc& a, const Smem& S, ClusterShared
 #pragma unroll
       for (int i = 0; i < NS; ++i) t[i] += cs.red_d[w][i];
     }
-    double vout[3] = {v64[0], v64[1], v64[2]};
-    auto minimal_velocity = [&]() {
-      if (!cs.win_has_v64) hyp_f64<DIM>(a, o, ci, hstar, N, vout);
-    };
-    int st = 0;
-    if (DIM == 2) {
-      const double tr = t[0] + t[2];
-      const double limit = 1e-12 * (tr * tr);
-      const double det = det2_f64(t[0], t[1], t[1], t[2]);
-      if (n_in >= 2 && fabs(det) > limit) {
-        const double G0[3] = {t[0], t[1], 0.0}, G1[3] = {t[1], t[2], 0.0}, g[3] = {t[3], t[4], 0.0};
-        double vs[3];
-        solve_f64<2>(G0, G1, nullptr, g, 0.0, vs, nullptr);
-        vout[0] = vs[0];
-        vout[1] = vs[1];
-        vout[2] = 0.0;
-      } else {
-        st |= RVH_STATUS_LSQ_FALLBACK;
-        minimal_velocity();
-      }
-    } else {
-      const double tr = t[0] + t[3] + t[5];
-      const double limit = 1e-12 * (tr * tr * tr);
-      const double G0[3] = {t[0], t[1], t[2]}, G1[3] = {t[1], t[3], t[4]}, G2[3] = {t[2], t[4], t[5]};
-      const double det = det3_f64(G0, G1, G2);
-      if (n_in >= 3 && fabs(det) > limit) {
-        const double g[3] = {t[6], t[7], t[8]};
-        double vs[3];
-        solve_f64<3>(G0, G1, G2, g, 0.0, vs, nullptr);
-        vout[0] = vs[0];
-        vout[1] = vs[1];
-        vout[2] = vs[2];
-      } else {
-        st |= RVH_STATUS_LSQ_FALLBACK;
-        minimal_velocity();
-      }
-    }
-    a.vx[ci] = vout[0];
-    a.vy[ci] = vout[1];
-    if (a.vz) a.vz[ci] = DIM == 3 ? vout[2] : 0.0;
-    a.heading[ci] = atan2(vout[1], vout[0]);
-    a.inlier_count[ci] = n_in;
-    a.best[ci] = hstar;
-    a.status[ci] = st;
+    finish_cluster<DIM>(a, R, ci, N, hstar, n_in, t, v64, cs.win_has_v64);
   }
   __syncthreads();
   stage_done(4);
@@ -513,8 +551,6 @@ __global__ void __launch_bounds__(kThreads, RVH_MIN_BLOCKS) fused_kernel(FusedAr
   S.tlo = reinterpret_cast<float*>(p);
   p += (size_t)a.hchunk * sizeof(float);
   S.U = reinterpret_cast<int*>(p);
-  p += (size_t)a.hchunk * sizeof(int);
-  S.cand = reinterpret_cast<int*>(p);
   p += (size_t)a.hchunk * sizeof(int);
   S.kind = reinterpret_cast<int8_t*>(p);
 
@@ -587,7 +623,7 @@ __global__ void worklist_kernel(FusedArgs a) {
 }
 
 size_t fused_smem_bytes(int nmax_smem, int hchunk) {
-  return (size_t)nmax_smem * sizeof(float4) + (size_t)hchunk * (sizeof(float4) + sizeof(float) + 2 * sizeof(int) + 1);
+  return (size_t)nmax_smem * sizeof(float4) + (size_t)hchunk * (sizeof(float4) + sizeof(float) + sizeof(int) + 1);
 }
 
 cudaError_t launch_worklist(const FusedArgs& a, cudaStream_t s) {

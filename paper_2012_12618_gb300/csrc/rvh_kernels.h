@@ -27,6 +27,7 @@ struct FrameDesc {
   int32_t H;
   int64_t n_points;
   float4* rows_g;            // [n_points] FP32 rows of clusters larger than nmax_smem
+  double4_32a* rows64_g;         // [n_points] FP64 rows (a0, a1, a2, w) of every point
   const double2* trig;       // (cos, sin)(k/128), k = -420..420
   double tau;
   double eps;
@@ -52,7 +53,7 @@ struct FusedArgs {
   int n_items;               // sum of n_clusters over the frames
   int2* worklist;            // [n_items] (frame, cluster), written by the worklist kernel
   int* work_counter;
-  unsigned long long* stats;  // [4 + 6]: candidates, band points, fp64 trials, reserved, phase cycles
+  unsigned long long* stats;  // [4 + 6]: exact counts, band points, fp64 trials, refined trials, stage cycles
   int nmax_smem;
   int hchunk;
   int pw, hpl;

@@ -3,7 +3,7 @@
 // forbid allocation after start-up, or plugins whose host framework owns all
 // device memory).  It runs the same worklist and fused kernels as
 // rvh_estimate, with their scratch (work list, work counter, FP32 rows of
-// large clusters) and the FP64 row table in file-scope device arrays of fixed
+// large clusters, FP64 rows) and the FP64 row table in file-scope device arrays of fixed
 // size instead of context memory.  It calls no cudaMalloc, cudaFree or other
 // allocating routine.
 #include <algorithm>
@@ -25,7 +25,8 @@ constexpr int32_t kMaxClusters = RVH_NOALLOC_MAX_CLUSTERS;
 constexpr size_t kWorklistBytes = sizeof(int2) * (size_t)kMaxClusters;
 constexpr size_t kCounterBytes = 256;
 constexpr size_t kRowsBytes = sizeof(float4) * (size_t)kMaxPoints;
-constexpr size_t kScratchBytes = kWorklistBytes + kCounterBytes + kRowsBytes;
+constexpr size_t kRows64Bytes = sizeof(double4_32a) * (size_t)kMaxPoints;
+constexpr size_t kScratchBytes = kWorklistBytes + kCounterBytes + kRowsBytes + kRows64Bytes;
 constexpr int kNmaxSmem = 1536;
 constexpr int kHchunk = 1024;
 
@@ -128,7 +129,7 @@ extern "C" int rvh_estimate_noalloc(const rvh_frame* f, const rvh_params* p, rvh
   memset(&a, 0, sizeof(a));
   rvh::FrameDesc& fd = a.f[0];
   const double eps = p->cond_eps > 0 ? p->cond_eps : (dim == 2 ? 1e-4 : 1e-6);
-  const double eD = (dim == 2 ? 1.081e-6 : 6.20e-6) + 0x1p-50;
+  const double eD = (dim == 2 ? 5.98e-7 : 3.65e-6) + 0x1p-50;
   fd.az = f->azimuth;
   fd.el = f->elevation;
   fd.dop = f->doppler;
@@ -137,6 +138,7 @@ extern "C" int rvh_estimate_noalloc(const rvh_frame* f, const rvh_params* p, rvh
   fd.H = p->num_hypotheses;
   fd.n_points = f->n_points;
   fd.rows_g = (float4*)(d->scratch + kWorklistBytes + kCounterBytes);
+  fd.rows64_g = (double4_32a*)(d->scratch + kWorklistBytes + kCounterBytes + kRowsBytes);
   fd.trig = d->trig;
   fd.tau = p->inlier_threshold;
   fd.eps = eps;

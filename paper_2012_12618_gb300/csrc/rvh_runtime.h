@@ -22,7 +22,8 @@ bool device_ptr(const void* p);
 int validate_host_offsets(const int32_t* off, int32_t n, int64_t n_points);
 void choose_schedule(rvh_ctx* ctx, int H, int* pw, int* hpl);
 void fill_desc(rvh_ctx* ctx, FrameDesc& d, const rvh_frame& f, const rvh_params& p, const float* az,
-               const float* el, const float* dop, const int32_t* off, float4* rows_g, const rvh_result& out);
+               const float* el, const float* dop, const int32_t* off, float4* rows_g, double4_32a* rows64_g,
+               const rvh_result& out);
 int launch_batch(rvh_ctx* ctx, FusedArgs& a, int dim, cudaStream_t s, cudaEvent_t t0, cudaEvent_t t1);
 
 // serving loop (rvh_server.cu)

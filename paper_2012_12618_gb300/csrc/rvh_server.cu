@@ -87,6 +87,7 @@ struct Req {
   size_t dev_off = 0, dev_bytes = 0;
   size_t pin_off = 0, pin_bytes = 0;
   size_t pin_out[8] = {};
+  size_t rows64_off = 0;
   cudaEvent_t copied = nullptr;  // host inputs are on the device
   int step = -1;
   int state = 0;            // 0 queued, 1 launched, 2 done
@@ -235,6 +236,8 @@ int server_submit(Server* s, const rvh_frame* f, const rvh_params* p, rvh_result
     return o;
   };
   const size_t o_rows = take(sizeof(float4) * (size_t)std::max<int64_t>(np, 1));
+  const size_t o_rows64 = take(sizeof(double4_32a) * (size_t)std::max<int64_t>(np, 1));
+  (void)o_rows;
   const size_t o_az = d_az ? 0 : take(4 * (size_t)np);
   const size_t o_el = d_el ? 0 : take(4 * (size_t)np);
   const size_t o_dop = d_dop ? 0 : take(4 * (size_t)np);
@@ -261,6 +264,7 @@ int server_submit(Server* s, const rvh_frame* f, const rvh_params* p, rvh_result
     }
     q->dev_bytes = off;
     q->pin_bytes = pin;
+    q->rows64_off = o_rows64;
   }
   char* b = (char*)s->pool + q->dev_off;
   q->frame = *f;
@@ -406,7 +410,7 @@ void Server::loop() {
       Req& q = *reqs[id];
       char* b = (char*)pool + q.dev_off;
       fill_desc(ctx, a.f[nf], q.frame, q.params, q.frame.azimuth, q.frame.elevation, q.frame.doppler,
-                q.frame.cluster_offsets, (float4*)b, q.dev);
+                q.frame.cluster_offsets, (float4*)b, (double4_32a*)(b + q.rows64_off), q.dev);
       cudaStreamWaitEvent(slot->stream, q.copied, 0);
       ++nf;
     }

@@ -26,7 +26,7 @@ RVH_STATUS_ALL_DEGENERATE = 2
 RVH_STATUS_LSQ_FALLBACK = 4
 RVH_STATUS_BAD_OFFSETS = 8
 
-RVH_NOALLOC_MAX_POINTS = 2097152
+RVH_NOALLOC_MAX_POINTS = 1048576
 RVH_NOALLOC_MAX_CLUSTERS = 65536
 
 
@@ -52,7 +52,8 @@ class rvh_stats(ctypes.Structure):
     _fields_ = [("hypotheses", ctypes.c_int64), ("pair_evals", ctypes.c_int64), ("candidates", ctypes.c_int64),
                 ("band_points", ctypes.c_int64), ("fp64_hypotheses", ctypes.c_int64),
                 ("kernel_ms", ctypes.c_float), ("grid", ctypes.c_int32), ("points_per_warp", ctypes.c_int32),
-                ("hyps_per_lane", ctypes.c_int32), ("phase_cycles", ctypes.c_int64 * 6)]
+                ("hyps_per_lane", ctypes.c_int32), ("phase_cycles", ctypes.c_int64 * 6),
+                ("refined_hypotheses", ctypes.c_int64)]
 
 
 # exported symbols and their ctypes signatures (restype, argtypes)

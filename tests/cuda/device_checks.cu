@@ -2,7 +2,7 @@
 // by tests/test_device_checks.py with the library's own flags (-fmad=false).
 //
 //   rows     every float t in [-pi, pi]: |sincosf - sincos(double)| relative
-//            error (the filter assumes <= 2^-21; this reports the maximum);
+//            error (the filter assumes <= 2^-22; this reports the maximum);
 //            the table-based FP64 sincos against the library sincos (absolute
 //            difference in units of 2^-53).
 //   filter   random and adversarial minimal sets and points: wherever the FP32
@@ -101,12 +101,20 @@ __global__ void k_filter(const double2* trig, int n_hyp, int pts_per_hyp, unsign
   float4 r[3];
   for (int k = 0; k < DIM; ++k) r[k] = row_f32<DIM>(az[k], el[k], w[k]);
   const TauPair tau = {0.1f, 0.1f};
-  Hyp32 hy = hyp_f32<DIM>(r[0], r[1], DIM == 3 ? r[2] : r[0], wmax, 0.0f, 0.0f, tau);
-  if (hy.kind != kHypNormal) return;
   double a0[3], a1[3], a2[3] = {0, 0, 0};
   row_f64<DIM>(trig, az[0], el[0], a0);
   row_f64<DIM>(trig, az[1], el[1], a1);
   if (DIM == 3) row_f64<DIM>(trig, az[2], el[2], a2);
+  // the FP64 rows the library keeps per point: (a0, a1, a2, w)
+  const double4_32a s64[3] = {make_double4_32a(a0[0], a0[1], a0[2], (double)w[0]),
+                              make_double4_32a(a1[0], a1[1], a1[2], (double)w[1]),
+                              make_double4_32a(a2[0], a2[1], a2[2], DIM == 3 ? (double)w[2] : 0.0)};
+  // odd trials run without the refinement step, even ones with it when it applies
+  const bool refine = (gid & 1) == 0;
+  auto seed64 = [&](int i) { return s64[i]; };
+  Hyp32 hy = hyp_f32<DIM>(r[0], r[1], DIM == 3 ? r[2] : r[0], seed64, refine, wmax, 0.0f, 0.0f, tau);
+  if (hy.kind != kHypNormal) return;
+  if (hy.refined) atomicAdd(&g_viol[3], 1ull);
   const double wd[3] = {w[0], w[1], DIM == 3 ? (double)w[2] : 0.0};
   double v[3];
   if (!solve_f64<DIM>(a0, a1, a2, wd, 0.0, v, nullptr)) return;
@@ -188,7 +196,8 @@ int main(int argc, char** argv) {
     unsigned long long cnt, v[4];
     CK(cudaMemcpyFromSymbol(&cnt, g_count, 8));
     CK(cudaMemcpyFromSymbol(v, g_viol, 32));
-    printf("mode=filter pairs=%llu bad_in=%llu bad_out=%llu bound_exceeded=%llu\n", cnt, v[0], v[1], v[2]);
+    printf("mode=filter pairs=%llu bad_in=%llu bad_out=%llu bound_exceeded=%llu refined_trials=%llu\n", cnt, v[0],
+           v[1], v[2], v[3]);
   }
   CK(cudaFree(trig));
   return 0;

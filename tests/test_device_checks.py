@@ -1,12 +1,13 @@
 """Device-level checks of the FP32 filter's assumptions (GPU).
 
 Builds tests/cuda/device_checks.cu with the library's compiler flags and runs:
-  rows    every float in [-pi, pi]: sincosf within 2^-22 relative of the FP64
-          value (the filter's bound assumes 2^-21, twice that), and the
+  rows    every float in [-pi, pi]: sincosf within 2^-23 relative of the FP64
+          value (the filter's bound assumes 2^-22, twice that), and the
           table-based FP64 sincos within 4 * 2^-53 (absolute) of the library's;
   filter  ~10^8 (trial, point) pairs of ordinary, near-degenerate and
-          large-velocity minimal sets: no FP32 'certainly in/out' decision
-          disagrees with FP64, and |r32 - r64| never exceeds the band.
+          large-velocity minimal sets, with and without the refinement step:
+          no FP32 'certainly in/out' decision disagrees with FP64, and
+          |r32 - r64| never exceeds the band.
 """
 import os
 import re
@@ -40,7 +41,7 @@ def _run(exe, *args):
 def test_row_accuracy_exhaustive(exe):
     d = _run(exe, "rows")
     assert int(d["count"]) > 2_000_000_000
-    assert float(d["max_rel_sincosf"]) <= 2.0 ** -22, d
+    assert float(d["max_rel_sincosf"]) <= 2.0 ** -23, d
     assert int(d["table_vs_sincos_max_abs_2^-53"]) <= 4, d
 
 
@@ -48,3 +49,4 @@ def test_filter_soundness(exe):
     d = _run(exe, "filter", str(1 << 19), "128")
     assert int(d["pairs"]) > 10_000_000
     assert int(d["bad_in"]) == 0 and int(d["bad_out"]) == 0 and int(d["bound_exceeded"]) == 0, d
+    assert int(d["refined_trials"]) > 1000, d  # the refinement step is exercised
