@@ -43,7 +43,7 @@ def kernel_hash() -> str:
 def recorded_traffic():
     """DRAM bytes per fused launch from the committed ncu summary, if it was
     taken on the current kernel source (else None)."""
-    path = os.path.join(ROOT, "profiles", "fused_dense2d_traffic.json")
+    path = os.path.join(ROOT, "profiles", "fused_dense2d_traffic.txt")
     try:
         rec = json.load(open(path))
     except (OSError, ValueError):
