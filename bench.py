@@ -154,6 +154,8 @@ def main():
                     help="dense2d is the headline workload; the others are the precision, 3D and small-frame cases")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-gpu-baseline", action="store_true")
+    ap.add_argument("--schedule", default="",
+                    help="points_per_warp,hyps_per_lane for the scoring pass (default: the library's choice)")
     ap.add_argument("--serving-seconds", type=float, default=3.0,
                     help="measured seconds of the 64-radar serving load (0 skips it)")
     args = ap.parse_args()
@@ -179,6 +181,9 @@ def main():
     pairs = int(sizes.sum()) * w.num_hypotheses
 
     ctx = rvh.Context(local)
+    if args.schedule:
+        pw, hpl = (int(x) for x in args.schedule.split(","))
+        ctx.check(rvh.rvh_set_schedule(ctx.handle, pw, hpl), "rvh_set_schedule")
     d_az = torch.from_numpy(f.azimuth).to(dev)
     d_el = None if f.elevation is None else torch.from_numpy(f.elevation).to(dev)
     d_dop = torch.from_numpy(f.doppler).to(dev)

@@ -511,14 +511,26 @@ __device__ void process_cluster(const FrameDesc& a, const Smem& S, ClusterShared
     }
     a.mask[o + j] = in ? 1 : 0;
   }
+  // Reduce the per-thread sums through shared memory (the trial area is free
+  // now): only threads that held points contribute, and each of NS * 8
+  // threads adds one 32-thread slice, a fifth of the FP64 adds of a shuffle
+  // tree (FP64 runs at 1/64 of the FP32 rate on this GPU).
   const int warp = tid >> 5, lane = tid & 31;
   nin = warp_sum(nin);
+  const int nact = min(N, kThreads);
+  double* red = reinterpret_cast<double*>(S.hyp);  // NS x kThreads
+  if (tid < nact) {
 #pragma unroll
-  for (int i = 0; i < NS; ++i) sums[i] = warp_sum(sums[i]);
-  if (lane == 0) {
-    cs.red_i[warp] = nin;
-#pragma unroll
-    for (int i = 0; i < NS; ++i) cs.red_d[warp][i] = sums[i];
+    for (int i = 0; i < NS; ++i) red[i * kThreads + tid] = sums[i];
+  }
+  if (lane == 0) cs.red_i[warp] = nin;
+  __syncthreads();
+  if (tid < NS * kWarps) {
+    const int i = tid / kWarps, seg = tid % kWarps;
+    const int lo = seg * 32, hi = min(lo + 32, nact);
+    double acc = 0.0;
+    for (int k = lo; k < hi; ++k) acc += red[i * kThreads + k];
+    cs.red_d[seg][i] = acc;
   }
   __syncthreads();
   if (tid == 0) {
@@ -528,8 +540,10 @@ __device__ void process_cluster(const FrameDesc& a, const Smem& S, ClusterShared
     for (int i = 0; i < NS; ++i) t[i] = 0.0;
     for (int w = 0; w < kWarps; ++w) {
       n_in += cs.red_i[w];
+      if (w * 32 < nact) {
 #pragma unroll
-      for (int i = 0; i < NS; ++i) t[i] += cs.red_d[w][i];
+        for (int i = 0; i < NS; ++i) t[i] += cs.red_d[w][i];
+      }
     }
     finish_cluster<DIM>(a, R, ci, N, hstar, n_in, t, v64, cs.win_has_v64);
   }
@@ -623,7 +637,10 @@ __global__ void worklist_kernel(FusedArgs a) {
 }
 
 size_t fused_smem_bytes(int nmax_smem, int hchunk) {
-  return (size_t)nmax_smem * sizeof(float4) + (size_t)hchunk * (sizeof(float4) + sizeof(float) + sizeof(int) + 1);
+  // the trial area also holds the final reduction (up to 9 sums per thread)
+  const size_t trials = (size_t)hchunk * (sizeof(float4) + sizeof(float) + sizeof(int) + 1);
+  const size_t reduction = (size_t)9 * kThreads * sizeof(double);
+  return (size_t)nmax_smem * sizeof(float4) + (trials > reduction ? trials : reduction);
 }
 
 cudaError_t launch_worklist(const FusedArgs& a, cudaStream_t s) {
@@ -647,5 +664,6 @@ cudaError_t launch_fused(int dim, const FusedArgs& a, int grid, size_t smem, cud
   else fused_kernel<3><<<grid, kThreads, smem, s>>>(a);
   return cudaGetLastError();
 }
+
 
 }  // namespace rvh
