@@ -202,6 +202,11 @@ def main():
     def step():
         ctx.check(rvh.rvh_estimate(ctx.handle, frame, params, res, sptr), "rvh_estimate")
 
+    # the scoring schedule is picked by the library's autotuner on this workload (untimed)
+    tuned = rvh.rvh_schedule()
+    if not args.schedule:
+        ctx.check(rvh.rvh_autotune(ctx.handle, frame, params, res, 2, tuned), "rvh_autotune")
+
     for _ in range(max(args.warmup, 3)):
         flush.fill_(1)
         step()
@@ -356,7 +361,8 @@ def main():
                      "refined_trials_per_step": refined / args.steps,
                      "band_rate_per_pair": band / args.steps / pairs},
             "schedule": {"grid": grid, "points_per_warp": stats.points_per_warp,
-                         "hyps_per_lane": stats.hyps_per_lane},
+                         "hyps_per_lane": stats.hyps_per_lane, "autotuned": not args.schedule,
+                         "cuda_graph_replays": stats.graph_replays},
             "stage_share": dict(zip(["rows", "hypotheses", "scoring", "exact_rescoring", "mask_refine", "other"],
                                     [round(float(x), 4) for x in phase / max(phase.sum(), 1.0)])),
             "wall_s": wall,

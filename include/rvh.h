@@ -127,7 +127,10 @@ void rvh_destroy(rvh_ctx* ctx);
  * memory, inputs are copied in and outputs copied back inside the call,
  * which returns after the stream has completed.  A context's scratch is
  * reused across calls; calls on one context are serialised on the device
- * (a later call waits for the previous one). */
+ * (a later call waits for the previous one).  In the all-device case on a
+ * stream that is not being captured, the fused kernel launch is captured
+ * once into a CUDA graph and replayed while the arguments stay the same
+ * (environment RVH_GRAPHS=0 turns this off). */
 int rvh_estimate(rvh_ctx* ctx, const rvh_frame* frame, const rvh_params* params,
                  rvh_result* result, void* stream);
 
@@ -200,6 +203,7 @@ typedef struct {
    * winner mask + refine, scheduling/other. */
   int64_t phase_cycles[6];
   int64_t refined_hypotheses;  /* trials whose FP32 solve took one refinement step */
+  int64_t graph_replays;       /* rvh_estimate calls served by replaying a captured CUDA graph */
 } rvh_stats;
 
 /* Counters of the last rvh_estimate on this context (synchronises its stream). */
@@ -209,6 +213,25 @@ int rvh_get_stats(rvh_ctx* ctx, rvh_stats* out);
  * per trial group) and hyps_per_lane in {4, 8}; 0 restores the automatic
  * choice. */
 int rvh_set_schedule(rvh_ctx* ctx, int32_t points_per_warp, int32_t hyps_per_lane);
+
+/* A scoring schedule and its measured fused-kernel time. */
+typedef struct {
+  int32_t points_per_warp;
+  int32_t hyps_per_lane;
+  float kernel_ms;
+} rvh_schedule;
+
+/* Autotuner: runs the fused kernel on this frame with every scoring schedule
+ * (points_per_warp in {1, 8, 32} x hyps_per_lane in {4, 8}), `reps` timed
+ * runs each after one warm-up (CUDA events on the context's stream), and
+ * keeps the fastest for frames of this model dimension and trial-count
+ * bucket (floor(log2 H)); later calls pick it automatically unless
+ * rvh_set_schedule fixed one.  `result` receives the frame's outputs.  When
+ * the environment variable RVH_TUNE_CACHE names a file, choices are loaded
+ * from it by rvh_create (entries keyed by GPU name, SM count, model and
+ * bucket) and saved to it here.  *best (may be NULL) receives the choice. */
+int rvh_autotune(rvh_ctx* ctx, const rvh_frame* frame, const rvh_params* params, rvh_result* result,
+                 int32_t reps, rvh_schedule* best);
 
 #ifdef __cplusplus
 }

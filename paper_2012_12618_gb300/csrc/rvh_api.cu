@@ -5,6 +5,7 @@
 #include <chrono>
 #include <cmath>
 #include <condition_variable>
+#include <cstdio>
 #include <cstdlib>
 #include <cstring>
 #include <deque>
@@ -122,6 +123,14 @@ struct rvh_ctx {
   std::mutex mu;  // serialises rvh_estimate calls on this context
   rvh::Server* server = nullptr;
   double2* trig = nullptr;  // device table of (cos, sin)(k/128)
+  std::map<int, std::pair<int, int>> tuned;  // (dim << 8 | log2 H) -> (pw, hpl)
+  // CUDA graph of the last all-device launch sequence, replayed while its
+  // arguments stay the same
+  bool graphs = true;
+  cudaGraphExec_t gexec = nullptr;
+  std::vector<char> gkey;
+  int64_t graph_replays = 0;
+  std::string tune_prefix;                    // "<gpu name>|<sms>|"
 };
 
 namespace rvh {
@@ -148,10 +157,22 @@ void ctx_free(rvh_ctx* ctx, void* p, size_t bytes) {
 int ctx_device(rvh_ctx* ctx) { return ctx->device; }
 int ctx_sms(rvh_ctx* ctx) { return ctx->sms; }
 
-void choose_schedule(rvh_ctx* ctx, int H, int* pw, int* hpl) {
+int tune_key(int dim, int H) {
+  int b = 0;
+  while ((H >> (b + 1)) > 0) ++b;
+  return dim << 8 | b;
+}
+
+void choose_schedule(rvh_ctx* ctx, int dim, int H, int* pw, int* hpl) {
   if (ctx->pw_fixed) {
     *pw = ctx->pw_fixed;
     *hpl = ctx->hpl_fixed ? ctx->hpl_fixed : 4;
+    return;
+  }
+  auto it = ctx->tuned.find(tune_key(dim, H));
+  if (it != ctx->tuned.end()) {
+    *pw = it->second.first;
+    *hpl = it->second.second;
     return;
   }
   if (H >= 1024) {
@@ -207,20 +228,113 @@ int configure_dim(rvh_ctx* ctx, int dim) {
   return RVH_OK;
 }
 
-// Launches worklist + fused kernel for a prepared batch.
-int launch_batch(rvh_ctx* ctx, FusedArgs& a, int dim, cudaStream_t s, cudaEvent_t t0, cudaEvent_t t1) {
+// Grid, shared memory and item mapping of a batch launch.
+int prepare_launch(rvh_ctx* ctx, FusedArgs& a, int dim, int* grid, size_t* smem) {
   int rc = configure_dim(ctx, dim);
   if (rc) return rc;
-  const size_t smem = fused_smem_bytes(ctx->nmax_smem, ctx->hchunk);
+  *smem = fused_smem_bytes(ctx->nmax_smem, ctx->hchunk);
   a.nmax_smem = ctx->nmax_smem;
   a.hchunk = ctx->hchunk;
-  const int grid = std::max(1, std::min(ctx->sms * ctx->occ[dim], a.n_items));
-  RVH_CUDA(launch_worklist(a, s));
+  const int resident = ctx->sms * ctx->occ[dim];
+  *grid = std::max(1, std::min(resident, a.n_items));
+  // when every item gets its own resident CTA the order cannot matter: skip
+  // the work-list kernel
+  a.direct = a.n_items <= resident ? 1 : 0;
+  return RVH_OK;
+}
+
+// Launches worklist + fused kernel for a prepared batch.
+int launch_batch(rvh_ctx* ctx, FusedArgs& a, int dim, cudaStream_t s, cudaEvent_t t0, cudaEvent_t t1) {
+  int grid = 1;
+  size_t smem = 0;
+  int rc = prepare_launch(ctx, a, dim, &grid, &smem);
+  if (rc) return rc;
+  if (!a.direct) RVH_CUDA(launch_worklist(a, s));
   if (t0) RVH_CUDA(cudaEventRecord(t0, s));
   RVH_CUDA(launch_fused(dim, a, grid, smem, s));
   if (t1) RVH_CUDA(cudaEventRecord(t1, s));
   ctx->last.grid = grid;
   return RVH_OK;
+}
+
+// Launches the fused kernel through a CUDA graph: the kernel (with its
+// ~6 KB argument block) is captured once and replayed while the arguments
+// equal those of the capture.  The stats reset, the work-list kernel and the
+// timing events stay outside the graph, so the events time the fused kernel.
+int launch_graph(rvh_ctx* ctx, FusedArgs& a, int dim, cudaStream_t s) {
+  int grid = 1;
+  size_t smem = 0;
+  int rc = prepare_launch(ctx, a, dim, &grid, &smem);
+  if (rc) return rc;
+  RVH_CUDA(cudaMemsetAsync(a.stats, 0, 80, s));
+  if (!a.direct) RVH_CUDA(launch_worklist(a, s));
+  std::vector<char> key(sizeof(FusedArgs) + 3 * sizeof(int64_t));
+  memcpy(key.data(), &a, sizeof(FusedArgs));
+  const int64_t extra[3] = {dim, grid, (int64_t)smem};
+  memcpy(key.data() + sizeof(FusedArgs), extra, sizeof(extra));
+  if (!(ctx->gexec && key == ctx->gkey)) {
+    RVH_CUDA(cudaStreamBeginCapture(s, cudaStreamCaptureModeThreadLocal));
+    cudaError_t e = launch_fused(dim, a, grid, smem, s);
+    cudaGraph_t g = nullptr;
+    const cudaError_t ee = cudaStreamEndCapture(s, &g);
+    if (e == cudaSuccess) e = ee;
+    cudaGraphExec_t exec = nullptr;
+    if (e == cudaSuccess) e = cudaGraphInstantiate(&exec, g, 0);
+    if (g) cudaGraphDestroy(g);
+    if (e != cudaSuccess) {
+      cudaGetLastError();
+      return fail(RVH_ECUDA, std::string("graph capture: ") + cudaGetErrorString(e));
+    }
+    if (ctx->gexec) cudaGraphExecDestroy(ctx->gexec);
+    ctx->gexec = exec;
+    ctx->gkey.swap(key);
+  } else {
+    ++ctx->graph_replays;
+  }
+  RVH_CUDA(cudaEventRecord(ctx->ev0, s));
+  RVH_CUDA(cudaGraphLaunch(ctx->gexec, s));
+  RVH_CUDA(cudaEventRecord(ctx->ev1, s));
+  ctx->last.grid = grid;
+  return RVH_OK;
+}
+
+// Tune cache: one line per choice, "<gpu>|<sms>|<dim>|<log2 H> <pw> <hpl> <ms>".
+void load_tune_cache(rvh_ctx* ctx) {
+  const char* path = getenv("RVH_TUNE_CACHE");
+  if (!path || !*path) return;
+  FILE* f = fopen(path, "r");
+  if (!f) return;
+  char line[512];
+  while (fgets(line, sizeof(line), f)) {
+    std::string l(line);
+    if (l.compare(0, ctx->tune_prefix.size(), ctx->tune_prefix) != 0) continue;
+    int dim = 0, b = 0, pw = 0, hpl = 0;
+    float ms = 0.f;
+    if (sscanf(l.c_str() + ctx->tune_prefix.size(), "%d|%d %d %d %f", &dim, &b, &pw, &hpl, &ms) == 5 &&
+        (pw == 1 || pw == 8 || pw == 32) && (hpl == 4 || hpl == 8))
+      ctx->tuned[dim << 8 | b] = std::make_pair(pw, hpl);
+  }
+  fclose(f);
+}
+
+void save_tune_cache(rvh_ctx* ctx, int key, int pw, int hpl, float ms) {
+  const char* path = getenv("RVH_TUNE_CACHE");
+  if (!path || !*path) return;
+  std::vector<std::string> keep;
+  const std::string mine = ctx->tune_prefix + std::to_string(key >> 8) + "|" + std::to_string(key & 255) + " ";
+  if (FILE* f = fopen(path, "r")) {
+    char line[512];
+    while (fgets(line, sizeof(line), f)) {
+      std::string l(line);
+      if (l.compare(0, mine.size(), mine) != 0) keep.push_back(l);
+    }
+    fclose(f);
+  }
+  if (FILE* f = fopen(path, "w")) {
+    for (auto& l : keep) fputs(l.c_str(), f);
+    fprintf(f, "%s%d %d %.6f\n", mine.c_str(), pw, hpl, ms);
+    fclose(f);
+  }
 }
 
 }  // namespace rvh
@@ -247,6 +361,7 @@ int rvh_create(rvh_ctx** out, int device, size_t mem_budget_bytes) {
   // tuning knobs for experiments: shared-memory row capacity and trial chunk
   if (const char* e = getenv("RVH_NMAX_SMEM")) c->nmax_smem = std::max(64, atoi(e));
   if (const char* e = getenv("RVH_HCHUNK")) c->hchunk = std::max(64, atoi(e));
+  if (const char* e = getenv("RVH_GRAPHS")) c->graphs = atoi(e) != 0;
   if (cudaStreamCreateWithFlags(&c->stream, cudaStreamNonBlocking) != cudaSuccess ||
       cudaEventCreateWithFlags(&c->last_done, cudaEventDisableTiming) != cudaSuccess ||
       cudaEventCreate(&c->ev0) != cudaSuccess || cudaEventCreate(&c->ev1) != cudaSuccess) {
@@ -272,6 +387,14 @@ int rvh_create(rvh_ctx** out, int device, size_t mem_budget_bytes) {
     }
     c->trig = (double2*)p;
   }
+  {
+    cudaDeviceProp prop;
+    if (cudaGetDeviceProperties(&prop, device) == cudaSuccess)
+      c->tune_prefix = std::string(prop.name) + "|" + std::to_string(c->sms) + "|";
+    else
+      cudaGetLastError();
+    load_tune_cache(c);
+  }
   *out = c;
   return RVH_OK;
 }
@@ -281,6 +404,7 @@ void rvh_destroy(rvh_ctx* ctx) {
   cudaSetDevice(ctx->device);
   if (ctx->server) server_destroy(ctx->server);
   cudaStreamSynchronize(ctx->stream);
+  if (ctx->gexec) cudaGraphExecDestroy(ctx->gexec);
   if (ctx->scratch) ctx_free(ctx, ctx->scratch, ctx->scratch_bytes);
   if (ctx->trig) ctx_free(ctx, ctx->trig, sizeof(double2) * kTrigSize);
   cudaEventDestroy(ctx->last_done);
@@ -311,6 +435,7 @@ int rvh_get_stats(rvh_ctx* ctx, rvh_stats* out) {
     RVH_CUDA(cudaMemcpy(h, ctx->stats_d, sizeof(h), cudaMemcpyDeviceToHost));
     for (int k = 0; k < 6; ++k) ctx->last.phase_cycles[k] = (int64_t)h[4 + k];
     ctx->last.refined_hypotheses = (int64_t)h[3];
+    ctx->last.graph_replays = ctx->graph_replays;
     ctx->last.candidates = (int64_t)h[0];
     ctx->last.band_points = (int64_t)h[1];
     ctx->last.fp64_hypotheses = (int64_t)h[2];
@@ -330,6 +455,7 @@ struct Staged {
   const int32_t* off;
   rvh_result dev_out;       // device pointers the kernel writes
   bool host_out[8];
+  bool staged_any;          // some input or output went through host memory
   char* base;
   int2* worklist;
   int* counter;
@@ -353,6 +479,8 @@ static int stage(rvh_ctx* ctx, const rvh_frame* f, const rvh_params* p, rvh_resu
   void* outs[8] = {r->vx, r->vy, r->vz, r->heading, r->inlier_count, r->best_hypothesis, r->status, r->inlier_mask};
   const size_t osz[8] = {8, 8, 8, 8, 4, 4, 4, 1};
   for (int i = 0; i < 8; ++i) st.host_out[i] = outs[i] && !is_device_ptr(outs[i]);
+  st.staged_any = !(d_az && d_dop && d_el && d_off);
+  for (int i = 0; i < 8; ++i) st.staged_any = st.staged_any || st.host_out[i];
   // layout
   size_t off = 0;
   auto take = [&](size_t bytes) {
@@ -445,7 +573,6 @@ int rvh_estimate(rvh_ctx* ctx, const rvh_frame* frame, const rvh_params* params,
   rc = stage(ctx, frame, params, result, s, true, st);
   if (rc) return rc;
   ctx->stats_d = st.stats;
-  RVH_CUDA(cudaMemsetAsync(st.stats, 0, 80, s));
   FusedArgs a;
   memset(&a, 0, sizeof(a));
   fill_desc(ctx, a.f[0], *frame, *params, st.az, st.el, st.dop, st.off, (float4*)st.rows, st.rows64, st.dev_out);
@@ -454,8 +581,15 @@ int rvh_estimate(rvh_ctx* ctx, const rvh_frame* frame, const rvh_params* params,
   a.worklist = st.worklist;
   a.work_counter = st.counter;
   a.stats = st.stats;
-  choose_schedule(ctx, params->num_hypotheses, &a.pw, &a.hpl);
-  rc = launch_batch(ctx, a, params->model_dim, s, ctx->ev0, ctx->ev1);
+  choose_schedule(ctx, params->model_dim, params->num_hypotheses, &a.pw, &a.hpl);
+  cudaStreamCaptureStatus cap = cudaStreamCaptureStatusNone;
+  RVH_CUDA(cudaStreamIsCapturing(s, &cap));
+  if (ctx->graphs && !st.staged_any && s != nullptr && cap == cudaStreamCaptureStatusNone) {
+    rc = launch_graph(ctx, a, params->model_dim, s);
+  } else {
+    RVH_CUDA(cudaMemsetAsync(st.stats, 0, 80, s));
+    rc = launch_batch(ctx, a, params->model_dim, s, ctx->ev0, ctx->ev1);
+  }
   if (rc) return rc;
   ctx->last.hypotheses = (int64_t)frame->n_clusters * params->num_hypotheses;
   ctx->last.pair_evals = frame->n_points * (int64_t)params->num_hypotheses;
@@ -515,6 +649,50 @@ int rvh_estimate_baseline(rvh_ctx* ctx, const rvh_frame* frame, const rvh_params
   rc = unstage(frame, result, st, s);
   RVH_CUDA(cudaEventRecord(ctx->last_done, s));
   return rc;
+}
+
+int rvh_autotune(rvh_ctx* ctx, const rvh_frame* frame, const rvh_params* params, rvh_result* result,
+                 int32_t reps, rvh_schedule* best) {
+  if (!ctx) return fail(RVH_EINVAL, "ctx is NULL");
+  if (reps < 1) return fail(RVH_EINVAL, "reps must be >= 1");
+  int rc = check_args(frame, params, result);
+  if (rc) return rc;
+  if (frame->n_clusters == 0) return fail(RVH_EINVAL, "empty frame");
+  static const int kCand[6][2] = {{1, 4}, {1, 8}, {8, 4}, {8, 8}, {32, 4}, {32, 8}};
+  const int save_pw = ctx->pw_fixed, save_hpl = ctx->hpl_fixed;
+  int bpw = 1, bhpl = 4;
+  float bms = 1e30f;
+  for (auto& c : kCand) {
+    ctx->pw_fixed = c[0];
+    ctx->hpl_fixed = c[1];
+    float tot = 0.f;
+    for (int r = 0; r <= reps && rc == RVH_OK; ++r) {
+      rc = rvh_estimate(ctx, frame, params, result, nullptr);
+      if (rc) break;
+      rvh_stats st;
+      rc = rvh_get_stats(ctx, &st);
+      if (r > 0) tot += st.kernel_ms;
+    }
+    if (rc) break;
+    const float ms = tot / reps;
+    if (ms < bms) {
+      bms = ms;
+      bpw = c[0];
+      bhpl = c[1];
+    }
+  }
+  ctx->pw_fixed = save_pw;
+  ctx->hpl_fixed = save_hpl;
+  if (rc) return rc;
+  const int key = tune_key(params->model_dim, params->num_hypotheses);
+  ctx->tuned[key] = std::make_pair(bpw, bhpl);
+  save_tune_cache(ctx, key, bpw, bhpl, bms);
+  if (best) {
+    best->points_per_warp = bpw;
+    best->hyps_per_lane = bhpl;
+    best->kernel_ms = bms;
+  }
+  return RVH_OK;
 }
 
 int rvh_submit(rvh_ctx* ctx, const rvh_frame* frame, const rvh_params* params, rvh_result* result,

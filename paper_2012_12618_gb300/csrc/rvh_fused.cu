@@ -571,13 +571,22 @@ __global__ void __launch_bounds__(kThreads, RVH_MIN_BLOCKS) fused_kernel(FusedAr
   if (threadIdx.x < 4) cs.ctr[threadIdx.x] = 0ull;
   if (threadIdx.x < 6) cs.clk[threadIdx.x] = 0ull;
   const long long t_kernel = clock64();
-  for (;;) {
+  for (int round = 0;; ++round) {
     __syncthreads();
-    if (threadIdx.x == 0) s_item = atomicAdd(a.work_counter, 1);
+    if (threadIdx.x == 0)
+      s_item = a.direct ? (round == 0 ? (int)blockIdx.x : a.n_items) : atomicAdd(a.work_counter, 1);
     __syncthreads();
     const int item = s_item;
     if (item >= a.n_items) break;
-    const int2 fc = a.worklist[item];
+    int2 fc;
+    if (a.direct) {
+      // as many CTAs as items: frame-major order needs no work list
+      int f = 0, rem = item;
+      while (rem >= a.f[f].n_clusters) rem -= a.f[f++].n_clusters;
+      fc = make_int2(f, rem);
+    } else {
+      fc = a.worklist[item];
+    }
     const FrameDesc& F = a.f[fc.x];
     const int ci = fc.y;
     const int64_t o = F.offsets[ci], e = F.offsets[ci + 1];

@@ -57,6 +57,7 @@ struct FusedArgs {
   int nmax_smem;
   int hchunk;
   int pw, hpl;
+  int direct;                // 1: one item per CTA, item = blockIdx.x (no work list)
 };
 
 size_t fused_smem_bytes(int nmax_smem, int hchunk);

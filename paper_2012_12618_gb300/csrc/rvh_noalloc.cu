@@ -170,9 +170,11 @@ extern "C" int rvh_estimate_noalloc(const rvh_frame* f, const rvh_params* p, rvh
     a.hpl = 4;
   }
   cudaStream_t s = (cudaStream_t)stream;
-  e = rvh::launch_worklist(a, s);
+  const int resident = d->sms * d->occ[dim];
+  a.direct = a.n_items <= resident ? 1 : 0;
+  e = a.direct ? cudaSuccess : rvh::launch_worklist(a, s);
   if (e == cudaSuccess) {
-    const int grid = std::max(1, std::min(d->sms * d->occ[dim], a.n_items));
+    const int grid = std::max(1, std::min(resident, a.n_items));
     e = rvh::launch_fused(dim, a, grid, rvh::fused_smem_bytes(kNmaxSmem, kHchunk), s);
   }
   if (e != cudaSuccess) return rvh::set_error(RVH_ECUDA, std::string("launch: ") + cudaGetErrorString(e));

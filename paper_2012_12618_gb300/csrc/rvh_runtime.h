@@ -20,7 +20,8 @@ int ctx_sms(rvh_ctx* ctx);
 int set_error(int code, const std::string& msg);
 bool device_ptr(const void* p);
 int validate_host_offsets(const int32_t* off, int32_t n, int64_t n_points);
-void choose_schedule(rvh_ctx* ctx, int H, int* pw, int* hpl);
+void choose_schedule(rvh_ctx* ctx, int dim, int H, int* pw, int* hpl);
+void load_tune_cache(rvh_ctx* ctx);
 void fill_desc(rvh_ctx* ctx, FrameDesc& d, const rvh_frame& f, const rvh_params& p, const float* az,
                const float* el, const float* dop, const int32_t* off, float4* rows_g, double4_32a* rows64_g,
                const rvh_result& out);

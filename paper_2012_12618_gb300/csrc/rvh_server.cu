@@ -421,7 +421,7 @@ void Server::loop() {
     a.stats = nullptr;
     int Hmax = 1;
     for (int i = 0; i < nf; ++i) Hmax = std::max(Hmax, a.f[i].H);
-    choose_schedule(ctx, Hmax, &a.pw, &a.hpl);
+    choose_schedule(ctx, dimsel ? 3 : 2, Hmax, &a.pw, &a.hpl);
     int rc = RVH_OK;
     if (n_items > 0) rc = launch_batch(ctx, a, dimsel ? 3 : 2, slot->stream, nullptr, nullptr);
     if (rc != RVH_OK) thread_error = "launch failed";

@@ -48,12 +48,17 @@ class rvh_result(ctypes.Structure):
                 ("inlier_mask", ctypes.c_void_p)]
 
 
+class rvh_schedule(ctypes.Structure):
+    _fields_ = [("points_per_warp", ctypes.c_int32), ("hyps_per_lane", ctypes.c_int32),
+                ("kernel_ms", ctypes.c_float)]
+
+
 class rvh_stats(ctypes.Structure):
     _fields_ = [("hypotheses", ctypes.c_int64), ("pair_evals", ctypes.c_int64), ("candidates", ctypes.c_int64),
                 ("band_points", ctypes.c_int64), ("fp64_hypotheses", ctypes.c_int64),
                 ("kernel_ms", ctypes.c_float), ("grid", ctypes.c_int32), ("points_per_warp", ctypes.c_int32),
                 ("hyps_per_lane", ctypes.c_int32), ("phase_cycles", ctypes.c_int64 * 6),
-                ("refined_hypotheses", ctypes.c_int64)]
+                ("refined_hypotheses", ctypes.c_int64), ("graph_replays", ctypes.c_int64)]
 
 
 # exported symbols and their ctypes signatures (restype, argtypes)
@@ -74,6 +79,8 @@ SIGNATURES = {
     "rvh_last_error": (ctypes.c_char_p, [_P]),
     "rvh_get_stats": (ctypes.c_int, [_P, ctypes.POINTER(rvh_stats)]),
     "rvh_set_schedule": (ctypes.c_int, [_P, ctypes.c_int32, ctypes.c_int32]),
+    "rvh_autotune": (ctypes.c_int, [_P, ctypes.POINTER(rvh_frame), ctypes.POINTER(rvh_params),
+                                    ctypes.POINTER(rvh_result), ctypes.c_int32, ctypes.POINTER(rvh_schedule)]),
 }
 
 _lib = None
@@ -142,6 +149,11 @@ def rvh_get_stats(ctx, out) -> int:
 
 def rvh_set_schedule(ctx, points_per_warp: int, hyps_per_lane: int) -> int:
     return load().rvh_set_schedule(ctx, points_per_warp, hyps_per_lane)
+
+
+def rvh_autotune(ctx, frame, params, result, reps: int, best) -> int:
+    return load().rvh_autotune(ctx, ctypes.byref(frame), ctypes.byref(params), ctypes.byref(result), reps,
+                               None if best is None else ctypes.byref(best))
 
 
 # ---- marshalling helpers ---------------------------------------------------------------

@@ -1,0 +1,101 @@
+"""Autotuner, CUDA-graph replay and the direct (no work list) launch (GPU).
+
+Whatever the schedule, the launch form or the replay, results stay those of
+the oracle (every schedule computes the same exact counts)."""
+import ctypes
+import os
+
+import numpy as np
+import pytest
+
+from paper_2012_12618_gb300 import rvh, synth
+from tests import gpu_util as G
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def torch():
+    t = pytest.importorskip("torch")
+    if not t.cuda.is_available():
+        pytest.skip("no CUDA device")
+    return t
+
+
+def _device_frame(torch, f):
+    dev = torch.device("cuda", 0)
+    t = [None if x is None else torch.from_numpy(x).to(dev) for x in (f.azimuth, f.elevation, f.doppler, f.offsets)]
+    return t, rvh.make_frame(t[0], t[2], t[3], t[1])
+
+
+def _np(outs, n):
+    d = {k: v.cpu().numpy() for k, v in outs.items()}
+    d["inlier_mask"] = d["inlier_mask"][:n]
+    return d
+
+
+def test_autotune_and_cache(torch, tmp_path, monkeypatch):
+    cache = tmp_path / "tune.txt"
+    monkeypatch.setenv("RVH_TUNE_CACHE", str(cache))
+    w = synth.WORKLOADS["dense2d"]
+    f = synth.make_frame(w, n_clusters=256, gen_seed=61)
+    keep, frame = _device_frame(torch, f)
+    params = rvh.make_params(2, 1024, w.tau, 3)
+    dev = torch.device("cuda", 0)
+    outs = rvh.alloc_outputs(f.n_clusters, f.n_points, dev)
+    ctx = rvh.Context(0)
+    try:
+        best = rvh.rvh_schedule()
+        ctx.check(rvh.rvh_autotune(ctx.handle, frame, params, rvh.make_result(outs), 2, best), "autotune")
+        assert best.points_per_warp in (1, 8, 32) and best.hyps_per_lane in (4, 8) and best.kernel_ms > 0
+        ctx.check(rvh.rvh_estimate(ctx.handle, frame, params, rvh.make_result(outs), None), "estimate")
+        torch.cuda.synchronize()
+        st = rvh.rvh_stats()
+        ctx.check(rvh.rvh_get_stats(ctx.handle, st), "stats")
+        assert (st.points_per_warp, st.hyps_per_lane) == (best.points_per_warp, best.hyps_per_lane)
+        g = _np(outs, f.n_points)
+    finally:
+        ctx.close()
+    o = G.run_oracle(f.azimuth, f.doppler, f.offsets, H=1024, tau=w.tau, seed=3)
+    rep = G.compare(g, o, f.offsets)
+    assert not rep["mismatch"], rep["mismatch"][:10]
+    text = cache.read_text()
+    assert f"|2|10 {best.points_per_warp} {best.hyps_per_lane} " in text
+    # a new context picks the cached choice up
+    ctx2 = rvh.Context(0)
+    try:
+        ctx2.check(rvh.rvh_estimate(ctx2.handle, frame, params, rvh.make_result(outs), None), "estimate")
+        st = rvh.rvh_stats()
+        ctx2.check(rvh.rvh_get_stats(ctx2.handle, st), "stats")
+        assert (st.points_per_warp, st.hyps_per_lane) == (best.points_per_warp, best.hyps_per_lane)
+    finally:
+        ctx2.close()
+
+
+def test_graph_replay_and_recapture(torch):
+    w = synth.WORKLOADS["frame64"]
+    f = synth.make_frame(w, n_clusters=64, gen_seed=62)
+    keep, frame = _device_frame(torch, f)
+    dev = torch.device("cuda", 0)
+    s = torch.cuda.Stream(dev)
+    sptr = ctypes.c_void_p(s.cuda_stream)
+    ctx = rvh.Context(0)
+    try:
+        results = []
+        for seed in (5, 5, 5, 9):
+            params = rvh.make_params(2, w.num_hypotheses, w.tau, seed)
+            outs = rvh.alloc_outputs(f.n_clusters, f.n_points, dev) if not results else results[-1][1]
+            ctx.check(rvh.rvh_estimate(ctx.handle, frame, params, rvh.make_result(outs), sptr), "estimate")
+            s.synchronize()
+            results.append((seed, outs, _np(outs, f.n_points)))
+        st = rvh.rvh_stats()
+        ctx.check(rvh.rvh_get_stats(ctx.handle, st), "stats")
+        assert st.graph_replays >= 2  # calls 2 and 3 replay the graph captured by call 1
+        for k in ("inlier_mask", "best_hypothesis", "vx"):
+            assert np.array_equal(results[0][2][k], results[2][2][k], equal_nan=True)
+    finally:
+        ctx.close()
+    for seed, _, g in (results[0], results[3]):
+        o = G.run_oracle(f.azimuth, f.doppler, f.offsets, H=w.num_hypotheses, tau=w.tau, seed=seed)
+        rep = G.compare(g, o, f.offsets)
+        assert not rep["mismatch"], (seed, rep["mismatch"][:10])
