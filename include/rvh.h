@@ -23,7 +23,7 @@
  *   - a point is an inlier of a trial iff |v_d - a.v| <= inlier_threshold;
  *   - the random minimal sets come from Philox4x32-10 (Salmon et al., SC'11)
  *     with key (seed low word, seed high word) and counter
- *     (hypothesis, cluster index within the frame, 0, 0); the first index is
+ *     (hypothesis, first_cluster + cluster index within the frame, 0, 0); the first index is
  *     floor(w0 * N / 2^32), the second floor(w1 * (N-1) / 2^32) skipping
  *     the first, the third floor(w2 * (N-2) / 2^32) skipping the smaller and
  *     then the larger of the two taken;
@@ -93,6 +93,9 @@ typedef struct {
   double inlier_threshold;   /* tau >= 0, m/s; inlier iff |residual| <= tau */
   uint64_t seed;             /* Philox key */
   double cond_eps;           /* minimal-set rejection; <= 0 selects 1e-4 (2D) / 1e-6 (3D) */
+  int32_t first_cluster;     /* cluster i of this frame draws as cluster first_cluster + i
+                                (0 normally; a shard of a larger frame passes the index of
+                                its first cluster there, so its results equal the whole's) */
 } rvh_params;
 
 /* Caller-owned, caller-sized outputs.  Per-cluster arrays have n_clusters

@@ -61,6 +61,8 @@ int check_args(const rvh_frame* f, const rvh_params* p, const rvh_result* r) {
   if (std::isnan(p->inlier_threshold) || p->inlier_threshold < 0)
     return fail(RVH_EINVAL, "inlier_threshold must be >= 0");
   if (std::isnan(p->cond_eps)) return fail(RVH_EINVAL, "cond_eps is NaN");
+  if (p->first_cluster < 0 || (int64_t)p->first_cluster + f->n_clusters > 0x7fffffffLL)
+    return fail(RVH_EINVAL, "first_cluster out of range");
   if (f->n_points > 0 && (!f->azimuth || !f->doppler)) return fail(RVH_EINVAL, "azimuth/doppler NULL");
   if (f->n_clusters > 0 && !f->cluster_offsets) return fail(RVH_EINVAL, "cluster_offsets NULL");
   if (f->n_clusters > 0 && (!r->vx || !r->vy || !r->heading || !r->inlier_count || !r->best_hypothesis || !r->status))
@@ -207,6 +209,7 @@ void fill_desc(rvh_ctx* ctx, FrameDesc& d, const rvh_frame& f, const rvh_params&
   d.acc = round_up_f(eps + eD);
   d.rej = (eps - eD > 0) ? round_down_f(eps - eD) : -1.0f;
   d.key = make_uint2((uint32_t)(p.seed & 0xFFFFFFFFu), (uint32_t)(p.seed >> 32));
+  d.cluster_base = p.first_cluster;
   d.vx = out.vx;
   d.vy = out.vy;
   d.vz = out.vz;
@@ -632,6 +635,7 @@ int rvh_estimate_baseline(rvh_ctx* ctx, const rvh_frame* frame, const rvh_params
   b.tau = d.tau;
   b.eps = d.eps;
   b.key = d.key;
+  b.cluster_base = d.cluster_base;
   b.vx = d.vx;
   b.vy = d.vy;
   b.vz = d.vz;

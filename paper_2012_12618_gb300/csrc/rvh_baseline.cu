@@ -60,7 +60,7 @@ __global__ void __launch_bounds__(kBaseThreads) baseline_kernel(BaselineArgs a, 
   unsigned long long mine = 0ull;
   for (int h = tid; h < a.H; h += kBaseThreads) {
     int q[3];
-    draw_minimal_set<DIM>(a.key, ci, h, N, q);
+    draw_minimal_set<DIM>(a.key, a.cluster_base + ci, h, N, q);
     const double* r0 = rows + 4 * q[0];
     const double* r1 = rows + 4 * q[1];
     const double* r2 = rows + 4 * q[DIM == 3 ? 2 : 0];
@@ -91,7 +91,7 @@ __global__ void __launch_bounds__(kBaseThreads) baseline_kernel(BaselineArgs a, 
   const int hstar = (int)(0xFFFFFFFFu - (uint32_t)(key & 0xFFFFFFFFull));
   if (tid == 0) {
     int q[3];
-    draw_minimal_set<DIM>(a.key, ci, hstar, N, q);
+    draw_minimal_set<DIM>(a.key, a.cluster_base + ci, hstar, N, q);
     const double* r0 = rows + 4 * q[0];
     const double* r1 = rows + 4 * q[1];
     const double* r2 = rows + 4 * q[DIM == 3 ? 2 : 0];

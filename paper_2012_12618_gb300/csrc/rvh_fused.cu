@@ -176,7 +176,7 @@ struct Rows64 {
 template <int DIM>
 __device__ bool hyp_f64(const FrameDesc& a, const Rows64<DIM>& R, int ci, int h, int N, double v[3]) {
   int q[3];
-  draw_minimal_set<DIM>(a.key, ci, h, N, q);
+  draw_minimal_set<DIM>(a.key, a.cluster_base + ci, h, N, q);
   const double4_32a s0 = R.at(q[0]), s1 = R.at(q[1]), s2 = R.at(DIM == 3 ? q[2] : q[0]);
   const double r0[3] = {s0.x, s0.y, s0.z}, r1[3] = {s1.x, s1.y, s1.z}, r2[3] = {s2.x, s2.y, s2.z};
   const double w[3] = {s0.w, s1.w, DIM == 3 ? s2.w : 0.0};
@@ -379,7 +379,7 @@ __device__ void process_cluster(const FrameDesc& a, const Smem& S, ClusterShared
     // a2 + a3: draw, FP32 solve (refined when ill-conditioned), bound
     for (int hl = tid; hl < nh; hl += kThreads) {
       int q[3];
-      draw_minimal_set<DIM>(a.key, ci, hc0 + hl, N, q);
+      draw_minimal_set<DIM>(a.key, a.cluster_base + ci, hc0 + hl, N, q);
       const int q2 = DIM == 3 ? q[2] : q[0];
       const float4 p0 = rows[q[0]], p1 = rows[q[1]], p2 = rows[q2];
       const int qs[3] = {q[0], q[1], q2};

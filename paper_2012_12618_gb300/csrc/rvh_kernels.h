@@ -34,6 +34,7 @@ struct FrameDesc {
   TauPair tau32;
   float acc, rej;            // FP32 conditioning thresholds (certain accept / certain reject)
   uint2 key;                 // Philox key = seed
+  int32_t cluster_base;      // Philox cluster counter = cluster_base + cluster index
   double* vx;
   double* vy;
   double* vz;
@@ -74,6 +75,7 @@ struct BaselineArgs {
   int64_t n_points;
   double* rows64_g;          // [n_points * 4] FP64 rows of clusters larger than nmax_smem
   const double2* trig;
+  int32_t cluster_base;
   int H;
   double tau;
   double eps;

@@ -99,3 +99,37 @@ def test_graph_replay_and_recapture(torch):
         o = G.run_oracle(f.azimuth, f.doppler, f.offsets, H=w.num_hypotheses, tau=w.tau, seed=seed)
         rep = G.compare(g, o, f.offsets)
         assert not rep["mismatch"], (seed, rep["mismatch"][:10])
+
+
+@pytest.mark.parametrize("name", ["dense2d", "dense3d"])
+def test_shards_equal_whole(torch, name):
+    """Contiguous cluster ranges estimated separately with first_cluster give
+    exactly the whole frame's results (the multi-GPU sharding rule)."""
+    from paper_2012_12618_gb300 import partition
+    w = synth.WORKLOADS[name]
+    f = synth.make_frame(w, n_clusters=300, gen_seed=71)
+    H = 512
+    dev = torch.device("cuda", 0)
+
+    def run(az, dop, off, el, first):
+        t = [None if x is None else torch.from_numpy(np.ascontiguousarray(x)).to(dev) for x in (az, el, dop, off)]
+        frame = rvh.make_frame(t[0], t[2], t[3], t[1])
+        params = rvh.make_params(w.model_dim, H, w.tau, 4, first_cluster=first)
+        outs = rvh.alloc_outputs(off.shape[0] - 1, az.shape[0], dev)
+        ctx.check(rvh.rvh_estimate(ctx.handle, frame, params, rvh.make_result(outs), None), "estimate")
+        torch.cuda.synchronize()
+        return _np(outs, az.shape[0])
+
+    ctx = rvh.Context(0)
+    try:
+        whole = run(f.azimuth, f.doppler, f.offsets, f.elevation, 0)
+        ranges = partition.balanced_ranges(f.offsets, H, 3)
+        parts = []
+        for c0, c1 in ranges:
+            az, dop, off, el, _ = partition.shard(f.azimuth, f.doppler, f.offsets, c0, c1, f.elevation)
+            parts.append(run(az, dop, off, el, c0))
+    finally:
+        ctx.close()
+    merged = partition.merge(parts, ranges, f.offsets)
+    for k in whole:
+        assert np.array_equal(merged[k], whole[k], equal_nan=True), k
