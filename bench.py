@@ -67,24 +67,36 @@ class ClockSampler:
         self._t = None
 
     def _run(self):
-        while not self._stop.is_set():
-            try:
-                out = subprocess.run(["nvidia-smi", "-i", str(self.index), f"--query-gpu={self.FIELDS}",
-                                      "--format=csv,noheader,nounits"], capture_output=True, text=True,
-                                     timeout=5).stdout.strip()
-                if out:
-                    self.samples.append([x.strip() for x in out.split(",")])
-            except Exception:
-                pass
-            self._stop.wait(0.2)
+        for line in self._p.stdout:
+            if self._stop.is_set():
+                break
+            line = line.strip()
+            if line:
+                self.samples.append([x.strip() for x in line.split(",")])
 
     def __enter__(self):
+        # one streaming nvidia-smi process, a sample every 100 ms
+        self._p = None
+        try:
+            self._p = subprocess.Popen(["nvidia-smi", "-i", str(self.index), f"--query-gpu={self.FIELDS}",
+                                        "--format=csv,noheader,nounits", "-lms", "100"],
+                                       stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+        except OSError:
+            return self
         self._t = threading.Thread(target=self._run, daemon=True)
         self._t.start()
         return self
 
     def __exit__(self, *exc):
         self._stop.set()
+        if self._p is None:
+            return
+        self._p.terminate()
+        try:
+            self._p.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self._p.kill()
+            self._p.wait(timeout=5)
         self._t.join(timeout=10)
 
     def summary(self):
@@ -147,7 +159,7 @@ def reference_arm(args):
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=100)
+    ap.add_argument("--steps", type=int, default=2000)
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", default="rvh", choices=["rvh", "reference"])
     ap.add_argument("--workload", default=WORKLOAD, choices=["frame64", "dense2d", "stress2d", "dense3d"],
@@ -213,7 +225,7 @@ def main():
     torch.cuda.synchronize()
 
     step_ms, kern_ms = [], []
-    band = cand = fp64h = refined = 0
+    band = cand = fp64h = refined = launches = 0
     phase = np.zeros(6)
     if ws > 1:
         torch.distributed.barrier()
@@ -235,6 +247,7 @@ def main():
             cand += stats.candidates
             fp64h += stats.fp64_hypotheses
             refined += stats.refined_hypotheses
+            launches += stats.kernel_launches
             phase += np.array(list(stats.phase_cycles), dtype=np.float64)
         torch.cuda.synchronize()
     wall = time.perf_counter() - t_wall
@@ -270,6 +283,17 @@ def main():
                 "frac_at_measured_clock": (achieved / (sms * FP32_LANES_PER_SM * 2 * clocks["sm_mhz"] * 1e6 / 1e12)
                                            if clocks.get("sm_mhz") else None),
                 "algorithmic_flops_per_launch": flops, "kernel_ms": kern_s * 1e3}
+    # the scoring pass alone: its share of the per-CTA stage clocks (clock64,
+    # summed over CTAs) times the kernel time; co-resident CTAs in other
+    # stages share the SM meanwhile, so this is an attribution, not a solo run
+    share = float(phase[2] / max(phase.sum(), 1.0))
+    if share > 0:
+        sc = flops / (share * kern_s) / 1e12
+        roofline["scoring_loop"] = {
+            "achieved": sc, "frac": sc / peak, "stage_share": share,
+            "frac_at_measured_clock": (sc / (sms * FP32_LANES_PER_SM * 2 * clocks["sm_mhz"] * 1e6 / 1e12)
+                                       if clocks.get("sm_mhz") else None),
+            "basis": "scoring-pass share of the per-CTA stage clocks x kernel time"}
 
     # ---- end to end through the C ABI with pinned host buffers (copies inside the timed region)
     h_az = torch.from_numpy(f.azimuth).pin_memory()
@@ -355,7 +379,7 @@ def main():
             "serving": serve,
             "e2e": e2e,
             "clocks": clocks,
-            "gpu_launches": 2 * args.steps,
+            "gpu_launches": launches,
             "band": {"fp64_band_decisions_per_step": band / args.steps, "candidates_per_step": cand / args.steps,
                      "fp64_trials_per_step": fp64h / args.steps,
                      "refined_trials_per_step": refined / args.steps,

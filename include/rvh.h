@@ -207,6 +207,7 @@ typedef struct {
   int64_t phase_cycles[6];
   int64_t refined_hypotheses;  /* trials whose FP32 solve took one refinement step */
   int64_t graph_replays;       /* rvh_estimate calls served by replaying a captured CUDA graph */
+  int32_t kernel_launches;     /* the library's kernels launched by the last call (work list + fused) */
 } rvh_stats;
 
 /* Counters of the last rvh_estimate on this context (synchronises its stream). */

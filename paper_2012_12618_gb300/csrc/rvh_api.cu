@@ -257,6 +257,7 @@ int launch_batch(rvh_ctx* ctx, FusedArgs& a, int dim, cudaStream_t s, cudaEvent_
   RVH_CUDA(launch_fused(dim, a, grid, smem, s));
   if (t1) RVH_CUDA(cudaEventRecord(t1, s));
   ctx->last.grid = grid;
+  ctx->last.kernel_launches = a.direct ? 1 : 2;
   return RVH_OK;
 }
 
@@ -298,6 +299,7 @@ int launch_graph(rvh_ctx* ctx, FusedArgs& a, int dim, cudaStream_t s) {
   RVH_CUDA(cudaGraphLaunch(ctx->gexec, s));
   RVH_CUDA(cudaEventRecord(ctx->ev1, s));
   ctx->last.grid = grid;
+  ctx->last.kernel_launches = a.direct ? 1 : 2;
   return RVH_OK;
 }
 

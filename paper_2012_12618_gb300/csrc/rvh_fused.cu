@@ -12,6 +12,7 @@
 // FP32 rows staged in shared memory and its FP64 rows in L1/L2-resident
 // global scratch.
 #include <cstdint>
+#include <type_traits>
 #include <cuda_runtime.h>
 
 #include "rvh_device.cuh"
@@ -26,7 +27,7 @@ constexpr int kWarps = kThreads / 32;
 #endif
 
 struct Smem {
-  float4* rows;       // [nmax_smem]
+  float* rows;        // [roundup32(nmax_smem) * 4] row tiles (TileRows)
   float4* hyp;        // [hchunk] (-X, -Y, -Z, thi)
   float* tlo;         // [hchunk]
   int* U;             // [hchunk] upper bounds of the exact counts (-1 = rejected)
@@ -96,12 +97,149 @@ __device__ __forceinline__ float block_max_float(float v, float* red) {
   return r;
 }
 
+// ---- FP32 rows of the cluster being processed ---------------------------------------
+// Shared memory holds them as tiles of 32 points, component-major inside a
+// tile (32 c | 32 s | 32 w | 32 unused in 2D; 32 a0 | 32 a1 | 32 a2 | 32 w in
+// 3D): a warp reading consecutive points touches 32 banks per component, and
+// four consecutive points of one component are one aligned float4, which the
+// scoring pass consumes as two packed pairs.  Clusters larger than the shared
+// memory area keep plain float4 rows in global scratch.
+struct TileRows {
+  float* f;
+  __device__ __forceinline__ float4 at(int j) const {
+    const float* b = f + ((j >> 5) << 7) + (j & 31);
+    return make_float4(b[0], b[32], b[64], b[96]);
+  }
+  __device__ __forceinline__ void put(int j, float4 v) const {
+    float* b = f + ((j >> 5) << 7) + (j & 31);
+    b[0] = v.x;
+    b[32] = v.y;
+    b[64] = v.z;
+    b[96] = v.w;
+  }
+  // component k of points 4q .. 4q + 3
+  __device__ __forceinline__ float4 quad(int q, int k) const {
+    return *reinterpret_cast<const float4*>(f + ((q >> 3) << 7) + (k << 5) + ((q & 7) << 2));
+  }
+};
+
+struct AosRows {
+  float4* p;
+  __device__ __forceinline__ float4 at(int j) const { return p[j]; }
+  __device__ __forceinline__ void put(int j, float4 v) const { p[j] = v; }
+};
+
+// Packed FP32 pairs (fma.rn.f32x2 / add.rn.f32x2 round each half like the
+// scalar instruction, so results are those of fmaf / FP32 add per element).
+__device__ __forceinline__ unsigned long long pack2(float lo, float hi) {
+  unsigned long long r;
+  asm("mov.b64 %0, {%1, %2};" : "=l"(r) : "f"(lo), "f"(hi));
+  return r;
+}
+__device__ __forceinline__ void unpack2(unsigned long long v, float& lo, float& hi) {
+  asm("mov.b64 {%0, %1}, %2;" : "=f"(lo), "=f"(hi) : "l"(v));
+}
+__device__ __forceinline__ unsigned long long fma2(unsigned long long a, unsigned long long b,
+                                                   unsigned long long c) {
+  unsigned long long d;
+  asm("fma.rn.f32x2 %0, %1, %2, %3;" : "=l"(d) : "l"(a), "l"(b), "l"(c));
+  return d;
+}
+__device__ __forceinline__ unsigned long long add2(unsigned long long a, unsigned long long b) {
+  unsigned long long d;
+  asm("add.rn.f32x2 %0, %1, %2;" : "=l"(d) : "l"(a), "l"(b));
+  return d;
+}
+// 1.0f if |r| <= t else 0.0f (false for NaN)
+__device__ __forceinline__ float in_band(float r, float t) {
+  float e;
+  asm("{.reg .f32 a; abs.f32 a, %1; set.le.f32.f32 %0, a, %2;}" : "=f"(e) : "f"(r), "f"(t));
+  return e;
+}
+
+// a4 over tiled rows: the residuals of two points per instruction.  Lane l
+// handles trial sub-group l / PW and point quads l % PW, l % PW + PW, ...;
+// the rows stage pads the last quad with NaN Dopplers, which never count.
+// Per element the arithmetic is resid_f32's: w + nz z + ny y + nx x by fmaf.
+template <int DIM, int PW, int HPL>
+__device__ __forceinline__ void phase_a_tiles(const TileRows rows, int N, const Smem& S, int nh) {
+  constexpr int NHL = 32 / PW;
+  constexpr int G = NHL * HPL;
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int hl = lane / PW, pl = lane % PW;
+  const int ngroups = (nh + G - 1) / G;
+  const int nq = (N + 3) >> 2;
+  for (int g = warp; g < ngroups; g += kWarps) {
+    const int base = g * G + hl * HPL;
+    unsigned long long nx[HPL], ny[HPL], nz[HPL], acc[HPL];
+    float th[HPL];
+#pragma unroll
+    for (int m = 0; m < HPL; ++m) {
+      const int h = base + m;
+      const float4 v = (h < nh) ? S.hyp[h] : make_float4(0.f, 0.f, 0.f, __int_as_float(0x7fc00000));
+      nx[m] = pack2(v.x, v.x);
+      ny[m] = pack2(v.y, v.y);
+      nz[m] = pack2(v.z, v.z);
+      th[m] = v.w;
+      acc[m] = 0ull;
+    }
+    for (int q = pl; q < nq; q += PW) {
+      const float4 c = rows.quad(q, 0), sn = rows.quad(q, 1), z = rows.quad(q, 2);
+      const unsigned long long c01 = pack2(c.x, c.y), c23 = pack2(c.z, c.w);
+      const unsigned long long s01 = pack2(sn.x, sn.y), s23 = pack2(sn.z, sn.w);
+      unsigned long long w01, w23, z01 = 0ull, z23 = 0ull;
+      if (DIM == 2) {
+        w01 = pack2(z.x, z.y);
+        w23 = pack2(z.z, z.w);
+      } else {
+        const float4 w = rows.quad(q, 3);
+        z01 = pack2(z.x, z.y);
+        z23 = pack2(z.z, z.w);
+        w01 = pack2(w.x, w.y);
+        w23 = pack2(w.z, w.w);
+      }
+#pragma unroll
+      for (int m = 0; m < HPL; ++m) {
+        unsigned long long r01, r23;
+        if (DIM == 2) {
+          r01 = fma2(nx[m], c01, fma2(ny[m], s01, w01));
+          r23 = fma2(nx[m], c23, fma2(ny[m], s23, w23));
+        } else {
+          r01 = fma2(nx[m], c01, fma2(ny[m], s01, fma2(nz[m], z01, w01)));
+          r23 = fma2(nx[m], c23, fma2(ny[m], s23, fma2(nz[m], z23, w23)));
+        }
+        float a0, a1, a2, a3;
+        unpack2(r01, a0, a1);
+        unpack2(r23, a2, a3);
+        acc[m] = add2(acc[m], pack2(in_band(a0, th[m]), in_band(a1, th[m])));
+        acc[m] = add2(acc[m], pack2(in_band(a2, th[m]), in_band(a3, th[m])));
+      }
+    }
+    float cnt[HPL];
+#pragma unroll
+    for (int m = 0; m < HPL; ++m) {
+      float lo, hi;
+      unpack2(acc[m], lo, hi);
+      cnt[m] = lo + hi;  // exact: integers below 2^24
+#pragma unroll
+      for (int o = PW / 2; o > 0; o >>= 1) cnt[m] += __shfl_xor_sync(0xffffffffu, cnt[m], o);
+    }
+    if (pl == 0) {
+#pragma unroll
+      for (int m = 0; m < HPL; ++m) {
+        const int h = base + m;
+        if (h < nh && S.kind[h] == kHypNormal) S.U[h] = (int)cnt[m];
+      }
+    }
+  }
+}
+
 // ---- a4: upper-bound counts U_h = #{|r32| <= thi_h} (the hot loop) -----------------
 // Lane l handles trial sub-group l / PW and points l % PW, l % PW + PW, ...;
 // each lane keeps HPL trials in registers.  PW = 32 is warp-per-trial-group
 // with lanes over points; PW = 1 is lanes over trials with broadcast rows.
 template <int DIM, int PW, int HPL>
-__device__ __forceinline__ void phase_a(const float4* __restrict__ rows, int N, const Smem& S, int nh) {
+__device__ __forceinline__ void phase_a(const float4* __restrict__ rows, int N, const Smem& S, int nh) {  // global rows
   constexpr int NHL = 32 / PW;
   constexpr int G = NHL * HPL;
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
@@ -143,14 +281,29 @@ __device__ __forceinline__ void phase_a(const float4* __restrict__ rows, int N, 
   }
 }
 
+// The tiled pass keeps four trials per lane whatever hpl asks: eight packed
+// trials (pairs of registers per coordinate) do not fit in the 64 registers a
+// thread has at four CTAs per SM.
 template <int DIM>
-__device__ void phase_a_dispatch(int pw, int hpl, const float4* rows, int N, const Smem& S, int nh) {
+__device__ void phase_a_dispatch(int pw, int hpl, const TileRows rows, int N, const Smem& S, int nh) {
+  (void)hpl;
   if (pw == 1) {
-    if (hpl == 8) phase_a<DIM, 1, 8>(rows, N, S, nh); else phase_a<DIM, 1, 4>(rows, N, S, nh);
+    phase_a_tiles<DIM, 1, 4>(rows, N, S, nh);
   } else if (pw == 8) {
-    if (hpl == 8) phase_a<DIM, 8, 8>(rows, N, S, nh); else phase_a<DIM, 8, 4>(rows, N, S, nh);
+    phase_a_tiles<DIM, 8, 4>(rows, N, S, nh);
   } else {
-    if (hpl == 8) phase_a<DIM, 32, 8>(rows, N, S, nh); else phase_a<DIM, 32, 4>(rows, N, S, nh);
+    phase_a_tiles<DIM, 32, 4>(rows, N, S, nh);
+  }
+}
+
+template <int DIM>
+__device__ void phase_a_dispatch(int pw, int hpl, const AosRows rows, int N, const Smem& S, int nh) {
+  if (pw == 1) {
+    if (hpl == 8) phase_a<DIM, 1, 8>(rows.p, N, S, nh); else phase_a<DIM, 1, 4>(rows.p, N, S, nh);
+  } else if (pw == 8) {
+    if (hpl == 8) phase_a<DIM, 8, 8>(rows.p, N, S, nh); else phase_a<DIM, 8, 4>(rows.p, N, S, nh);
+  } else {
+    if (hpl == 8) phase_a<DIM, 32, 8>(rows.p, N, S, nh); else phase_a<DIM, 32, 4>(rows.p, N, S, nh);
   }
 }
 
@@ -202,13 +355,13 @@ struct ClusterShared {
 // Exact count of one trial by the whole CTA: FP32 certainties, then an FP64
 // re-decision of the points inside the trial's error band.  When there are
 // band points the trial's FP64 velocity is left in cs.cv64 and *band > 0.
-template <int DIM>
-__device__ int exact_count_block(const FrameDesc& a, const float4* __restrict__ rows, const Rows64<DIM>& R,
+template <int DIM, typename RV>
+__device__ int exact_count_block(const FrameDesc& a, const RV rows, const Rows64<DIM>& R,
                                  int ci, int h, int N, float4 hy, float tlo, ClusterShared& cs, int* band) {
   const int tid = threadIdx.x;
   unsigned long long lb = 0;  // L in the low word, B in the high word
   for (int j = tid; j < N; j += kThreads) {
-    const float r = fabsf(resid_f32<DIM>(rows[j], hy.x, hy.y, hy.z));
+    const float r = fabsf(resid_f32<DIM>(rows.at(j), hy.x, hy.y, hy.z));
     if (r <= tlo) lb += 1ull;
     else if (!(r > hy.w)) lb += 1ull << 32;
   }
@@ -229,7 +382,7 @@ __device__ int exact_count_block(const FrameDesc& a, const float4* __restrict__ 
   const double v[3] = {cs.cv64[0], cs.cv64[1], cs.cv64[2]};
   unsigned long long lbin = 0;
   for (int j = tid; j < N; j += kThreads) {
-    const float r = fabsf(resid_f32<DIM>(rows[j], hy.x, hy.y, hy.z));
+    const float r = fabsf(resid_f32<DIM>(rows.at(j), hy.x, hy.y, hy.z));
     if (!(r <= tlo) && !(r > hy.w)) {
       const double4_32a s = R.at(j);
       const double a64[3] = {s.x, s.y, s.z};
@@ -339,7 +492,13 @@ __device__ void process_cluster(const FrameDesc& a, const Smem& S, ClusterShared
     if (tid == 0) write_invalid<DIM>(a, ci, RVH_STATUS_TOO_FEW_POINTS);
     return;
   }
-  float4* rows = SMEM_ROWS ? S.rows : (a.rows_g + o);
+  using RV = typename std::conditional<SMEM_ROWS, TileRows, AosRows>::type;
+  RV rows;
+  if constexpr (SMEM_ROWS) {
+    rows.f = S.rows;
+  } else {
+    rows.p = a.rows_g + o;
+  }
   const Rows64<DIM> R = {&a, o, a.rows64_g + o};
   long long t_stage = clock64();
   auto stage_done = [&](int k) {
@@ -356,13 +515,20 @@ __device__ void process_cluster(const FrameDesc& a, const Smem& S, ClusterShared
     const float w = a.dop[o + j];
     const float az = a.az[o + j];
     const float el = DIM == 3 ? a.el[o + j] : 0.0f;
-    rows[j] = row_f32<DIM>(az, el, w);
+    rows.put(j, row_f32<DIM>(az, el, w));
     if (DIM == 3) {
       double a64[3];
       row_f64<DIM>(a.trig, az, el, a64);
       R.pre[j] = make_double4_32a(a64[0], a64[1], a64[2], (double)w);
     }
     wm = fmaxf(wm, fabsf(w));
+  }
+  if constexpr (SMEM_ROWS) {
+    // pad the last quad of the scoring pass: NaN Dopplers never count
+    if (tid < ((N + 3) & ~3) - N) {
+      const float nan = __int_as_float(0x7fc00000);
+      rows.put(N + tid, make_float4(0.0f, 0.0f, nan, nan));
+    }
   }
   wm = block_max_float(wm, cs.red_f);  // includes a __syncthreads after the row writes
   if (tid == 0) {
@@ -381,7 +547,7 @@ __device__ void process_cluster(const FrameDesc& a, const Smem& S, ClusterShared
       int q[3];
       draw_minimal_set<DIM>(a.key, a.cluster_base + ci, hc0 + hl, N, q);
       const int q2 = DIM == 3 ? q[2] : q[0];
-      const float4 p0 = rows[q[0]], p1 = rows[q[1]], p2 = rows[q2];
+      const float4 p0 = rows.at(q[0]), p1 = rows.at(q[1]), p2 = rows.at(q2);
       const int qs[3] = {q[0], q[1], q2};
       auto seed64 = [&](int i) { return R.at(qs[i]); };
       // 2D minimal sets are mildly conditioned (|det| = |sin(t1 - t0)|): their
@@ -442,7 +608,7 @@ __device__ void process_cluster(const FrameDesc& a, const Smem& S, ClusterShared
           const float4 hy = S.hyp[c];
           const float htlo = S.tlo[c];
           int B = 0;
-          const int C = exact_count_block<DIM>(a, rows, R, ci, hc0 + c, N, hy, htlo, cs, &B);
+          const int C = exact_count_block<DIM, RV>(a, rows, R, ci, hc0 + c, N, hy, htlo, cs, &B);
           ++n_cand;
           if (tid == 0) {
             const unsigned long long k = best_key(C, hc0 + c);
@@ -495,7 +661,7 @@ __device__ void process_cluster(const FrameDesc& a, const Smem& S, ClusterShared
   for (int i = 0; i < NS; ++i) sums[i] = 0.0;
   int nin = 0;
   for (int j = tid; j < N; j += kThreads) {
-    const float r = fabsf(resid_f32<DIM>(rows[j], win.x, win.y, win.z));
+    const float r = fabsf(resid_f32<DIM>(rows.at(j), win.x, win.y, win.z));
     bool in = r <= wtlo;
     const bool band = !in && !(r > win.w);
     if (in || band) {
@@ -558,8 +724,8 @@ __global__ void __launch_bounds__(kThreads, RVH_MIN_BLOCKS) fused_kernel(FusedAr
   __shared__ int s_item;
   Smem S;
   unsigned char* p = smem_raw;
-  S.rows = reinterpret_cast<float4*>(p);
-  p += (size_t)a.nmax_smem * sizeof(float4);
+  S.rows = reinterpret_cast<float*>(p);
+  p += (size_t)((a.nmax_smem + 31) & ~31) * sizeof(float4);
   S.hyp = reinterpret_cast<float4*>(p);
   p += (size_t)a.hchunk * sizeof(float4);
   S.tlo = reinterpret_cast<float*>(p);
@@ -649,7 +815,7 @@ size_t fused_smem_bytes(int nmax_smem, int hchunk) {
   // the trial area also holds the final reduction (up to 9 sums per thread)
   const size_t trials = (size_t)hchunk * (sizeof(float4) + sizeof(float) + sizeof(int) + 1);
   const size_t reduction = (size_t)9 * kThreads * sizeof(double);
-  return (size_t)nmax_smem * sizeof(float4) + (trials > reduction ? trials : reduction);
+  return (size_t)((nmax_smem + 31) & ~31) * sizeof(float4) + (trials > reduction ? trials : reduction);
 }
 
 cudaError_t launch_worklist(const FusedArgs& a, cudaStream_t s) {

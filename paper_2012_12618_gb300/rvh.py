@@ -59,7 +59,8 @@ class rvh_stats(ctypes.Structure):
                 ("band_points", ctypes.c_int64), ("fp64_hypotheses", ctypes.c_int64),
                 ("kernel_ms", ctypes.c_float), ("grid", ctypes.c_int32), ("points_per_warp", ctypes.c_int32),
                 ("hyps_per_lane", ctypes.c_int32), ("phase_cycles", ctypes.c_int64 * 6),
-                ("refined_hypotheses", ctypes.c_int64), ("graph_replays", ctypes.c_int64)]
+                ("refined_hypotheses", ctypes.c_int64), ("graph_replays", ctypes.c_int64),
+                ("kernel_launches", ctypes.c_int32)]
 
 
 # exported symbols and their ctypes signatures (restype, argtypes)

@@ -133,3 +133,36 @@ def test_shards_equal_whole(torch, name):
     merged = partition.merge(parts, ranges, f.offsets)
     for k in whole:
         assert np.array_equal(merged[k], whole[k], equal_nan=True), k
+
+
+@pytest.mark.parametrize("dim", [2, 3])
+def test_every_schedule_same_result(torch, dim):
+    """Both scoring passes (tiled shared-memory rows, float4 global rows) under
+    every schedule: cluster sizes 2..2600 cover ragged quads (N mod 4 != 0),
+    single tiles and clusters above the shared-memory capacity."""
+    w = synth.WORKLOADS["dense2d" if dim == 2 else "dense3d"]
+    sizes = np.array([2, 3, 5, 7, 31, 33, 64, 101, 257, 1000, 1535, 1536, 1537, 2049, 2600], np.int64)
+    f = synth.make_frame(w, sizes=sizes, gen_seed=63)
+    keep, frame = _device_frame(torch, f)
+    H = 512
+    params = rvh.make_params(dim, H, w.tau, 9)
+    dev = torch.device("cuda", 0)
+    ctx = rvh.Context(0)
+    results = {}
+    try:
+        for pw in (1, 8, 32):
+            for hpl in (4, 8):
+                ctx.check(rvh.rvh_set_schedule(ctx.handle, pw, hpl), "schedule")
+                outs = rvh.alloc_outputs(f.n_clusters, f.n_points, dev)
+                ctx.check(rvh.rvh_estimate(ctx.handle, frame, params, rvh.make_result(outs), None), "estimate")
+                torch.cuda.synchronize()
+                results[(pw, hpl)] = _np(outs, f.n_points)
+    finally:
+        ctx.close()
+    first = results[(1, 4)]
+    for key, r in results.items():
+        for k in ("inlier_mask", "inlier_count", "best_hypothesis", "status", "vx", "vy", "vz", "heading"):
+            assert np.array_equal(r[k], first[k], equal_nan=True), (key, k)
+    o = G.run_oracle(f.azimuth, f.doppler, f.offsets, el=f.elevation, H=H, tau=w.tau, seed=9)
+    rep = G.compare(first, o, f.offsets)
+    assert not rep["mismatch"], rep["mismatch"][:10]
