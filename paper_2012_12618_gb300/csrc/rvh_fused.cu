@@ -343,7 +343,7 @@ struct ClusterShared {
   float win_tlo;
   int red_i[kWarps];
   float red_f[kWarps];
-  double red_d[kWarps][10];
+  double red_t[9];            // the normal-equation sums of the winner's inliers
   unsigned long long ctr[4];  // exact counts, band points, fp64 trials, refined trials
   unsigned long long clk[6];  // cycles per stage (thread 0's view of the CTA)
   unsigned long long red_u[kWarps];
@@ -408,7 +408,7 @@ __device__ void write_invalid(const FrameDesc& a, int ci, int st) {
 // Scv, Ssv; 3D the six entries of G then g), Cramer's rule, fallback to the
 // winning minimal-set velocity, heading atan2(vy, vx).  One thread.
 template <int DIM>
-__device__ void finish_cluster(const FrameDesc& a, const Rows64<DIM>& R, int ci, int N, int hstar, int n_in,
+__device__ __noinline__ void finish_cluster(const FrameDesc& a, const Rows64<DIM>& R, int ci, int N, int hstar, int n_in,
                                const double* t, const double* v64, bool has_v64) {
   double vout[3] = {v64[0], v64[1], v64[2]};
   int st = 0;
@@ -454,6 +454,19 @@ __device__ void finish_cluster(const FrameDesc& a, const Rows64<DIM>& R, int ci,
   a.status[ci] = st;
 }
 
+// A cluster waiting for its final solve and heading (finish_cluster): the
+// CTA queues up to kFinishBatch of them in shared memory and finishes them
+// together, one lane each.  Serial FP64 on one lane costs as much pipe time
+// per instruction as a full warp, so a lone thread finishing each cluster
+// kept the other 255 threads at the next barrier for microseconds.
+constexpr int kFinishBatch = 32;
+struct FinishRec {
+  double t[9];
+  double v64[3];
+  int64_t o;
+  int n_in, hstar, ci, frame, N, has_v64;
+};
+
 // Accumulates the normal-equation sums of one inlier row (a0, a1, a2, w).
 template <int DIM>
 __device__ __forceinline__ void accumulate_row(double* sums, const double4_32a& s) {
@@ -478,7 +491,7 @@ __device__ __forceinline__ void accumulate_row(double* sums, const double4_32a& 
 
 template <int DIM, bool SMEM_ROWS>
 __device__ void process_cluster(const FrameDesc& a, const Smem& S, ClusterShared& cs, int ci, int hchunk,
-                                int pw, int hpl) {
+                                int pw, int hpl, int frame, FinishRec* fq, int* fq_n) {
   const int tid = threadIdx.x;
   const int64_t o = a.offsets[ci];
   const int64_t e = a.offsets[ci + 1];
@@ -678,9 +691,8 @@ __device__ void process_cluster(const FrameDesc& a, const Smem& S, ClusterShared
     a.mask[o + j] = in ? 1 : 0;
   }
   // Reduce the per-thread sums through shared memory (the trial area is free
-  // now): only threads that held points contribute, and each of NS * 8
-  // threads adds one 32-thread slice, a fifth of the FP64 adds of a shuffle
-  // tree (FP64 runs at 1/64 of the FP32 rate on this GPU).
+  // now): warp i sums sum i, each lane a strided share of the threads that
+  // held points, then a shuffle tree; 12 dependent FP64 adds per sum.
   const int warp = tid >> 5, lane = tid & 31;
   nin = warp_sum(nin);
   const int nact = min(N, kThreads);
@@ -691,37 +703,43 @@ __device__ void process_cluster(const FrameDesc& a, const Smem& S, ClusterShared
   }
   if (lane == 0) cs.red_i[warp] = nin;
   __syncthreads();
-  if (tid < NS * kWarps) {
-    const int i = tid / kWarps, seg = tid % kWarps;
-    const int lo = seg * 32, hi = min(lo + 32, nact);
+  for (int i = warp; i < NS; i += kWarps) {
     double acc = 0.0;
-    for (int k = lo; k < hi; ++k) acc += red[i * kThreads + k];
-    cs.red_d[seg][i] = acc;
+    for (int k = lane; k < nact; k += 32) acc += red[i * kThreads + k];
+#pragma unroll
+    for (int off = 16; off > 0; off >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, off);
+    if (lane == 0) cs.red_t[i] = acc;
   }
   __syncthreads();
   if (tid == 0) {
     int n_in = 0;
-    double t[NS];
+    for (int w = 0; w < kWarps; ++w) n_in += cs.red_i[w];
+    FinishRec& q = fq[*fq_n];
 #pragma unroll
-    for (int i = 0; i < NS; ++i) t[i] = 0.0;
-    for (int w = 0; w < kWarps; ++w) {
-      n_in += cs.red_i[w];
-      if (w * 32 < nact) {
-#pragma unroll
-        for (int i = 0; i < NS; ++i) t[i] += cs.red_d[w][i];
-      }
-    }
-    finish_cluster<DIM>(a, R, ci, N, hstar, n_in, t, v64, cs.win_has_v64);
+    for (int i = 0; i < NS; ++i) q.t[i] = cs.red_t[i];
+    q.v64[0] = v64[0];
+    q.v64[1] = v64[1];
+    q.v64[2] = v64[2];
+    q.o = o;
+    q.n_in = n_in;
+    q.hstar = hstar;
+    q.ci = ci;
+    q.frame = frame;
+    q.N = N;
+    q.has_v64 = cs.win_has_v64;
+    *fq_n += 1;
   }
   __syncthreads();
   stage_done(4);
 }
 
 template <int DIM>
-__global__ void __launch_bounds__(kThreads, RVH_MIN_BLOCKS) fused_kernel(FusedArgs a) {
+__global__ void __launch_bounds__(kThreads, RVH_MIN_BLOCKS) fused_kernel(const __grid_constant__ FusedArgs a) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   __shared__ ClusterShared cs;
   __shared__ int s_item;
+  __shared__ FinishRec fq[kFinishBatch];
+  __shared__ int fq_n;
   Smem S;
   unsigned char* p = smem_raw;
   S.rows = reinterpret_cast<float*>(p);
@@ -736,6 +754,20 @@ __global__ void __launch_bounds__(kThreads, RVH_MIN_BLOCKS) fused_kernel(FusedAr
 
   if (threadIdx.x < 4) cs.ctr[threadIdx.x] = 0ull;
   if (threadIdx.x < 6) cs.clk[threadIdx.x] = 0ull;
+  if (threadIdx.x == 0) fq_n = 0;
+  // the queued clusters' solves and headings, one lane each
+  auto flush = [&]() {
+    const int n = fq_n;
+    if (threadIdx.x < n) {
+      const FinishRec& q = fq[threadIdx.x];
+      const FrameDesc& F = a.f[q.frame];
+      const Rows64<DIM> R = {&F, q.o, F.rows64_g + q.o};
+      finish_cluster<DIM>(F, R, q.ci, q.N, q.hstar, q.n_in, q.t, q.v64, q.has_v64 != 0);
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) fq_n = 0;
+    __syncthreads();
+  };
   const long long t_kernel = clock64();
   for (int round = 0;; ++round) {
     __syncthreads();
@@ -757,12 +789,15 @@ __global__ void __launch_bounds__(kThreads, RVH_MIN_BLOCKS) fused_kernel(FusedAr
     const int ci = fc.y;
     const int64_t o = F.offsets[ci], e = F.offsets[ci + 1];
     if (e - o <= (int64_t)a.nmax_smem || e < o) {
-      process_cluster<DIM, true>(F, S, cs, ci, a.hchunk, a.pw, a.hpl);
+      process_cluster<DIM, true>(F, S, cs, ci, a.hchunk, a.pw, a.hpl, fc.x, fq, &fq_n);
     } else {
-      process_cluster<DIM, false>(F, S, cs, ci, a.hchunk, a.pw, a.hpl);
+      process_cluster<DIM, false>(F, S, cs, ci, a.hchunk, a.pw, a.hpl, fc.x, fq, &fq_n);
     }
+    __syncthreads();
+    if (fq_n == kFinishBatch) flush();
   }
   __syncthreads();
+  flush();
   if (threadIdx.x == 0) {
     unsigned long long staged = 0;
     for (int k = 0; k < 5; ++k) staged += cs.clk[k];
