@@ -206,27 +206,56 @@ struct Hyp32 {
   int refined;
 };
 
+// Reciprocal by rcp.approx.f32 (one instruction; at most one ulp from 1/x,
+// i.e. relative error below 2^-23, for normal x).  Used instead of IEEE
+// division in the FP32 solve: the error bounds below account for it.
+__device__ __forceinline__ float rcp_approx(float x) {
+  float r;
+  asm("rcp.approx.ftz.f32 %0, %1;" : "=f"(r) : "f"(x));
+  return r;
+}
+// |rcp_approx(x)| * kRcpUp, rounded to nearest, is >= 1/|x| even after one
+// more rounding of x itself: (1 - 2^-23)(1 - 2^-24)^2 (1 + 2^-19) > 1.
+constexpr float kRcpUp = 1.0f + 0x1p-19f;
+
+// >= 1 / (|d| - eD) for |d| > eD.
+__device__ __forceinline__ float inv_minus(float d, float eD) { return rcp_approx(fabsf(d) - eD) * kRcpUp; }
+
+// Reciprocals of a trial's FP32 determinant d: rd = rcp(d) (|rd - 1/d| <=
+// 2^-23 |1/d|), inv >= 1/|d| and slack >= eD / (|d| - eD) (meaningful while
+// |d| > eD; callers treat |d| <= 2 eD as unusable).
+struct DetRcp {
+  float rd, inv, slack;
+};
+__device__ __forceinline__ DetRcp det_rcp(float d, float eD) {
+  DetRcp r;
+  r.rd = rcp_approx(d);
+  r.inv = fabsf(r.rd) * kRcpUp;
+  r.slack = eD * inv_minus(d, eD) * kRcpUp;
+  return r;
+}
+
 // FP32 Cramer solve of the rows p, q[, r] with right side b (exact floats),
-// determinant d already formed.  X receives the solution, e a bound on
-// |X - A64^-1 b| per component, where A64 holds the FP64 rows: the bound
-// covers the FP32 rows' error (rho per entry), every FP32 rounding, and the
-// error of d (eD).
+// determinant d already formed (reciprocals in R).  X receives the solution,
+// e a bound on |X - A64^-1 b| per component, where A64 holds the FP64 rows:
+// the bound covers the FP32 rows' error (rho per entry), every FP32
+// rounding, the error of d (eD, through slack), and the quotient n * rd,
+// whose relative error is below 2^-23 + 2^-24 + 2^-47 < 4u.
 template <int DIM>
-__device__ __forceinline__ void cramer_f32(float4 p, float4 q, float4 r, const float* b, float d, float eD,
+__device__ __forceinline__ void cramer_f32(float4 p, float4 q, float4 r, const float* b, const DetRcp& R,
                                            float* X, float* e) {
-  const float ad = fabsf(d);
-  const float inv = 1.0f / ad;
-  const float slack = eD / (ad - eD);
+  const float inv = R.inv;
+  const float slack = R.slack;
   if (DIM == 2) {
     const float n0 = fmaf(b[0], q.y, -(b[1] * p.y));
     const float n1 = fmaf(p.x, b[1], -(b[0] * q.x));
-    X[0] = n0 / d;
-    X[1] = n1 / d;
+    X[0] = n0 * R.rd;
+    X[1] = n1 * R.rd;
     X[2] = 0.0f;
     const float A = (kRowRel + kU) * 1.0001f * (fabsf(b[0]) + fabsf(b[1]));
     const float e0 = A + kU * fabsf(n0), e1 = A + kU * fabsf(n1);
-    e[0] = (e0 + (fabsf(n0) + e0) * slack) * inv + kU * fabsf(X[0]);
-    e[1] = (e1 + (fabsf(n1) + e1) * slack) * inv + kU * fabsf(X[1]);
+    e[0] = (e0 + (fabsf(n0) + e0) * slack) * inv + 4.0f * kU * fabsf(X[0]);
+    e[1] = (e1 + (fabsf(n1) + e1) * slack) * inv + 4.0f * kU * fabsf(X[1]);
     e[2] = 0.0f;
   } else {
     float n[3];
@@ -251,9 +280,9 @@ __device__ __forceinline__ void cramer_f32(float4 p, float4 q, float4 r, const f
     const float A = (4.0f * kRowRel3 + 8.0f * kU) * 1.0001f * (fabsf(b[0]) + fabsf(b[1]) + fabsf(b[2]));
 #pragma unroll
     for (int k = 0; k < 3; ++k) {
-      X[k] = n[k] / d;
+      X[k] = n[k] * R.rd;
       const float ek = A + kU * fabsf(n[k]);
-      e[k] = (ek + (fabsf(n[k]) + ek) * slack) * inv + kU * fabsf(X[k]);
+      e[k] = (ek + (fabsf(n[k]) + ek) * slack) * inv + 4.0f * kU * fabsf(X[k]);
     }
   }
 }
@@ -309,12 +338,13 @@ __device__ __forceinline__ Hyp32 hyp_f32(float4 p, float4 q, float4 r, const See
   }
   const float eD = DIM == 2 ? kDetErr2 : kDetErr3;
   const float w[3] = {DIM == 2 ? p.z : p.w, DIM == 2 ? q.z : q.w, DIM == 2 ? 0.0f : r.w};
+  const DetRcp R = det_rcp(d, eD);
   float X[3], e[3];
-  cramer_f32<DIM>(p, q, r, w, d, eD, X, e);
+  cramer_f32<DIM>(p, q, r, w, R, X, e);
   // error of the FP64 solve (the oracle's X64) against the exact solution with FP64 rows
   const float sw = fabsf(w[0]) + fabsf(w[1]) + fabsf(w[2]);
   const float sx = fabsf(X[0]) + fabsf(X[1]) + fabsf(X[2]);
-  const float e64 = (DIM == 2 ? 0x1p-50f : 0x1p-48f) * (2.0f * sw + 2.0f * sx) / ad;
+  const float e64 = (DIM == 2 ? 0x1p-50f : 0x1p-48f) * (2.0f * sw + 2.0f * sx) * R.inv;
 #pragma unroll
   for (int k = 0; k < DIM; ++k) e[k] += e64;
   float b = band_f32<DIM>(wmax, X, e);
@@ -331,8 +361,8 @@ __device__ __forceinline__ Hyp32 hyp_f32(float4 p, float4 q, float4 r, const See
       rerr = fmaxf(rerr, kU * fabsf(rf[i]) + 0x1p-51f * (fabsf(w[i]) + sx));
     }
     float dX[3], de[3];
-    cramer_f32<DIM>(p, q, r, rf, d, eD, dX, de);
-    const float inv_norm = (float)DIM / (ad - eD);  // ||A64^-1||_inf (adjugate entries <= 1)
+    cramer_f32<DIM>(p, q, r, rf, R, dX, de);
+    const float inv_norm = (float)DIM * inv_minus(d, eD) * kRcpUp;  // >= ||A64^-1||_inf (adjugate entries <= 1)
 #pragma unroll
     for (int k = 0; k < DIM; ++k) {
       X[k] = X[k] + dX[k];
