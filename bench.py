@@ -29,7 +29,7 @@ sys.path.insert(0, ROOT)
 WORKLOAD = "dense2d"
 FP32_LANES_PER_SM = 128          # FP32 FMA lanes per SM (Blackwell)
 SM_MAX_MHZ_FALLBACK = 2070.0
-KERNEL_SOURCES = ["rvh_fused.cu", "rvh_device.cuh", "rvh_kernels.h"]
+KERNEL_SOURCES = ["rvh_fused.cu", "rvh_scoring.cuh", "rvh_device.cuh", "rvh_kernels.h"]
 
 
 def kernel_hash() -> str:
