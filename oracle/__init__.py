@@ -39,7 +39,8 @@ def build(force: bool = False) -> str:
 class _Params(ctypes.Structure):
     _fields_ = [("model_dim", ctypes.c_int32), ("num_hypotheses", ctypes.c_int32),
                 ("tau", ctypes.c_double), ("seed", ctypes.c_uint64),
-                ("cond_eps", ctypes.c_double), ("enumerate", ctypes.c_int32)]
+                ("cond_eps", ctypes.c_double), ("enumerate", ctypes.c_int32),
+                ("refine_iterations", ctypes.c_int32)]
 
 
 _lib = None
@@ -91,9 +92,11 @@ def _p(a):
 def estimate(azimuth, doppler, offsets, *, elevation=None, num_hypotheses: int, tau: float,
              seed: int, cond_eps: float | None = None, enumerate_subsets: bool = False,
              subset=None, want_counts: bool = False, want_fragile: bool = False,
-             _lib=None) -> dict:
+             refine_iterations: int = 0, _lib=None) -> dict:
     """Run the oracle over all clusters (or the listed subset).  Inputs are
-    widened to FP64 exactly."""
+    widened to FP64 exactly.  refine_iterations > 0 adds that many local
+    optimisation rounds (re-threshold against the least-squares velocity,
+    re-fit) after the refine."""
     az = np.ascontiguousarray(azimuth, dtype=np.float64)
     dp = np.ascontiguousarray(doppler, dtype=np.float64)
     el = None if elevation is None else np.ascontiguousarray(elevation, dtype=np.float64)
@@ -104,7 +107,8 @@ def estimate(azimuth, doppler, offsets, *, elevation=None, num_hypotheses: int, 
     n_out = nc if sub is None else sub.shape[0]
     H = int(num_hypotheses)
     p = _Params(k, H, float(tau), int(seed) & 0xFFFFFFFFFFFFFFFF,
-                default_cond_eps(k) if cond_eps is None else float(cond_eps), int(enumerate_subsets))
+                default_cond_eps(k) if cond_eps is None else float(cond_eps), int(enumerate_subsets),
+                int(refine_iterations))
     out = {
         "vx": np.full(n_out, np.nan), "vy": np.full(n_out, np.nan), "vz": np.full(n_out, np.nan),
         "heading": np.full(n_out, np.nan),

@@ -305,6 +305,8 @@ int oracle_estimate(const double* azimuth, const double* elevation, const double
                          : det3(G[0], G[1], G[2]);
     if (fabs(fabs(detG) - limit) <= 1e-13 * (k == 2 ? trace * trace : trace * trace * trace))
       frag = 1;
+    int solved = 0;
+    double cnd = 0.0; /* trace^k / |det G|: bounds the condition number of G */
     if (n_in >= k && fabs(detG) > limit) {
       double vs[3];
       int ok = 0;
@@ -312,8 +314,63 @@ int oracle_estimate(const double* azimuth, const double* elevation, const double
       vout[0] = vs[0];
       vout[1] = vs[1];
       vout[2] = k == 3 ? vs[2] : 0.0;
+      solved = 1;
+      cnd = (k == 2 ? trace * trace : trace * trace * trace) / fabs(detG);
     } else {
       st |= ORC_LSQ_FALLBACK;
+    }
+
+    /* Local optimisation rounds: re-threshold all points against the current
+     * least-squares velocity (the same residual test as Alg. 1) and solve the
+     * normal equations of the new inlier set.  A round that changes nothing
+     * ends the loop; so does a new set whose system is short or singular,
+     * in which case the previous velocity and inlier set stand.  After a
+     * fallback the current velocity is the winner's, whose re-threshold
+     * reproduces the current set, so nothing changes. */
+    if (solved && p->refine_iterations > 0) {
+      uint8_t* m2 = (uint8_t*)malloc((size_t)n);
+      for (int32_t it = 0; it < p->refine_iterations; ++it) {
+        int32_t n2 = 0, changed = 0;
+        double G2[3][3] = {{0, 0, 0}, {0, 0, 0}, {0, 0, 0}};
+        double g2[3] = {0, 0, 0};
+        /* another order of the same sums moves the solved velocity by about
+         * n u cond(G) |v|: decisions that close to tau are rounding ties */
+        double amp = 1e-12 * (1.0 + cnd);
+        double vs1 = fabs(vout[0]) + fabs(vout[1]) + fabs(vout[2]);
+        for (int32_t q = 0; q < n; ++q) {
+          const double* aq = &a[3 * q];
+          double r = residual(k, aq, w[q], vout);
+          uint8_t in = fabs(r) <= tau;
+          if (fabs(fabs(r) - tau) <= amp * (vs1 + fabs(w[q]) + tau)) frag = 1;
+          m2[q] = in;
+          if (in != mask[o + q]) changed = 1;
+          if (!in) continue;
+          ++n2;
+          for (int rr = 0; rr < k; ++rr) {
+            for (int cc = rr; cc < k; ++cc) G2[rr][cc] = fma(aq[rr], aq[cc], G2[rr][cc]);
+            g2[rr] = fma(aq[rr], w[q], g2[rr]);
+          }
+        }
+        if (!changed) break;
+        for (int rr = 0; rr < k; ++rr)
+          for (int cc = 0; cc < rr; ++cc) G2[rr][cc] = G2[cc][rr];
+        double tr2 = 0.0;
+        for (int rr = 0; rr < k; ++rr) tr2 += G2[rr][rr];
+        double trk = k == 2 ? tr2 * tr2 : tr2 * tr2 * tr2;
+        double det2G = k == 2 ? det2(G2[0][0], G2[0][1], G2[1][0], G2[1][1]) : det3(G2[0], G2[1], G2[2]);
+        if (fabs(fabs(det2G) - 1e-12 * trk) <= 1e-13 * trk) frag = 1;
+        if (!(n2 >= k && fabs(det2G) > 1e-12 * trk)) break;
+        double vs[3];
+        int ok = 0;
+        cramer_solve(k, G2[0], G2[1], G2[2], g2, 0.0, vs, &ok);
+        vout[0] = vs[0];
+        vout[1] = vs[1];
+        vout[2] = k == 3 ? vs[2] : 0.0;
+        cnd = trk / fabs(det2G);
+        n_in = n2;
+        for (int32_t q = 0; q < n; ++q) mask[o + q] = m2[q];
+      }
+      free(m2);
     }
 
     vx[oi] = vout[0];

@@ -27,7 +27,14 @@
  *   - the pseudo-inverse of Eq. (eq:LSQPerCluster) is computed through the
  *     normal equations, with a fallback to the winning minimal-set velocity
  *     when they are singular or have fewer than k rows;
- *   - the heading is atan2(vy, vx) (Sec. III-B writes arctan(vy/vx)).
+ *   - the heading is atan2(vy, vx) (Sec. III-B writes arctan(vy/vx));
+ *   - optional local optimisation (refine_iterations > 0): the velocity of
+ *     Sec. III-B is computed "subsequent to" inlier detection; here that is
+ *     repeated: every point of the cluster is re-thresholded against the
+ *     current least-squares velocity and the normal equations of the new
+ *     inlier set are solved again, until the set stops changing, its system
+ *     is singular or short (the last accepted velocity and set then stand),
+ *     or the round limit is reached.
  */
 #ifndef RVH_ORACLE_H
 #define RVH_ORACLE_H
@@ -49,6 +56,7 @@ typedef struct {
   uint64_t seed;
   double cond_eps;        /* minimal set rejected unless |det| >= cond_eps */
   int32_t enumerate;      /* 0: Philox draws; 1: h-th k-subset, lexicographic */
+  int32_t refine_iterations; /* >= 0: re-threshold + re-fit rounds after the refine */
 } orc_params;
 
 /* Philox4x32 with 10 rounds: out = Philox(ctr; key). */

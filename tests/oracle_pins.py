@@ -16,6 +16,10 @@ violation.  What pins what:
   lstsq       the refine equals numpy.linalg.lstsq on the inlier rows (the
               least-squares comparator of the paper's Table II)
   status      too-few-points, all-degenerate and least-squares fallback cases
+  local_opt   the re-threshold + re-fit rounds: one round's inlier set is
+              numpy's re-threshold of the refined velocity, every result is
+              numpy.linalg.lstsq of its own inlier set, a converged result is
+              a fixed point of threshold-then-fit, the exact symmetries hold
 """
 from __future__ import annotations
 
@@ -283,5 +287,66 @@ def check_planted(L):
     assert np.median(err) < 0.05
 
 
+def _rows(f):
+    th = f.azimuth.astype(np.float64)
+    if f.elevation is None:
+        return np.stack([np.cos(th), np.sin(th)], 1)
+    el = f.elevation.astype(np.float64)
+    return np.stack([np.cos(th) * np.cos(el), np.sin(th) * np.cos(el), np.sin(el)], 1)
+
+
+def check_local_opt(L):
+    for name, nc, H in (("stress2d", 96, 256), ("dense3d", 12, 256)):
+        w, f = _frame(name, nc)
+        A, dop, off = _rows(f), f.doppler.astype(np.float64), f.offsets
+        k = A.shape[1]
+        kw = dict(elevation=f.elevation, num_hypotheses=H, tau=w.tau, seed=1)
+        base = _est(L, f.azimuth, f.doppler, off, **kw)
+        zero = _est(L, f.azimuth, f.doppler, off, refine_iterations=0, **kw)
+        for key in ("vx", "vy", "vz", "inlier_mask", "inlier_count", "status"):
+            assert np.array_equal(base[key], zero[key], equal_nan=True), key
+        one = _est(L, f.azimuth, f.doppler, off, refine_iterations=1, **kw)
+        many = _est(L, f.azimuth, f.doppler, off, refine_iterations=12, **kw)
+        more = _est(L, f.azimuth, f.doppler, off, refine_iterations=13, **kw)
+        moved = fixed = 0
+        for c in range(nc):
+            if base["status"][c] != 0:
+                continue
+            s, e = off[c], off[c + 1]
+            Ac, wc = A[s:e], dop[s:e]
+            vb = np.array([base["vx"][c], base["vy"][c], base["vz"][c]])[:k]
+            # one round: the inlier set is the re-threshold of the refined velocity
+            r = np.abs(wc - Ac @ vb)
+            clear = np.abs(r - w.tau) > 1e-9
+            m1 = one["inlier_mask"][s:e].astype(bool)
+            re = r <= w.tau
+            if re.sum() >= k and not np.array_equal(re, base["inlier_mask"][s:e].astype(bool)):
+                assert np.array_equal(m1[clear], re[clear]), c
+                moved += 1
+            for o in (one, many):
+                m = o["inlier_mask"][s:e].astype(bool)
+                assert m.sum() == o["inlier_count"][c]
+                ref = np.linalg.lstsq(Ac[m], wc[m], rcond=None)[0]
+                got = np.array([o["vx"][c], o["vy"][c], o["vz"][c]])[:k]
+                assert np.allclose(got, ref, rtol=1e-9, atol=1e-9), (name, c, got, ref)
+                assert abs(o["heading"][c] - math.atan2(got[1], got[0])) < 1e-12
+            # converged (one more round changes nothing): threshold-then-fit fixed point
+            if np.array_equal(many["inlier_mask"][s:e], more["inlier_mask"][s:e]):
+                vm = np.array([many["vx"][c], many["vy"][c], many["vz"][c]])[:k]
+                rm = np.abs(wc - Ac @ vm)
+                cl = np.abs(rm - w.tau) > 1e-9
+                assert np.array_equal(many["inlier_mask"][s:e].astype(bool)[cl], (rm <= w.tau)[cl]), c
+                fixed += 1
+        assert moved >= 5 and fixed >= nc // 2, (name, moved, fixed)
+        # exact symmetries survive the rounds
+        neg = _est(L, -f.azimuth.astype(np.float64), f.doppler, off, refine_iterations=12, **kw)
+        assert np.array_equal(many["inlier_mask"], neg["inlier_mask"])
+        assert np.array_equal(many["vy"], -neg["vy"]) and np.array_equal(many["vx"], neg["vx"])
+        sc = _est(L, f.azimuth, f.doppler.astype(np.float64) * 8.0, off, refine_iterations=12,
+                  **dict(kw, tau=w.tau * 8.0))
+        assert np.array_equal(many["inlier_mask"], sc["inlier_mask"])
+        assert np.array_equal(many["vx"] * 8.0, sc["vx"]) and np.array_equal(many["vy"] * 8.0, sc["vy"])
+
+
 ALL_CHECKS = [check_philox, check_draws, check_recovery, check_brute, check_symmetry,
-              check_rotation, check_lstsq, check_status, check_planted]
+              check_rotation, check_lstsq, check_status, check_planted, check_local_opt]

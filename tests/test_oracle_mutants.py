@@ -40,6 +40,10 @@ MUTANTS = {
                            "*ok = fabs(det) >= 0.5 * eps + 0.5;\n    if (*ok) {\n      v[0]"),
     "fallback_limit_dropped": ("if (n_in >= k && fabs(detG) > limit) {",
                                "if (fabs(detG) > 0.0) {"),
+    "lo_mask_not_updated": ("for (int32_t q = 0; q < n; ++q) mask[o + q] = m2[q];", ""),
+    "lo_winner_velocity": ("double r = residual(k, aq, w[q], vout);", "double r = residual(k, aq, w[q], vb);"),
+    "lo_dropped_rhs": ("g2[rr] = fma(aq[rr], w[q], g2[rr]);", "g2[rr] = fma(aq[rr], aq[rr], g2[rr]);"),
+    "lo_count_not_updated": ("n_in = n2;", ""),
 }
 
 
