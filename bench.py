@@ -206,6 +206,10 @@ def main():
                     help="points_per_warp,hyps_per_lane for the scoring pass (default: the library's choice)")
     ap.add_argument("--serving-seconds", type=float, default=3.0,
                     help="measured seconds of the 64-radar serving load (0 skips it)")
+    ap.add_argument("--refine-iterations", type=int, default=0,
+                    help="local-optimisation rounds in the timed steps (default 0: the single-pass method)")
+    ap.add_argument("--local-opt-steps", type=int, default=50,
+                    help="steps of the extra 2-round local-optimisation measurement (0 skips it)")
     args = ap.parse_args()
     if args.impl == "reference":
         return reference_arm(args)
@@ -238,7 +242,7 @@ def main():
     d_off = torch.from_numpy(f.offsets).to(dev)
     outs = rvh.alloc_outputs(nc, npts, dev)
     frame = rvh.make_frame(d_az, d_dop, d_off, d_el)
-    params = rvh.make_params(dim, w.num_hypotheses, w.tau, w.seed)
+    params = rvh.make_params(dim, w.num_hypotheses, w.tau, w.seed, refine_iterations=args.refine_iterations)
     res = rvh.make_result(outs)
     # a dedicated stream: the library and the timing events share it
     stream = torch.cuda.Stream(dev)
@@ -331,6 +335,30 @@ def main():
                                        if clocks.get("sm_mhz") else None),
             "basis": "scoring-pass share of the per-CTA stage clocks x kernel time"}
 
+    # ---- local-optimisation rounds (refine_iterations = 2) on the same frame:
+    # kernel time and how many mask entries the rounds change
+    local_opt = None
+    if args.local_opt_steps > 0 and args.refine_iterations == 0:
+        lo_outs = rvh.alloc_outputs(nc, npts, dev)
+        lo_res = rvh.make_result(lo_outs)
+        lo_params = rvh.make_params(dim, w.num_hypotheses, w.tau, w.seed, refine_iterations=2)
+        lo_ms = []
+        for i in range(3 + args.local_opt_steps):
+            flush.fill_(5)
+            ctx.check(rvh.rvh_estimate(ctx.handle, frame, lo_params, lo_res, sptr), "rvh_estimate(local opt)")
+            ctx.check(rvh.rvh_get_stats(ctx.handle, stats), "rvh_get_stats")
+            if i >= 3:
+                lo_ms.append(stats.kernel_ms)
+        torch.cuda.synchronize()
+        changed = int((lo_outs["inlier_mask"] != outs["inlier_mask"]).sum().item())
+        lk = float(np.mean(lo_ms))
+        local_opt = {"refine_iterations": 2, "kernel_ms": lk, "clusters_per_s": nc / (lk * 1e-3),
+                     "kernel_ms_single_pass": kern_s * 1e3, "mask_changed": changed,
+                     "mask_changed_fraction": changed / max(npts, 1),
+                     "inliers_single_pass": int(outs["inlier_count"].sum().item()),
+                     "inliers_after_rounds": int(lo_outs["inlier_count"].sum().item()),
+                     "steps": args.local_opt_steps}
+
     # ---- end to end through the C ABI with pinned host buffers (copies inside the timed region)
     h_az = torch.from_numpy(f.azimuth).pin_memory()
     h_el = None if f.elevation is None else torch.from_numpy(f.elevation).pin_memory()
@@ -355,7 +383,7 @@ def main():
 
     # ---- plain all-FP64 one-launch-per-cluster GPU version (same frame)
     gpu_base = None
-    if not args.no_gpu_baseline:
+    if not args.no_gpu_baseline and args.refine_iterations == 0:
         base_out = rvh.alloc_outputs(nc, npts, dev)
         bres = rvh.make_result(base_out)
         ctx.check(rvh.rvh_estimate_baseline(ctx.handle, frame, params, bres, sptr), "baseline")
@@ -406,7 +434,8 @@ def main():
             "scaling": "weak", "vs_baseline": None, "dtype": "f32+f64", "data": "synthetic",
             "config": {"workload": f"{wname}: {nc} clusters, sizes {w.size_law} {w.size_lo}..{w.size_hi}, "
                                    f"{npts} points, {dim}D, H={w.num_hypotheses}, tau={w.tau} m/s, "
-                                   f"outliers {w.outlier_frac:g}, noise {w.noise_sigma:g} m/s, seed={w.seed}",
+                                   f"outliers {w.outlier_frac:g}, noise {w.noise_sigma:g} m/s, seed={w.seed}, "
+                                   f"refine_iterations={args.refine_iterations}",
                        "l2": "flushed between timed steps (256 MiB write outside the step events)",
                        "per_rank": "one independent frame per rank"},
             "pair_evals_per_s": pairs * ws / t_max,
@@ -415,6 +444,7 @@ def main():
             "cpu_baseline_all_cores": cpu_all,
             "gpu_baseline": gpu_base,
             "serving": serve,
+            "local_opt": local_opt,
             "e2e": e2e,
             "clocks": clocks,
             "gpu_launches": launches,

@@ -96,7 +96,23 @@ typedef struct {
   int32_t first_cluster;     /* cluster i of this frame draws as cluster first_cluster + i
                                 (0 normally; a shard of a larger frame passes the index of
                                 its first cluster there, so its results equal the whole's) */
+  int32_t refine_iterations; /* local-optimisation rounds after the refine, 0 (none) ..
+                                RVH_MAX_REFINE_ITERATIONS; see below */
 } rvh_params;
+
+/* Local optimisation (refine_iterations > 0).  Sec. III-B computes the
+ * velocity "subsequent to" inlier detection; these rounds repeat that step.
+ * Each round solves the normal equations of the current inlier set,
+ * re-thresholds every point of the cluster against that velocity with the
+ * same test |v_d - a.v| <= inlier_threshold (decided exactly as in FP64),
+ * and keeps the new set when its normal equations are solvable (at least k
+ * rows, |det| > 1e-12 trace^k); a round that changes no point, or whose new
+ * set is not solvable (the previous set then stands), ends the loop.
+ * inlier_mask, inlier_count and the velocity are those of the final set;
+ * best_hypothesis stays the RANSAC winner.  A cluster whose first refine
+ * fell back (RVH_STATUS_LSQ_FALLBACK) is left as it is.  Not supported by
+ * rvh_estimate_baseline (RVH_EINVAL). */
+#define RVH_MAX_REFINE_ITERATIONS 64
 
 /* Caller-owned, caller-sized outputs.  Per-cluster arrays have n_clusters
  * entries, inlier_mask has n_points.  vz may be NULL (it is written with 0

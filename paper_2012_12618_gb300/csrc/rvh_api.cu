@@ -63,6 +63,8 @@ int check_args(const rvh_frame* f, const rvh_params* p, const rvh_result* r) {
   if (std::isnan(p->cond_eps)) return fail(RVH_EINVAL, "cond_eps is NaN");
   if (p->first_cluster < 0 || (int64_t)p->first_cluster + f->n_clusters > 0x7fffffffLL)
     return fail(RVH_EINVAL, "first_cluster out of range");
+  if (p->refine_iterations < 0 || p->refine_iterations > RVH_MAX_REFINE_ITERATIONS)
+    return fail(RVH_EINVAL, "refine_iterations out of range [0, RVH_MAX_REFINE_ITERATIONS]");
   if (f->n_points > 0 && (!f->azimuth || !f->doppler)) return fail(RVH_EINVAL, "azimuth/doppler NULL");
   if (f->n_clusters > 0 && !f->cluster_offsets) return fail(RVH_EINVAL, "cluster_offsets NULL");
   if (f->n_clusters > 0 && (!r->vx || !r->vy || !r->heading || !r->inlier_count || !r->best_hypothesis || !r->status))
@@ -210,6 +212,7 @@ void fill_desc(rvh_ctx* ctx, FrameDesc& d, const rvh_frame& f, const rvh_params&
   d.rej = (eps - eD > 0) ? round_down_f(eps - eD) : -1.0f;
   d.key = make_uint2((uint32_t)(p.seed & 0xFFFFFFFFu), (uint32_t)(p.seed >> 32));
   d.cluster_base = p.first_cluster;
+  d.lo_iters = p.refine_iterations;
   d.vx = out.vx;
   d.vy = out.vy;
   d.vz = out.vz;
@@ -611,6 +614,8 @@ int rvh_estimate_baseline(rvh_ctx* ctx, const rvh_frame* frame, const rvh_params
   if (!ctx) return fail(RVH_EINVAL, "ctx is NULL");
   int rc = check_args(frame, params, result);
   if (rc) return rc;
+  if (params->refine_iterations != 0)
+    return fail(RVH_EINVAL, "rvh_estimate_baseline runs the method without local optimisation (refine_iterations 0)");
   if (frame->n_clusters == 0) return RVH_OK;
   std::lock_guard<std::mutex> lk(ctx->mu);
   RVH_CUDA(cudaSetDevice(ctx->device));

@@ -200,7 +200,34 @@ struct ClusterShared {
   double cv64[3];             // FP64 velocity of the trial being counted (when it has band points)
   double win_v64[3];          // FP64 velocity of the current winner (valid if win_has_v64)
   int win_has_v64;
+  int red_c[kWarps];          // changed mask entries (local-optimisation rounds)
+  double lo_v[3];             // least-squares velocity of the current inlier set
+  float4 lo_hy;               // its FP32 record (-X, -Y, -Z, thi) and lower threshold
+  float lo_tlo;
+  int lo_ok;
 };
+
+// FP32 record of an FP64 velocity v for the re-threshold of a local
+// optimisation round: X = fl32(v), e >= |X - v|, the band of band_f32 around
+// tau outside which FP32 residuals decide like FP64 ones.
+template <int DIM>
+__device__ __forceinline__ void velocity_record(const double v[3], float wmax, TauPair tau, float4* hy, float* tlo) {
+  float X[3], e[3];
+#pragma unroll
+  for (int k = 0; k < 3; ++k) {
+    X[k] = __double2float_rn(v[k]);
+    e[k] = __double2float_ru(fabs((double)X[k] - v[k]));
+  }
+  float b = band_f32<DIM>(wmax, X, e);
+  if (!(b < 1e30f) || !(fabsf(X[0]) < 1e30f) || !(fabsf(X[1]) < 1e30f) || !(fabsf(X[2]) < 1e30f)) {
+    *hy = make_float4(-X[0], -X[1], -X[2], __int_as_float(0x7f800000));  // every point decided in FP64
+    *tlo = -1.0f;
+    return;
+  }
+  b = fmaxf(b, kBandFloor);
+  *hy = make_float4(-X[0], -X[1], -X[2], __fadd_ru(tau.hi, b));
+  *tlo = __fsub_rd(tau.lo, b);
+}
 
 // Exact count of one trial by the whole CTA: FP32 certainties, then an FP64
 // re-decision of the points inside the trial's error band.  When there are
@@ -255,42 +282,49 @@ __device__ void write_invalid(const FrameDesc& a, int ci, int st) {
 }
 
 // a8: normal equations G v = g over the inliers (sums t: 2D Scc, Scs, Sss,
-// Scv, Ssv; 3D the six entries of G then g), Cramer's rule, fallback to the
-// winning minimal-set velocity, heading atan2(vy, vx).  One thread.
+// Scv, Ssv; 3D the six entries of G then g), solved by Cramer's rule when
+// there are at least k inliers and |det G| > 1e-12 trace^k.  Returns false
+// (v untouched) otherwise.  The local-optimisation rounds and the final
+// solve both use this, so a set accepted by a round solves identically.
 template <int DIM>
-__device__ __noinline__ void finish_cluster(const FrameDesc& a, const Rows64<DIM>& R, int ci, int N, int hstar, int n_in,
-                               const double* t, const double* v64, bool has_v64) {
-  double vout[3] = {v64[0], v64[1], v64[2]};
-  int st = 0;
-  bool ok = false;
+__device__ __forceinline__ bool solve_normal(const double* t, int n_in, double v[3]) {
   if (DIM == 2) {
     const double tr = t[0] + t[2];
     const double limit = 1e-12 * (tr * tr);
     const double det = det2_f64(t[0], t[1], t[1], t[2]);
-    if (n_in >= 2 && fabs(det) > limit) {
-      const double G0[3] = {t[0], t[1], 0.0}, G1[3] = {t[1], t[2], 0.0}, g[3] = {t[3], t[4], 0.0};
-      double vs[3];
-      solve_f64<2>(G0, G1, nullptr, g, 0.0, vs, nullptr);
-      vout[0] = vs[0];
-      vout[1] = vs[1];
-      vout[2] = 0.0;
-      ok = true;
-    }
+    if (!(n_in >= 2 && fabs(det) > limit)) return false;
+    const double G0[3] = {t[0], t[1], 0.0}, G1[3] = {t[1], t[2], 0.0}, g[3] = {t[3], t[4], 0.0};
+    double vs[3];
+    solve_f64<2>(G0, G1, nullptr, g, 0.0, vs, nullptr);
+    v[0] = vs[0];
+    v[1] = vs[1];
+    v[2] = 0.0;
+    return true;
   } else {
     const double tr = t[0] + t[3] + t[5];
     const double limit = 1e-12 * (tr * tr * tr);
     const double G0[3] = {t[0], t[1], t[2]}, G1[3] = {t[1], t[3], t[4]}, G2[3] = {t[2], t[4], t[5]};
     const double det = det3_f64(G0, G1, G2);
-    if (n_in >= 3 && fabs(det) > limit) {
-      const double g[3] = {t[6], t[7], t[8]};
-      double vs[3];
-      solve_f64<3>(G0, G1, G2, g, 0.0, vs, nullptr);
-      vout[0] = vs[0];
-      vout[1] = vs[1];
-      vout[2] = vs[2];
-      ok = true;
-    }
+    if (!(n_in >= 3 && fabs(det) > limit)) return false;
+    const double g[3] = {t[6], t[7], t[8]};
+    double vs[3];
+    solve_f64<3>(G0, G1, G2, g, 0.0, vs, nullptr);
+    v[0] = vs[0];
+    v[1] = vs[1];
+    v[2] = vs[2];
+    return true;
   }
+}
+
+// Final solve and heading of a cluster: the normal equations, with a
+// fallback to the winning minimal-set velocity, heading atan2(vy, vx).
+// One thread.
+template <int DIM>
+__device__ __noinline__ void finish_cluster(const FrameDesc& a, const Rows64<DIM>& R, int ci, int N, int hstar, int n_in,
+                               const double* t, const double* v64, bool has_v64) {
+  double vout[3] = {v64[0], v64[1], v64[2]};
+  int st = 0;
+  const bool ok = solve_normal<DIM>(t, n_in, vout);
   if (!ok) {
     st |= RVH_STATUS_LSQ_FALLBACK;
     if (!has_v64) hyp_f64<DIM>(a, R, ci, hstar, N, vout);
@@ -339,7 +373,128 @@ __device__ __forceinline__ void accumulate_row(double* sums, const double4_32a& 
   }
 }
 
-template <int DIM, bool SMEM_ROWS>
+// a7 + a8: decides every point of the cluster against one velocity (FP32
+// certainties from the record hy / tlo, FP64 re-decisions with v64 inside
+// the band), writes the mask, and reduces the normal-equation sums of the
+// inliers into cs.red_t.  Returns the inlier count; with count_changes,
+// *changed receives the number of mask entries that differ from what the
+// mask held before.  The trial area of shared memory is free at this point
+// and holds the reduction.
+template <int DIM, typename RV>
+__device__ __forceinline__ int mask_and_sums(const FrameDesc& a, const RV rows, const Rows64<DIM>& R, int64_t o, int N,
+                                             float4 hy, float tlo, const double v64[3], const Smem& S,
+                                             ClusterShared& cs, bool count_changes, int* changed) {
+  const int tid = threadIdx.x;
+  constexpr int NS = DIM == 2 ? 5 : 9;
+  double sums[NS];
+#pragma unroll
+  for (int i = 0; i < NS; ++i) sums[i] = 0.0;
+  int nin = 0, nch = 0;
+  for (int j = tid; j < N; j += kThreads) {
+    const float r = fabsf(resid_f32<DIM>(rows.at(j), hy.x, hy.y, hy.z));
+    bool in = r <= tlo;
+    const bool band = !in && !(r > hy.w);
+    if (in || band) {
+      const double4_32a s = R.at(j);
+      if (band) {
+        const double a64[3] = {s.x, s.y, s.z};
+        in = fabs(residual_f64<DIM>(a64, s.w, v64)) <= a.tau;
+      }
+      if (in) {
+        ++nin;
+        accumulate_row<DIM>(sums, s);
+      }
+    }
+    if (count_changes) nch += (a.mask[o + j] != (in ? 1 : 0));
+    a.mask[o + j] = in ? 1 : 0;
+  }
+  // Reduce the per-thread sums through shared memory: warp i sums sum i,
+  // each lane a strided share of the threads that held points, then a
+  // shuffle tree; 12 dependent FP64 adds per sum.
+  const int warp = tid >> 5, lane = tid & 31;
+  nin = warp_sum(nin);
+  if (count_changes) nch = warp_sum(nch);
+  const int nact = min(N, kThreads);
+  double* red = reinterpret_cast<double*>(S.hyp);  // NS x kThreads
+  if (tid < nact) {
+#pragma unroll
+    for (int i = 0; i < NS; ++i) red[i * kThreads + tid] = sums[i];
+  }
+  if (lane == 0) {
+    cs.red_i[warp] = nin;
+    cs.red_c[warp] = nch;
+  }
+  __syncthreads();
+  for (int i = warp; i < NS; i += kWarps) {
+    double acc = 0.0;
+    for (int k = lane; k < nact; k += 32) acc += red[i * kThreads + k];
+#pragma unroll
+    for (int off = 16; off > 0; off >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, off);
+    if (lane == 0) cs.red_t[i] = acc;
+  }
+  int n_in = 0, n_ch = 0;
+#pragma unroll
+  for (int w = 0; w < kWarps; ++w) {
+    n_in += cs.red_i[w];
+    n_ch += cs.red_c[w];
+  }
+  __syncthreads();
+  if (changed) *changed = n_ch;
+  return n_in;
+}
+
+// Local-optimisation rounds (refine_iterations > 0): solve the current set,
+// re-threshold every point against that velocity, keep the new set if its
+// normal equations are solvable (else restore the previous set by
+// re-deciding with the record and velocity that produced it), stop when
+// nothing changes.  Starts from the winner's set (its sums in cs.red_t) and
+// returns the final set's inlier count, its sums left in cs.red_t.  Kept out
+// of line so that the default path's register allocation does not carry it.
+template <int DIM, typename RV>
+__device__ __noinline__ int local_opt_rounds(const FrameDesc& a, const RV rows, const Rows64<DIM>& R, int64_t o, int N,
+                                             float4 gen_hy, float gen_tlo, const double* v64, float wmax, int n_in,
+                                             const Smem& S, ClusterShared& cs) {
+  const int tid = threadIdx.x;
+  double gen_v[3] = {v64[0], v64[1], v64[2]};  // the FP64 velocity that produced the current set
+  for (int it = 0; it < a.lo_iters; ++it) {
+    if (tid == 0) {
+      double v[3] = {0.0, 0.0, 0.0};
+      cs.lo_ok = solve_normal<DIM>(cs.red_t, n_in, v) ? 1 : 0;
+      if (cs.lo_ok) {
+        cs.lo_v[0] = v[0];
+        cs.lo_v[1] = v[1];
+        cs.lo_v[2] = v[2];
+        velocity_record<DIM>(v, wmax, a.tau32, &cs.lo_hy, &cs.lo_tlo);
+      }
+    }
+    __syncthreads();
+    if (!cs.lo_ok) break;
+    const float4 nhy = cs.lo_hy;
+    const float ntlo = cs.lo_tlo;
+    const double nv[3] = {cs.lo_v[0], cs.lo_v[1], cs.lo_v[2]};
+    int changed = 0;
+    const int n2 = mask_and_sums<DIM, RV>(a, rows, R, o, N, nhy, ntlo, nv, S, cs, true, &changed);
+    if (changed == 0) break;  // same set, same sums
+    if (tid == 0) {
+      double vt[3];
+      cs.lo_ok = solve_normal<DIM>(cs.red_t, n2, vt) ? 1 : 0;
+    }
+    __syncthreads();
+    if (!cs.lo_ok) {
+      n_in = mask_and_sums<DIM, RV>(a, rows, R, o, N, gen_hy, gen_tlo, gen_v, S, cs, false, nullptr);
+      break;
+    }
+    gen_hy = nhy;
+    gen_tlo = ntlo;
+    gen_v[0] = nv[0];
+    gen_v[1] = nv[1];
+    gen_v[2] = nv[2];
+    n_in = n2;
+  }
+  return n_in;
+}
+
+template <int DIM, bool SMEM_ROWS, bool LO>
 __device__ void process_cluster(const FrameDesc& a, const Smem& S, ClusterShared& cs, int ci, int hchunk,
                                 int pw, int hpl, int frame, FinishRec* fq, int* fq_n) {
   const int tid = threadIdx.x;
@@ -519,51 +674,12 @@ __device__ void process_cluster(const FrameDesc& a, const Smem& S, ClusterShared
   const float wtlo = cs.win_tlo;
   const double v64[3] = {cs.win_v64[0], cs.win_v64[1], cs.win_v64[2]};
   constexpr int NS = DIM == 2 ? 5 : 9;
-  double sums[NS];
-#pragma unroll
-  for (int i = 0; i < NS; ++i) sums[i] = 0.0;
-  int nin = 0;
-  for (int j = tid; j < N; j += kThreads) {
-    const float r = fabsf(resid_f32<DIM>(rows.at(j), win.x, win.y, win.z));
-    bool in = r <= wtlo;
-    const bool band = !in && !(r > win.w);
-    if (in || band) {
-      const double4_32a s = R.at(j);
-      if (band) {
-        const double a64[3] = {s.x, s.y, s.z};
-        in = fabs(residual_f64<DIM>(a64, s.w, v64)) <= a.tau;
-      }
-      if (in) {
-        ++nin;
-        accumulate_row<DIM>(sums, s);
-      }
-    }
-    a.mask[o + j] = in ? 1 : 0;
+  int n_in = mask_and_sums<DIM, RV>(a, rows, R, o, N, win, wtlo, v64, S, cs, false, nullptr);
+
+  if constexpr (LO) {
+    if (a.lo_iters > 0) n_in = local_opt_rounds<DIM, RV>(a, rows, R, o, N, win, wtlo, v64, wmax, n_in, S, cs);
   }
-  // Reduce the per-thread sums through shared memory (the trial area is free
-  // now): warp i sums sum i, each lane a strided share of the threads that
-  // held points, then a shuffle tree; 12 dependent FP64 adds per sum.
-  const int warp = tid >> 5, lane = tid & 31;
-  nin = warp_sum(nin);
-  const int nact = min(N, kThreads);
-  double* red = reinterpret_cast<double*>(S.hyp);  // NS x kThreads
-  if (tid < nact) {
-#pragma unroll
-    for (int i = 0; i < NS; ++i) red[i * kThreads + tid] = sums[i];
-  }
-  if (lane == 0) cs.red_i[warp] = nin;
-  __syncthreads();
-  for (int i = warp; i < NS; i += kWarps) {
-    double acc = 0.0;
-    for (int k = lane; k < nact; k += 32) acc += red[i * kThreads + k];
-#pragma unroll
-    for (int off = 16; off > 0; off >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, off);
-    if (lane == 0) cs.red_t[i] = acc;
-  }
-  __syncthreads();
   if (tid == 0) {
-    int n_in = 0;
-    for (int w = 0; w < kWarps; ++w) n_in += cs.red_i[w];
     FinishRec& q = fq[*fq_n];
 #pragma unroll
     for (int i = 0; i < NS; ++i) q.t[i] = cs.red_t[i];
@@ -583,7 +699,10 @@ __device__ void process_cluster(const FrameDesc& a, const Smem& S, ClusterShared
   stage_done(4);
 }
 
-template <int DIM>
+// LO = true: the instantiation with the local-optimisation rounds, launched
+// only for batches that ask for them (the default instantiation carries no
+// trace of them).
+template <int DIM, bool LO>
 __global__ void __launch_bounds__(kThreads, RVH_MIN_BLOCKS) fused_kernel(const __grid_constant__ FusedArgs a) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   __shared__ ClusterShared cs;
@@ -639,9 +758,9 @@ __global__ void __launch_bounds__(kThreads, RVH_MIN_BLOCKS) fused_kernel(const _
     const int ci = fc.y;
     const int64_t o = F.offsets[ci], e = F.offsets[ci + 1];
     if (e - o <= (int64_t)a.nmax_smem || e < o) {
-      process_cluster<DIM, true>(F, S, cs, ci, a.hchunk, a.pw, a.hpl, fc.x, fq, &fq_n);
+      process_cluster<DIM, true, LO>(F, S, cs, ci, a.hchunk, a.pw, a.hpl, fc.x, fq, &fq_n);
     } else {
-      process_cluster<DIM, false>(F, S, cs, ci, a.hchunk, a.pw, a.hpl, fc.x, fq, &fq_n);
+      process_cluster<DIM, false, LO>(F, S, cs, ci, a.hchunk, a.pw, a.hpl, fc.x, fq, &fq_n);
     }
     __syncthreads();
     if (fq_n == kFinishBatch) flush();
@@ -709,21 +828,31 @@ cudaError_t launch_worklist(const FusedArgs& a, cudaStream_t s) {
 }
 
 cudaError_t fused_configure(int dim, size_t smem) {
-  if (dim == 2) return cudaFuncSetAttribute(fused_kernel<2>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-  return cudaFuncSetAttribute(fused_kernel<3>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  const cudaFuncAttribute at = cudaFuncAttributeMaxDynamicSharedMemorySize;
+  cudaError_t e = dim == 2 ? cudaFuncSetAttribute(fused_kernel<2, false>, at, (int)smem)
+                           : cudaFuncSetAttribute(fused_kernel<3, false>, at, (int)smem);
+  if (e != cudaSuccess) return e;
+  return dim == 2 ? cudaFuncSetAttribute(fused_kernel<2, true>, at, (int)smem)
+                  : cudaFuncSetAttribute(fused_kernel<3, true>, at, (int)smem);
 }
 
 cudaError_t fused_occupancy(int dim, size_t smem, int* blocks_per_sm) {
   if (dim == 2)
-    return cudaOccupancyMaxActiveBlocksPerMultiprocessor(blocks_per_sm, fused_kernel<2>, kThreads, smem);
-  return cudaOccupancyMaxActiveBlocksPerMultiprocessor(blocks_per_sm, fused_kernel<3>, kThreads, smem);
+    return cudaOccupancyMaxActiveBlocksPerMultiprocessor(blocks_per_sm, fused_kernel<2, false>, kThreads, smem);
+  return cudaOccupancyMaxActiveBlocksPerMultiprocessor(blocks_per_sm, fused_kernel<3, false>, kThreads, smem);
 }
 
 cudaError_t launch_fused(int dim, const FusedArgs& a, int grid, size_t smem, cudaStream_t s) {
-  if (dim == 2) fused_kernel<2><<<grid, kThreads, smem, s>>>(a);
-  else fused_kernel<3><<<grid, kThreads, smem, s>>>(a);
+  bool lo = false;
+  for (int f = 0; f < a.n_frames; ++f) lo = lo || a.f[f].lo_iters > 0;
+  if (dim == 2) {
+    if (lo) fused_kernel<2, true><<<grid, kThreads, smem, s>>>(a);
+    else fused_kernel<2, false><<<grid, kThreads, smem, s>>>(a);
+  } else {
+    if (lo) fused_kernel<3, true><<<grid, kThreads, smem, s>>>(a);
+    else fused_kernel<3, false><<<grid, kThreads, smem, s>>>(a);
+  }
   return cudaGetLastError();
 }
-
 
 }  // namespace rvh

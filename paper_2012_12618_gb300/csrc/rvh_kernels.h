@@ -35,6 +35,7 @@ struct FrameDesc {
   float acc, rej;            // FP32 conditioning thresholds (certain accept / certain reject)
   uint2 key;                 // Philox key = seed
   int32_t cluster_base;      // Philox cluster counter = cluster_base + cluster index
+  int32_t lo_iters;          // local-optimisation rounds after the refine (0 = none)
   double* vx;
   double* vy;
   double* vz;

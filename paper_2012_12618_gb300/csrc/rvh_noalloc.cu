@@ -112,6 +112,8 @@ extern "C" int rvh_estimate_noalloc(const rvh_frame* f, const rvh_params* p, rvh
     return rvh::set_error(RVH_EINVAL, "inlier_threshold must be >= 0 and cond_eps not NaN");
   if (p->first_cluster < 0 || (int64_t)p->first_cluster + f->n_clusters > 0x7fffffffLL)
     return rvh::set_error(RVH_EINVAL, "first_cluster out of range");
+  if (p->refine_iterations < 0 || p->refine_iterations > RVH_MAX_REFINE_ITERATIONS)
+    return rvh::set_error(RVH_EINVAL, "refine_iterations out of range [0, RVH_MAX_REFINE_ITERATIONS]");
   if (f->n_clusters == 0) return f->n_points == 0 ? RVH_OK : rvh::set_error(RVH_EINVAL, "points without clusters");
   const void* ptrs[11] = {f->azimuth, f->doppler, f->cluster_offsets, r->vx, r->vy, r->heading, r->inlier_count,
                           r->best_hypothesis, r->status, r->inlier_mask, p->model_dim == 3 ? f->elevation : f->azimuth};
@@ -150,6 +152,7 @@ extern "C" int rvh_estimate_noalloc(const rvh_frame* f, const rvh_params* p, rvh
   fd.rej = (eps - eD > 0) ? round_down_f(eps - eD) : -1.0f;
   fd.key = make_uint2((uint32_t)(p->seed & 0xFFFFFFFFu), (uint32_t)(p->seed >> 32));
   fd.cluster_base = p->first_cluster;
+  fd.lo_iters = p->refine_iterations;
   fd.vx = r->vx;
   fd.vy = r->vy;
   fd.vz = r->vz;

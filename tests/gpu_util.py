@@ -22,7 +22,7 @@ def alloc_outputs(n_clusters: int, n_points: int, device: str):
 
 
 def run_rvh(ctx, az, dop, off, *, el=None, H: int, tau: float, seed: int, cond_eps: float = 0.0,
-            baseline: bool = False, device: str = "cuda", stream=None) -> dict:
+            baseline: bool = False, device: str = "cuda", stream=None, refine_iterations: int = 0) -> dict:
     """Runs rvh_estimate (or the baseline) through the C ABI and returns numpy outputs."""
     torch = torch_mod()
     from paper_2012_12618_gb300 import rvh
@@ -35,7 +35,8 @@ def run_rvh(ctx, az, dop, off, *, el=None, H: int, tau: float, seed: int, cond_e
     n_points = int(np.asarray(az).shape[0])
     outs = alloc_outputs(int(np.asarray(off).shape[0]) - 1, n_points, device)
     frame = rvh.make_frame(taz, tdop, toff, tel)
-    params = rvh.make_params(3 if el is not None else 2, H, tau, seed, cond_eps)
+    params = rvh.make_params(3 if el is not None else 2, H, tau, seed, cond_eps,
+                             refine_iterations=refine_iterations)
     res = rvh.make_result(outs)
     fn = rvh.rvh_estimate_baseline if baseline else rvh.rvh_estimate
     rc = fn(ctx.handle, frame, params, res, stream)
@@ -48,9 +49,11 @@ def run_rvh(ctx, az, dop, off, *, el=None, H: int, tau: float, seed: int, cond_e
     return out
 
 
-def run_oracle(az, dop, off, *, el=None, H: int, tau: float, seed: int, cond_eps=None, subset=None) -> dict:
+def run_oracle(az, dop, off, *, el=None, H: int, tau: float, seed: int, cond_eps=None, subset=None,
+               refine_iterations: int = 0) -> dict:
     return oracle.estimate(az, dop, off, elevation=el, num_hypotheses=H, tau=tau, seed=seed,
-                           cond_eps=cond_eps, subset=subset, want_fragile=True)
+                           cond_eps=cond_eps, subset=subset, want_fragile=True,
+                           refine_iterations=refine_iterations)
 
 
 def compare(gpu: dict, orc: dict, off, *, subset=None, vel_tol: float = 1e-6, head_tol: float = 1e-6) -> dict:

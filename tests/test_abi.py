@@ -50,3 +50,15 @@ def test_create_without_gpu_reports_cuda_error():
     rc = rvh.rvh_create(ctypes.byref(h), 0, 0)
     assert rc == rvh.RVH_ECUDA and not h.value
     assert rvh.rvh_last_error(None)
+
+
+def test_params_layout_and_refine_range():
+    # rvh_params as declared in include/rvh.h: 40 bytes, refine_iterations last
+    assert ctypes.sizeof(rvh.rvh_params) == 40
+    assert rvh.rvh_params.refine_iterations.offset == 36
+    f = rvh.rvh_frame()
+    r = rvh.rvh_result()
+    for bad in (-1, 65):
+        p = rvh.make_params(2, 8, 0.1, 1, refine_iterations=bad)
+        assert rvh.rvh_estimate_noalloc(f, p, r, None) == rvh.RVH_EINVAL
+        assert "refine_iterations" in rvh.rvh_last_error(None)
