@@ -40,7 +40,8 @@ class _Params(ctypes.Structure):
     _fields_ = [("model_dim", ctypes.c_int32), ("num_hypotheses", ctypes.c_int32),
                 ("tau", ctypes.c_double), ("seed", ctypes.c_uint64),
                 ("cond_eps", ctypes.c_double), ("enumerate", ctypes.c_int32),
-                ("refine_iterations", ctypes.c_int32)]
+                ("refine_iterations", ctypes.c_int32), ("confidence", ctypes.c_double),
+                ("trial_block", ctypes.c_int32)]
 
 
 _lib = None
@@ -92,11 +93,13 @@ def _p(a):
 def estimate(azimuth, doppler, offsets, *, elevation=None, num_hypotheses: int, tau: float,
              seed: int, cond_eps: float | None = None, enumerate_subsets: bool = False,
              subset=None, want_counts: bool = False, want_fragile: bool = False,
-             refine_iterations: int = 0, _lib=None) -> dict:
+             refine_iterations: int = 0, confidence: float = 0.0, trial_block: int = 128,
+             want_trials: bool = False, _lib=None) -> dict:
     """Run the oracle over all clusters (or the listed subset).  Inputs are
     widened to FP64 exactly.  refine_iterations > 0 adds that many local
     optimisation rounds (re-threshold against the least-squares velocity,
-    re-fit) after the refine."""
+    re-fit) after the refine.  confidence in (0, 1) selects the adaptive trial
+    count (stopping checks every trial_block trials)."""
     az = np.ascontiguousarray(azimuth, dtype=np.float64)
     dp = np.ascontiguousarray(doppler, dtype=np.float64)
     el = None if elevation is None else np.ascontiguousarray(elevation, dtype=np.float64)
@@ -108,7 +111,7 @@ def estimate(azimuth, doppler, offsets, *, elevation=None, num_hypotheses: int, 
     H = int(num_hypotheses)
     p = _Params(k, H, float(tau), int(seed) & 0xFFFFFFFFFFFFFFFF,
                 default_cond_eps(k) if cond_eps is None else float(cond_eps), int(enumerate_subsets),
-                int(refine_iterations))
+                int(refine_iterations), float(confidence), int(trial_block))
     out = {
         "vx": np.full(n_out, np.nan), "vy": np.full(n_out, np.nan), "vz": np.full(n_out, np.nan),
         "heading": np.full(n_out, np.nan),
@@ -117,15 +120,18 @@ def estimate(azimuth, doppler, offsets, *, elevation=None, num_hypotheses: int, 
     }
     counts = np.zeros(n_out * H, np.int32) if want_counts else None
     fragile = np.zeros(n_out, np.uint8) if want_fragile else None
+    trials = np.zeros(n_out, np.int32) if want_trials else None
     rc = (_lib or lib()).oracle_estimate(
         _p(az), _p(el), _p(dp), _p(off), ctypes.c_int32(nc), _p(sub), ctypes.c_int32(n_out),
         ctypes.byref(p), _p(out["vx"]), _p(out["vy"]), _p(out["vz"]), _p(out["heading"]),
         _p(out["inlier_count"]), _p(out["best_hypothesis"]), _p(out["status"]),
-        _p(out["inlier_mask"]), _p(counts), _p(fragile))
+        _p(out["inlier_mask"]), _p(counts), _p(fragile), _p(trials))
     if rc != 0:
         raise ValueError("oracle_estimate rejected its arguments")
     if want_counts:
         out["hyp_counts"] = counts.reshape(n_out, H)
     if want_fragile:
         out["fragile"] = fragile.astype(bool)
+    if want_trials:
+        out["trials_used"] = trials
     return out

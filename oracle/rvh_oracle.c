@@ -146,6 +146,27 @@ static double residual(int k, const double* a, double w, const double* v) {
   return w - fma(v[0], a[0], fma(v[1], a[1], v[2] * a[2]));
 }
 
+/* x^n by binary exponentiation (squarings from the lowest bit up), one
+ * rounding per multiplication in this order. */
+static double pow_uint(double x, int32_t n) {
+  double r = 1.0, b = x;
+  while (n > 0) {
+    if (n & 1) r = r * b;
+    b = b * b;
+    n >>= 1;
+  }
+  return r;
+}
+
+/* Adaptive trial count: after m trials with best count `best` of n points,
+ * stop once (1 - eps^k)^m <= 1 - p with eps = best / n. */
+static int adaptive_stop(int32_t best, int32_t n, int k, int32_t m, double p) {
+  if (best < 0) return 0;
+  double eps = (double)best / (double)n;
+  double ek = k == 2 ? eps * eps : (eps * eps) * eps;
+  return pow_uint(1.0 - ek, m) <= 1.0 - p;
+}
+
 static void write_invalid(int32_t out, double* vx, double* vy, double* vz, double* heading,
                           int32_t* inlier_count, int32_t* best, int32_t* status, int32_t bits) {
   vx[out] = NAN;
@@ -162,12 +183,14 @@ int oracle_estimate(const double* azimuth, const double* elevation, const double
                     const int32_t* subset, int32_t n_subset, const orc_params* p,
                     double* vx, double* vy, double* vz, double* heading,
                     int32_t* inlier_count, int32_t* best_hypothesis, int32_t* status,
-                    uint8_t* mask, int32_t* hyp_counts, uint8_t* fragile) {
+                    uint8_t* mask, int32_t* hyp_counts, uint8_t* fragile, int32_t* trials_used) {
   if (!p || !offsets || !azimuth || !doppler || n_clusters < 0) return -1;
   const int k = p->model_dim;
   if (k != 2 && k != 3) return -1;
   if ((k == 3) != (elevation != NULL)) return -1;
   if (p->num_hypotheses < 1 || !(p->tau >= 0.0)) return -1;
+  if (!(p->confidence >= 0.0 && p->confidence < 1.0)) return -1;
+  if (p->confidence > 0.0 && p->trial_block < 1) return -1;
   const int32_t H = p->num_hypotheses;
   const double tau = p->tau;
   const int32_t n_out = subset ? n_subset : n_clusters;
@@ -178,6 +201,7 @@ int oracle_estimate(const double* azimuth, const double* elevation, const double
     const int64_t o = offsets[ci];
     const int32_t n = (int32_t)(offsets[ci + 1] - offsets[ci]);
     if (fragile) fragile[oi] = 0;
+    if (trials_used) trials_used[oi] = 0;
     for (int32_t q = 0; q < n; ++q) mask[o + q] = 0;
     if (hyp_counts)
       for (int32_t h = 0; h < H; ++h) hyp_counts[(int64_t)oi * H + h] = -1;
@@ -217,33 +241,45 @@ int oracle_estimate(const double* azimuth, const double* elevation, const double
      * count (Sec. III-A). */
     int32_t best = -1, best_count = -1;
     double min_det_margin = INFINITY;
+    int32_t trials = 0;
     for (int32_t h = 0; h < H; ++h) {
-      int32_t qs[3] = {0, 0, 0};
-      int drawn = p->enumerate ? enumerate_subset(h, n, k, qs)
-                               : oracle_draw(p->seed, ci, h, n, k, qs);
       counts[h] = -1;
-      if (drawn != 0) continue;
-      double rhs[3] = {w[qs[0]], w[qs[1]], k == 3 ? w[qs[2]] : 0.0};
-      double v[3] = {0.0, 0.0, 0.0};
-      int ok = 0;
-      double det = cramer_solve(k, &a[3 * qs[0]], &a[3 * qs[1]], k == 3 ? &a[3 * qs[2]] : NULL,
-                                rhs, p->cond_eps, v, &ok);
-      double dm = fabs(fabs(det) - p->cond_eps);
-      if (dm < min_det_margin) min_det_margin = dm;
-      hyp_det[h] = det;
-      if (!ok) continue;
-      int32_t count = 0;
-      for (int32_t q = 0; q < n; ++q)
-        if (fabs(residual(k, &a[3 * q], w[q], v)) <= tau) ++count;
-      counts[h] = count;
-      hyp_v[3 * h + 0] = v[0];
-      hyp_v[3 * h + 1] = v[1];
-      hyp_v[3 * h + 2] = v[2];
-      if (count > best_count) {
-        best_count = count;
-        best = h;
-      }
+      hyp_det[h] = INFINITY;
     }
+    for (int32_t h = 0; h < H; ++h) {
+      trials = h + 1;
+      do {
+        int32_t qs[3] = {0, 0, 0};
+        int drawn = p->enumerate ? enumerate_subset(h, n, k, qs)
+                                 : oracle_draw(p->seed, ci, h, n, k, qs);
+        if (drawn != 0) break;
+        double rhs[3] = {w[qs[0]], w[qs[1]], k == 3 ? w[qs[2]] : 0.0};
+        double v[3] = {0.0, 0.0, 0.0};
+        int ok = 0;
+        double det = cramer_solve(k, &a[3 * qs[0]], &a[3 * qs[1]], k == 3 ? &a[3 * qs[2]] : NULL,
+                                  rhs, p->cond_eps, v, &ok);
+        double dm = fabs(fabs(det) - p->cond_eps);
+        if (dm < min_det_margin) min_det_margin = dm;
+        hyp_det[h] = det;
+        if (!ok) break;
+        int32_t count = 0;
+        for (int32_t q = 0; q < n; ++q)
+          if (fabs(residual(k, &a[3 * q], w[q], v)) <= tau) ++count;
+        counts[h] = count;
+        hyp_v[3 * h + 0] = v[0];
+        hyp_v[3 * h + 1] = v[1];
+        hyp_v[3 * h + 2] = v[2];
+        if (count > best_count) {
+          best_count = count;
+          best = h;
+        }
+      } while (0);
+      /* adaptive trial count: check the bound after every block of trials */
+      if (p->confidence > 0.0 && trials % p->trial_block == 0 && trials < H &&
+          adaptive_stop(best_count, n, k, trials, p->confidence))
+        break;
+    }
+    if (trials_used) trials_used[oi] = trials;
     if (hyp_counts)
       for (int32_t h = 0; h < H; ++h) hyp_counts[(int64_t)oi * H + h] = counts[h];
 
@@ -261,7 +297,7 @@ int oracle_estimate(const double* azimuth, const double* elevation, const double
      * row values (another libm's cos/sin) can move it: the trial's velocity
      * moves by ~ulp * |v| / |det| and the residual by that times |a| <= 1. */
     if (fragile) {
-      for (int32_t h = 0; h < H && !frag; ++h) {
+      for (int32_t h = 0; h < trials && !frag; ++h) {
         if (counts[h] < 0 || counts[h] < best_count - 1) continue;
         const double* v = &hyp_v[3 * h];
         double scale = fabs(v[0]) + fabs(v[1]) + fabs(v[2]);

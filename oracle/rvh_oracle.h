@@ -34,7 +34,15 @@
  *     current least-squares velocity and the normal equations of the new
  *     inlier set are solved again, until the set stops changing, its system
  *     is singular or short (the last accepted velocity and set then stand),
- *     or the round limit is reached.
+ *     or the round limit is reached;
+ *   - optional adaptive trial count (confidence p in (0, 1)): Sec. III-A
+ *     sets max_trials per hardware and cites work on optimal RANSAC; here
+ *     trials run in index order in blocks of B, and after each block the
+ *     count stops once (1 - eps^k)^m <= 1 - p, where m is the number of
+ *     trials run and eps = best count / N the best inlier ratio so far (the
+ *     standard bound on the chance that every trial drew an outlier).  The
+ *     power is taken by binary exponentiation in a fixed order, so that any
+ *     IEEE implementation decides the same way.
  */
 #ifndef RVH_ORACLE_H
 #define RVH_ORACLE_H
@@ -57,6 +65,8 @@ typedef struct {
   double cond_eps;        /* minimal set rejected unless |det| >= cond_eps */
   int32_t enumerate;      /* 0: Philox draws; 1: h-th k-subset, lexicographic */
   int32_t refine_iterations; /* >= 0: re-threshold + re-fit rounds after the refine */
+  double confidence;      /* 0: all H trials; in (0, 1): adaptive trial count */
+  int32_t trial_block;    /* adaptive: trials between stopping checks (B >= 1) */
 } orc_params;
 
 /* Philox4x32 with 10 rounds: out = Philox(ctr; key). */
@@ -74,13 +84,14 @@ int oracle_draw(uint64_t seed, int32_t cluster, int32_t h, int32_t n, int32_t k,
  * hyp_counts (optional) receives [n_out * H] exact counts (-1 = rejected).
  * fragile (optional) receives 1 for a cluster where some decision that can
  * change the outputs lies within rounding distance of its threshold.
+ * trials_used (optional) receives the number of trials run per cluster.
  * Returns 0, or -1 on invalid arguments. */
 int oracle_estimate(const double* azimuth, const double* elevation, const double* doppler,
                     const int32_t* offsets, int32_t n_clusters,
                     const int32_t* subset, int32_t n_subset, const orc_params* p,
                     double* vx, double* vy, double* vz, double* heading,
                     int32_t* inlier_count, int32_t* best_hypothesis, int32_t* status,
-                    uint8_t* mask, int32_t* hyp_counts, uint8_t* fragile);
+                    uint8_t* mask, int32_t* hyp_counts, uint8_t* fragile, int32_t* trials_used);
 
 #ifdef __cplusplus
 }

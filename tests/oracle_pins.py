@@ -16,6 +16,11 @@ violation.  What pins what:
   lstsq       the refine equals numpy.linalg.lstsq on the inlier rows (the
               least-squares comparator of the paper's Table II)
   status      too-few-points, all-degenerate and least-squares fallback cases
+  adaptive    the adaptive trial count: the winner is the first maximum of the
+              full run's counts over the trials run; the stopping rule
+              (1 - eps^k)^m <= 1 - p, evaluated with Python's float power,
+              holds where the count stopped and at no earlier block end;
+              all-inlier clusters stop after one block
   local_opt   the re-threshold + re-fit rounds: one round's inlier set is
               numpy's re-threshold of the refined velocity, every result is
               numpy.linalg.lstsq of its own inlier set, a converged result is
@@ -348,5 +353,58 @@ def check_local_opt(L):
         assert np.array_equal(many["vx"] * 8.0, sc["vx"]) and np.array_equal(many["vy"] * 8.0, sc["vy"])
 
 
+def _bound_holds(best, n, k, m, p):
+    """(1 - (best/n)^k)^m <= 1 - p by Python's float power, or None when the
+    two sides are too close to call against another evaluation order."""
+    if best < 0:
+        return False
+    lhs = (1.0 - (best / n) ** k) ** m
+    rhs = 1.0 - p
+    if abs(lhs - rhs) <= 1e-9 * max(rhs, 1e-300):
+        return None
+    return lhs <= rhs
+
+
+def check_adaptive(L):
+    for name, nc, H, p, B in (("stress2d", 128, 512, 0.99, 32), ("frame64", 64, 256, 0.999, 64),
+                              ("dense3d", 16, 512, 0.99, 32), ("stress2d", 64, 512, 0.9999999, 32)):
+        w, f = _frame(name, nc)
+        k = 2 if f.elevation is None else 3
+        kw = dict(elevation=f.elevation, num_hypotheses=H, tau=w.tau, seed=2)
+        full = _est(L, f.azimuth, f.doppler, f.offsets, want_counts=True, want_trials=True, **kw)
+        assert (full["trials_used"][np.diff(f.offsets) >= k] == H).all()
+        ad = _est(L, f.azimuth, f.doppler, f.offsets, confidence=p, trial_block=B, want_counts=True,
+                  want_trials=True, **kw)
+        n = np.diff(f.offsets)
+        early = 0
+        for c in range(nc):
+            if n[c] < k:
+                continue
+            m = int(ad["trials_used"][c])
+            assert m == H or m % B == 0, (c, m)
+            cnt = full["hyp_counts"][c]
+            assert np.array_equal(ad["hyp_counts"][c][:m], cnt[:m]) and (ad["hyp_counts"][c][m:] == -1).all()
+            best = int(cnt[:m].max())
+            assert ad["best_hypothesis"][c] == (int(np.argmax(cnt[:m])) if best >= 0 else -1)
+            if best >= 0:
+                assert ad["inlier_count"][c] == best or ad["status"][c] != 0
+            if m < H:
+                early += 1
+                assert _bound_holds(best, int(n[c]), k, m, p) in (True, None), (c, m)
+            for m2 in range(B, m, B):
+                assert _bound_holds(int(cnt[:m2].max()), int(n[c]), k, m2, p) in (False, None), (c, m2)
+            if ad["best_hypothesis"][c] == full["best_hypothesis"][c]:
+                s_, e_ = f.offsets[c], f.offsets[c + 1]
+                assert np.array_equal(ad["inlier_mask"][s_:e_], full["inlier_mask"][s_:e_])
+                assert ad["vx"][c] == full["vx"][c] and ad["vy"][c] == full["vy"][c]
+        assert early >= nc // 2, (name, early)
+    # all-inlier (noise-free) clusters: eps = 1 stops after the first block
+    rng = np.random.default_rng(8)
+    th, _, dop = _noise_free(rng, 50, 2, np.array([12.0, -5.0, 0.0]))
+    o = _est(L, th, dop, [0, 50], num_hypotheses=512, tau=0.1, seed=4, confidence=0.99, trial_block=32,
+             want_trials=True)
+    assert o["trials_used"][0] == 32 and o["inlier_count"][0] == 50
+
+
 ALL_CHECKS = [check_philox, check_draws, check_recovery, check_brute, check_symmetry,
-              check_rotation, check_lstsq, check_status, check_planted, check_local_opt]
+              check_rotation, check_lstsq, check_status, check_planted, check_local_opt, check_adaptive]

@@ -44,6 +44,11 @@ MUTANTS = {
     "lo_winner_velocity": ("double r = residual(k, aq, w[q], vout);", "double r = residual(k, aq, w[q], vb);"),
     "lo_dropped_rhs": ("g2[rr] = fma(aq[rr], w[q], g2[rr]);", "g2[rr] = fma(aq[rr], aq[rr], g2[rr]);"),
     "lo_count_not_updated": ("n_in = n2;", ""),
+    "adaptive_eps_not_powered": ("double ek = k == 2 ? eps * eps : (eps * eps) * eps;", "double ek = eps;"),
+    "adaptive_power_off_by_block": ("adaptive_stop(best_count, n, k, trials, p->confidence))",
+                                    "adaptive_stop(best_count, n, k, trials - p->trial_block + 1, p->confidence))"),
+    "adaptive_every_trial": ("trials % p->trial_block == 0 && trials < H", "trials < H"),
+    "adaptive_pow_skips_bit": ("if (n & 1) r = r * b;", "if (n & 2) r = r * b;"),
 }
 
 
