@@ -209,7 +209,8 @@ def main():
     ap.add_argument("--refine-iterations", type=int, default=0,
                     help="local-optimisation rounds in the timed steps (default 0: the single-pass method)")
     ap.add_argument("--local-opt-steps", type=int, default=50,
-                    help="steps of the extra 2-round local-optimisation measurement (0 skips it)")
+                    help="steps of each extra measurement on the same frame: 2 local-optimisation rounds, "
+                         "and the adaptive trial count at confidence 0.99 (0 skips them)")
     args = ap.parse_args()
     if args.impl == "reference":
         return reference_arm(args)
@@ -359,6 +360,31 @@ def main():
                      "inliers_after_rounds": int(lo_outs["inlier_count"].sum().item()),
                      "steps": args.local_opt_steps}
 
+    # ---- adaptive trial count (confidence 0.99, blocks of 128 trials) on the same frame
+    adaptive = None
+    if args.local_opt_steps > 0 and args.refine_iterations == 0:
+        ad_outs = rvh.alloc_outputs(nc, npts, dev)
+        ad_res = rvh.make_result(ad_outs)
+        ad_params = rvh.make_params(dim, w.num_hypotheses, w.tau, w.seed, confidence=0.99, trial_block=128)
+        ad_ms, ad_trials, ad_pairs = [], 0, 0
+        for i in range(3 + args.local_opt_steps):
+            flush.fill_(6)
+            ctx.check(rvh.rvh_estimate(ctx.handle, frame, ad_params, ad_res, sptr), "rvh_estimate(adaptive)")
+            ctx.check(rvh.rvh_get_stats(ctx.handle, stats), "rvh_get_stats")
+            if i >= 3:
+                ad_ms.append(stats.kernel_ms)
+                ad_trials, ad_pairs = stats.hypotheses, stats.pair_evals
+        torch.cuda.synchronize()
+        ak = float(np.mean(ad_ms))
+        adaptive = {"confidence": 0.99, "trial_block": 128, "kernel_ms": ak, "clusters_per_s": nc / (ak * 1e-3),
+                    "pair_evals_per_s": ad_pairs / (ak * 1e-3), "trials_per_cluster": ad_trials / nc,
+                    "pair_fraction_of_full": ad_pairs / pairs,
+                    "inliers_full": int(outs["inlier_count"].sum().item()),
+                    "inliers_adaptive": int(ad_outs["inlier_count"].sum().item()),
+                    "same_winner_fraction": float((ad_outs["best_hypothesis"] == outs["best_hypothesis"])
+                                                  .float().mean().item()),
+                    "steps": args.local_opt_steps}
+
     # ---- end to end through the C ABI with pinned host buffers (copies inside the timed region)
     h_az = torch.from_numpy(f.azimuth).pin_memory()
     h_el = None if f.elevation is None else torch.from_numpy(f.elevation).pin_memory()
@@ -445,6 +471,7 @@ def main():
             "gpu_baseline": gpu_base,
             "serving": serve,
             "local_opt": local_opt,
+            "adaptive": adaptive,
             "e2e": e2e,
             "clocks": clocks,
             "gpu_launches": launches,

@@ -98,7 +98,23 @@ typedef struct {
                                 its first cluster there, so its results equal the whole's) */
   int32_t refine_iterations; /* local-optimisation rounds after the refine, 0 (none) ..
                                 RVH_MAX_REFINE_ITERATIONS; see below */
+  double confidence;         /* 0: every cluster runs all num_hypotheses trials;
+                                in (0, 1): adaptive trial count, see below */
+  int32_t trial_block;       /* adaptive: trials between stopping checks, a multiple of 32
+                                in [32, 1024]; 0 selects 128.  Ignored when confidence is 0 */
 } rvh_params;
+
+/* Adaptive trial count (confidence p > 0).  Sec. III-A tunes max_trials to
+ * the hardware and cites work on optimal RANSAC; here each cluster runs its
+ * trials in index order in blocks of trial_block, and after a block stops
+ * once (1 - eps^k)^m <= 1 - p, where m is the number of trials run and eps
+ * the best inlier count so far divided by the cluster's N: the standard
+ * bound on the chance that every trial so far drew an outlier.  The power
+ * is evaluated by binary exponentiation (lowest bit first), one FP64
+ * rounding per operation, so the decision is reproducible.  The winner is
+ * the lowest-index trial with the largest count among the trials run;
+ * rvh_stats.hypotheses / pair_evals count the trials actually run.  Not
+ * supported by rvh_estimate_baseline (RVH_EINVAL). */
 
 /* Local optimisation (refine_iterations > 0).  Sec. III-B computes the
  * velocity "subsequent to" inlier detection; these rounds repeat that step.
@@ -112,6 +128,7 @@ typedef struct {
  * best_hypothesis stays the RANSAC winner.  A cluster whose first refine
  * fell back (RVH_STATUS_LSQ_FALLBACK) is left as it is.  Not supported by
  * rvh_estimate_baseline (RVH_EINVAL). */
+#define RVH_DEFAULT_TRIAL_BLOCK 128
 #define RVH_MAX_REFINE_ITERATIONS 64
 
 /* Caller-owned, caller-sized outputs.  Per-cluster arrays have n_clusters
@@ -208,8 +225,8 @@ const char* rvh_last_error(rvh_ctx* ctx);
 
 /* ---- measurement and tuning ------------------------------------------------------ */
 typedef struct {
-  int64_t hypotheses;          /* trials scored (sum over clusters of H) */
-  int64_t pair_evals;          /* trial x point evaluations in the scoring pass */
+  int64_t hypotheses;          /* trials run (sum over clusters with N >= k of the trials drawn) */
+  int64_t pair_evals;          /* trial x point evaluations in the scoring pass (sum of trials x N) */
   int64_t candidates;          /* trials re-scored exactly (upper bound reached the lead) */
   int64_t band_points;         /* point decisions taken in FP64 (inside the error band) */
   int64_t fp64_hypotheses;     /* trials whose conditioning or bound needed FP64 */

@@ -65,6 +65,10 @@ int check_args(const rvh_frame* f, const rvh_params* p, const rvh_result* r) {
     return fail(RVH_EINVAL, "first_cluster out of range");
   if (p->refine_iterations < 0 || p->refine_iterations > RVH_MAX_REFINE_ITERATIONS)
     return fail(RVH_EINVAL, "refine_iterations out of range [0, RVH_MAX_REFINE_ITERATIONS]");
+  if (!(p->confidence >= 0.0 && p->confidence < 1.0)) return fail(RVH_EINVAL, "confidence must be in [0, 1)");
+  if (p->confidence > 0.0 && p->trial_block != 0 &&
+      (p->trial_block < 32 || p->trial_block > 1024 || p->trial_block % 32 != 0))
+    return fail(RVH_EINVAL, "trial_block must be 0 or a multiple of 32 in [32, 1024]");
   if (f->n_points > 0 && (!f->azimuth || !f->doppler)) return fail(RVH_EINVAL, "azimuth/doppler NULL");
   if (f->n_clusters > 0 && !f->cluster_offsets) return fail(RVH_EINVAL, "cluster_offsets NULL");
   if (f->n_clusters > 0 && (!r->vx || !r->vy || !r->heading || !r->inlier_count || !r->best_hypothesis || !r->status))
@@ -83,6 +87,13 @@ int check_host_offsets(const int32_t* off, int32_t n, int64_t n_points) {
 }
 
 double default_eps(int dim) { return dim == 2 ? 1e-4 : 1e-6; }
+
+// Trials the fused kernel scores together in one chunk: the adaptive block,
+// or all of them (the scoring schedule is chosen and tuned for this size).
+int trials_per_chunk(const rvh_params& p) {
+  if (p.confidence > 0.0) return std::min(p.num_hypotheses, p.trial_block ? p.trial_block : RVH_DEFAULT_TRIAL_BLOCK);
+  return p.num_hypotheses;
+}
 
 rvh::TauPair tau_pair(double tau) {
   float f = (float)tau;
@@ -213,6 +224,8 @@ void fill_desc(rvh_ctx* ctx, FrameDesc& d, const rvh_frame& f, const rvh_params&
   d.key = make_uint2((uint32_t)(p.seed & 0xFFFFFFFFu), (uint32_t)(p.seed >> 32));
   d.cluster_base = p.first_cluster;
   d.lo_iters = p.refine_iterations;
+  d.confidence = p.confidence;
+  d.trial_block = p.confidence > 0.0 ? (p.trial_block ? p.trial_block : RVH_DEFAULT_TRIAL_BLOCK) : 0;
   d.vx = out.vx;
   d.vy = out.vy;
   d.vz = out.vz;
@@ -273,7 +286,7 @@ int launch_graph(rvh_ctx* ctx, FusedArgs& a, int dim, cudaStream_t s) {
   size_t smem = 0;
   int rc = prepare_launch(ctx, a, dim, &grid, &smem);
   if (rc) return rc;
-  RVH_CUDA(cudaMemsetAsync(a.stats, 0, 80, s));
+  RVH_CUDA(cudaMemsetAsync(a.stats, 0, 96, s));
   if (!a.direct) RVH_CUDA(launch_worklist(a, s));
   std::vector<char> key(sizeof(FusedArgs) + 3 * sizeof(int64_t));
   memcpy(key.data(), &a, sizeof(FusedArgs));
@@ -439,8 +452,10 @@ int rvh_get_stats(rvh_ctx* ctx, rvh_stats* out) {
   RVH_CUDA(cudaSetDevice(ctx->device));
   if (ctx->have_launch) {
     RVH_CUDA(cudaEventSynchronize(ctx->last_done));
-    unsigned long long h[10] = {0, 0, 0, 0, 0, 0, 0, 0, 0, 0};
+    unsigned long long h[12] = {0, 0, 0, 0, 0, 0, 0, 0, 0, 0, 0, 0};
     RVH_CUDA(cudaMemcpy(h, ctx->stats_d, sizeof(h), cudaMemcpyDeviceToHost));
+    ctx->last.hypotheses = (int64_t)h[10];
+    ctx->last.pair_evals = (int64_t)h[11];
     for (int k = 0; k < 6; ++k) ctx->last.phase_cycles[k] = (int64_t)h[4 + k];
     ctx->last.refined_hypotheses = (int64_t)h[3];
     ctx->last.graph_replays = ctx->graph_replays;
@@ -589,18 +604,16 @@ int rvh_estimate(rvh_ctx* ctx, const rvh_frame* frame, const rvh_params* params,
   a.worklist = st.worklist;
   a.work_counter = st.counter;
   a.stats = st.stats;
-  choose_schedule(ctx, params->model_dim, params->num_hypotheses, &a.pw, &a.hpl);
+  choose_schedule(ctx, params->model_dim, trials_per_chunk(*params), &a.pw, &a.hpl);
   cudaStreamCaptureStatus cap = cudaStreamCaptureStatusNone;
   RVH_CUDA(cudaStreamIsCapturing(s, &cap));
   if (ctx->graphs && !st.staged_any && s != nullptr && cap == cudaStreamCaptureStatusNone) {
     rc = launch_graph(ctx, a, params->model_dim, s);
   } else {
-    RVH_CUDA(cudaMemsetAsync(st.stats, 0, 80, s));
+    RVH_CUDA(cudaMemsetAsync(st.stats, 0, 96, s));
     rc = launch_batch(ctx, a, params->model_dim, s, ctx->ev0, ctx->ev1);
   }
   if (rc) return rc;
-  ctx->last.hypotheses = (int64_t)frame->n_clusters * params->num_hypotheses;
-  ctx->last.pair_evals = frame->n_points * (int64_t)params->num_hypotheses;
   ctx->last.points_per_warp = a.pw;
   ctx->last.hyps_per_lane = a.hpl;
   ctx->have_launch = true;
@@ -614,8 +627,8 @@ int rvh_estimate_baseline(rvh_ctx* ctx, const rvh_frame* frame, const rvh_params
   if (!ctx) return fail(RVH_EINVAL, "ctx is NULL");
   int rc = check_args(frame, params, result);
   if (rc) return rc;
-  if (params->refine_iterations != 0)
-    return fail(RVH_EINVAL, "rvh_estimate_baseline runs the method without local optimisation (refine_iterations 0)");
+  if (params->refine_iterations != 0 || params->confidence != 0.0)
+    return fail(RVH_EINVAL, "rvh_estimate_baseline runs the plain method (refine_iterations 0, confidence 0)");
   if (frame->n_clusters == 0) return RVH_OK;
   std::lock_guard<std::mutex> lk(ctx->mu);
   RVH_CUDA(cudaSetDevice(ctx->device));
@@ -695,7 +708,7 @@ int rvh_autotune(rvh_ctx* ctx, const rvh_frame* frame, const rvh_params* params,
   ctx->pw_fixed = save_pw;
   ctx->hpl_fixed = save_hpl;
   if (rc) return rc;
-  const int key = tune_key(params->model_dim, params->num_hypotheses);
+  const int key = tune_key(params->model_dim, trials_per_chunk(*params));
   ctx->tuned[key] = std::make_pair(bpw, bhpl);
   save_tune_cache(ctx, key, bpw, bhpl, bms);
   if (best) {

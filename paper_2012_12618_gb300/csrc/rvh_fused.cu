@@ -194,7 +194,7 @@ struct ClusterShared {
   int red_i[kWarps];
   float red_f[kWarps];
   double red_t[9];            // the normal-equation sums of the winner's inliers
-  unsigned long long ctr[4];  // exact counts, band points, fp64 trials, refined trials
+  unsigned long long ctr[6];  // exact counts, band points, fp64 trials, refined trials, trials run, pairs scored
   unsigned long long clk[6];  // cycles per stage (thread 0's view of the CTA)
   unsigned long long red_u[kWarps];
   double cv64[3];             // FP64 velocity of the trial being counted (when it has band points)
@@ -205,7 +205,27 @@ struct ClusterShared {
   float4 lo_hy;               // its FP32 record (-X, -Y, -Z, thi) and lower threshold
   float lo_tlo;
   int lo_ok;
+  int stop;                   // adaptive trial count: enough trials have run
 };
+
+// Adaptive trial count: with `best` the best (count + 1, -index) key so far,
+// n points, k = DIM and m trials run, true once (1 - eps^k)^m <= 1 - p for
+// eps = count / n: the standard RANSAC bound on the chance that every trial
+// so far drew an outlier.  The power is taken by binary exponentiation in
+// the same order as the oracle's, one IEEE rounding per operation, so both
+// decide alike.  One thread; kept out of line.
+__device__ __noinline__ int adaptive_stop(unsigned long long best, int n, int k, int m, double p) {
+  const int count = (int)(best >> 32) - 1;
+  if (count < 0) return 0;
+  const double eps = (double)count / (double)n;
+  const double ek = k == 2 ? eps * eps : (eps * eps) * eps;
+  double r = 1.0, b = 1.0 - ek;
+  for (int e = m; e > 0; e >>= 1) {
+    if (e & 1) r = r * b;
+    b = b * b;
+  }
+  return r <= 1.0 - p ? 1 : 0;
+}
 
 // FP32 record of an FP64 velocity v for the re-threshold of a local
 // optimisation round: X = fl32(v), e >= |X - v|, the band of band_f32 around
@@ -494,7 +514,7 @@ __device__ __noinline__ int local_opt_rounds(const FrameDesc& a, const RV rows, 
   return n_in;
 }
 
-template <int DIM, bool SMEM_ROWS, bool LO>
+template <int DIM, bool SMEM_ROWS, bool EXT>
 __device__ void process_cluster(const FrameDesc& a, const Smem& S, ClusterShared& cs, int ci, int hchunk,
                                 int pw, int hpl, int frame, FinishRec* fq, int* fq_n) {
   const int tid = threadIdx.x;
@@ -558,8 +578,11 @@ __device__ void process_cluster(const FrameDesc& a, const Smem& S, ClusterShared
   unsigned long long n_fp64 = 0, n_cand = 0, n_ref = 0;
   stage_done(0);
 
-  for (int hc0 = 0; hc0 < a.H; hc0 += hchunk) {
-    const int nh = min(hchunk, a.H - hc0);
+  // trials run in chunks of hchunk, or in the adaptive blocks of trial_block
+  const int chunk = (EXT && a.trial_block > 0) ? a.trial_block : hchunk;
+  int trials_run = 0;
+  for (int hc0 = 0; hc0 < a.H; hc0 += chunk) {
+    const int nh = min(chunk, a.H - hc0);
     // a2 + a3: draw, FP32 solve (refined when ill-conditioned), bound
     for (int hl = tid; hl < nh; hl += kThreads) {
       int q[3];
@@ -652,9 +675,22 @@ __device__ void process_cluster(const FrameDesc& a, const Smem& S, ClusterShared
     }
     __syncthreads();
     stage_done(3);
+    trials_run = hc0 + nh;
+    if constexpr (EXT) {
+      // adaptive trial count: stop once the bound says enough trials have run
+      if (a.confidence > 0.0 && trials_run < a.H) {
+        if (tid == 0) cs.stop = adaptive_stop(cs.best, N, DIM, trials_run, a.confidence);
+        __syncthreads();
+        if (cs.stop) break;
+      }
+    }
   }
 
-  if (tid == 0) cs.ctr[0] += n_cand;
+  if (tid == 0) {
+    cs.ctr[0] += n_cand;
+    cs.ctr[4] += (unsigned long long)trials_run;
+    cs.ctr[5] += (unsigned long long)trials_run * (unsigned long long)N;
+  }
   if (n_fp64) atomicAdd(&cs.ctr[2], n_fp64);
   if (n_ref) atomicAdd(&cs.ctr[3], n_ref);
 
@@ -676,7 +712,7 @@ __device__ void process_cluster(const FrameDesc& a, const Smem& S, ClusterShared
   constexpr int NS = DIM == 2 ? 5 : 9;
   int n_in = mask_and_sums<DIM, RV>(a, rows, R, o, N, win, wtlo, v64, S, cs, false, nullptr);
 
-  if constexpr (LO) {
+  if constexpr (EXT) {
     if (a.lo_iters > 0) n_in = local_opt_rounds<DIM, RV>(a, rows, R, o, N, win, wtlo, v64, wmax, n_in, S, cs);
   }
   if (tid == 0) {
@@ -699,10 +735,11 @@ __device__ void process_cluster(const FrameDesc& a, const Smem& S, ClusterShared
   stage_done(4);
 }
 
-// LO = true: the instantiation with the local-optimisation rounds, launched
-// only for batches that ask for them (the default instantiation carries no
-// trace of them).
-template <int DIM, bool LO>
+// EXT = true: the instantiation with the extensions of the method (the
+// local-optimisation rounds and the adaptive trial count), launched only for
+// batches that ask for one of them; the default instantiation carries no
+// trace of them.
+template <int DIM, bool EXT>
 __global__ void __launch_bounds__(kThreads, RVH_MIN_BLOCKS) fused_kernel(const __grid_constant__ FusedArgs a) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   __shared__ ClusterShared cs;
@@ -721,7 +758,7 @@ __global__ void __launch_bounds__(kThreads, RVH_MIN_BLOCKS) fused_kernel(const _
   p += (size_t)a.hchunk * sizeof(int);
   S.kind = reinterpret_cast<int8_t*>(p);
 
-  if (threadIdx.x < 4) cs.ctr[threadIdx.x] = 0ull;
+  if (threadIdx.x < 6) cs.ctr[threadIdx.x] = 0ull;
   if (threadIdx.x < 6) cs.clk[threadIdx.x] = 0ull;
   if (threadIdx.x == 0) fq_n = 0;
   // the queued clusters' solves and headings, one lane each
@@ -758,9 +795,9 @@ __global__ void __launch_bounds__(kThreads, RVH_MIN_BLOCKS) fused_kernel(const _
     const int ci = fc.y;
     const int64_t o = F.offsets[ci], e = F.offsets[ci + 1];
     if (e - o <= (int64_t)a.nmax_smem || e < o) {
-      process_cluster<DIM, true, LO>(F, S, cs, ci, a.hchunk, a.pw, a.hpl, fc.x, fq, &fq_n);
+      process_cluster<DIM, true, EXT>(F, S, cs, ci, a.hchunk, a.pw, a.hpl, fc.x, fq, &fq_n);
     } else {
-      process_cluster<DIM, false, LO>(F, S, cs, ci, a.hchunk, a.pw, a.hpl, fc.x, fq, &fq_n);
+      process_cluster<DIM, false, EXT>(F, S, cs, ci, a.hchunk, a.pw, a.hpl, fc.x, fq, &fq_n);
     }
     __syncthreads();
     if (fq_n == kFinishBatch) flush();
@@ -779,13 +816,15 @@ __global__ void __launch_bounds__(kThreads, RVH_MIN_BLOCKS) fused_kernel(const _
     if (v) atomicAdd(&a.stats[threadIdx.x], v);
   }
   if (threadIdx.x < 6 && a.stats) atomicAdd(&a.stats[4 + threadIdx.x], cs.clk[threadIdx.x]);
+  if (threadIdx.x < 2 && a.stats) atomicAdd(&a.stats[10 + threadIdx.x], cs.ctr[4 + threadIdx.x]);
 }
 
 // Orders the batch's (frame, cluster) items by decreasing floor(log2(N * H))
+// (H: the trial_block of adaptive frames, which mostly stop after one block)
 // (longest-processing-time first) and resets the work counter.  One CTA.
 __device__ __forceinline__ int item_bucket(const FrameDesc& F, int ci) {
   const int64_t n = (int64_t)F.offsets[ci + 1] - F.offsets[ci];
-  const int64_t cost = n > 0 ? n * (int64_t)F.H : 1;
+  const int64_t cost = n > 0 ? n * (int64_t)(F.trial_block > 0 ? min(F.trial_block, F.H) : F.H) : 1;
   return 63 - min(63 - __clzll(cost), 63);  // 0 = most expensive
 }
 
@@ -843,13 +882,13 @@ cudaError_t fused_occupancy(int dim, size_t smem, int* blocks_per_sm) {
 }
 
 cudaError_t launch_fused(int dim, const FusedArgs& a, int grid, size_t smem, cudaStream_t s) {
-  bool lo = false;
-  for (int f = 0; f < a.n_frames; ++f) lo = lo || a.f[f].lo_iters > 0;
+  bool ext = false;
+  for (int f = 0; f < a.n_frames; ++f) ext = ext || a.f[f].lo_iters > 0 || a.f[f].confidence > 0.0;
   if (dim == 2) {
-    if (lo) fused_kernel<2, true><<<grid, kThreads, smem, s>>>(a);
+    if (ext) fused_kernel<2, true><<<grid, kThreads, smem, s>>>(a);
     else fused_kernel<2, false><<<grid, kThreads, smem, s>>>(a);
   } else {
-    if (lo) fused_kernel<3, true><<<grid, kThreads, smem, s>>>(a);
+    if (ext) fused_kernel<3, true><<<grid, kThreads, smem, s>>>(a);
     else fused_kernel<3, false><<<grid, kThreads, smem, s>>>(a);
   }
   return cudaGetLastError();

@@ -36,6 +36,8 @@ struct FrameDesc {
   uint2 key;                 // Philox key = seed
   int32_t cluster_base;      // Philox cluster counter = cluster_base + cluster index
   int32_t lo_iters;          // local-optimisation rounds after the refine (0 = none)
+  double confidence;         // adaptive trial count: p in (0, 1), 0 = all H trials
+  int32_t trial_block;       // adaptive: trials per block between checks (0 = not adaptive)
   double* vx;
   double* vy;
   double* vz;
@@ -55,7 +57,8 @@ struct FusedArgs {
   int n_items;               // sum of n_clusters over the frames
   int2* worklist;            // [n_items] (frame, cluster), written by the worklist kernel
   int* work_counter;
-  unsigned long long* stats;  // [4 + 6]: exact counts, band points, fp64 trials, refined trials, stage cycles
+  unsigned long long* stats;  // [4 + 6 + 2]: exact counts, band points, fp64 trials, refined trials,
+                              // stage cycles, trials run, pairs scored
   int nmax_smem;
   int hchunk;
   int pw, hpl;

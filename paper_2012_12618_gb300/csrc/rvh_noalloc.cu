@@ -114,6 +114,10 @@ extern "C" int rvh_estimate_noalloc(const rvh_frame* f, const rvh_params* p, rvh
     return rvh::set_error(RVH_EINVAL, "first_cluster out of range");
   if (p->refine_iterations < 0 || p->refine_iterations > RVH_MAX_REFINE_ITERATIONS)
     return rvh::set_error(RVH_EINVAL, "refine_iterations out of range [0, RVH_MAX_REFINE_ITERATIONS]");
+  if (!(p->confidence >= 0.0 && p->confidence < 1.0)) return rvh::set_error(RVH_EINVAL, "confidence must be in [0, 1)");
+  if (p->confidence > 0.0 && p->trial_block != 0 &&
+      (p->trial_block < 32 || p->trial_block > 1024 || p->trial_block % 32 != 0))
+    return rvh::set_error(RVH_EINVAL, "trial_block must be 0 or a multiple of 32 in [32, 1024]");
   if (f->n_clusters == 0) return f->n_points == 0 ? RVH_OK : rvh::set_error(RVH_EINVAL, "points without clusters");
   const void* ptrs[11] = {f->azimuth, f->doppler, f->cluster_offsets, r->vx, r->vy, r->heading, r->inlier_count,
                           r->best_hypothesis, r->status, r->inlier_mask, p->model_dim == 3 ? f->elevation : f->azimuth};
@@ -153,6 +157,8 @@ extern "C" int rvh_estimate_noalloc(const rvh_frame* f, const rvh_params* p, rvh
   fd.key = make_uint2((uint32_t)(p->seed & 0xFFFFFFFFu), (uint32_t)(p->seed >> 32));
   fd.cluster_base = p->first_cluster;
   fd.lo_iters = p->refine_iterations;
+  fd.confidence = p->confidence;
+  fd.trial_block = p->confidence > 0.0 ? (p->trial_block ? p->trial_block : RVH_DEFAULT_TRIAL_BLOCK) : 0;
   fd.vx = r->vx;
   fd.vy = r->vy;
   fd.vz = r->vz;
@@ -168,7 +174,8 @@ extern "C" int rvh_estimate_noalloc(const rvh_frame* f, const rvh_params* p, rvh
   a.stats = nullptr;
   a.nmax_smem = kNmaxSmem;
   a.hchunk = kHchunk;
-  if (p->num_hypotheses >= 1024) {
+  // the scoring schedule follows the trials scored together (the adaptive block, or all)
+  if ((fd.trial_block > 0 ? std::min(fd.trial_block, p->num_hypotheses) : p->num_hypotheses) >= 1024) {
     a.pw = 1;
     a.hpl = 4;
   } else {

@@ -420,7 +420,8 @@ void Server::loop() {
     a.work_counter = (int*)(sb + gran(sizeof(int2) * (size_t)kStepItems));
     a.stats = nullptr;
     int Hmax = 1;
-    for (int i = 0; i < nf; ++i) Hmax = std::max(Hmax, a.f[i].H);
+    for (int i = 0; i < nf; ++i)
+      Hmax = std::max(Hmax, a.f[i].trial_block > 0 ? std::min(a.f[i].trial_block, a.f[i].H) : a.f[i].H);
     choose_schedule(ctx, dimsel ? 3 : 2, Hmax, &a.pw, &a.hpl);
     int rc = RVH_OK;
     if (n_items > 0) rc = launch_batch(ctx, a, dimsel ? 3 : 2, slot->stream, nullptr, nullptr);

@@ -22,7 +22,8 @@ def alloc_outputs(n_clusters: int, n_points: int, device: str):
 
 
 def run_rvh(ctx, az, dop, off, *, el=None, H: int, tau: float, seed: int, cond_eps: float = 0.0,
-            baseline: bool = False, device: str = "cuda", stream=None, refine_iterations: int = 0) -> dict:
+            baseline: bool = False, device: str = "cuda", stream=None, refine_iterations: int = 0,
+            confidence: float = 0.0, trial_block: int = 0) -> dict:
     """Runs rvh_estimate (or the baseline) through the C ABI and returns numpy outputs."""
     torch = torch_mod()
     from paper_2012_12618_gb300 import rvh
@@ -36,7 +37,8 @@ def run_rvh(ctx, az, dop, off, *, el=None, H: int, tau: float, seed: int, cond_e
     outs = alloc_outputs(int(np.asarray(off).shape[0]) - 1, n_points, device)
     frame = rvh.make_frame(taz, tdop, toff, tel)
     params = rvh.make_params(3 if el is not None else 2, H, tau, seed, cond_eps,
-                             refine_iterations=refine_iterations)
+                             refine_iterations=refine_iterations, confidence=confidence,
+                             trial_block=trial_block)
     res = rvh.make_result(outs)
     fn = rvh.rvh_estimate_baseline if baseline else rvh.rvh_estimate
     rc = fn(ctx.handle, frame, params, res, stream)
@@ -50,10 +52,12 @@ def run_rvh(ctx, az, dop, off, *, el=None, H: int, tau: float, seed: int, cond_e
 
 
 def run_oracle(az, dop, off, *, el=None, H: int, tau: float, seed: int, cond_eps=None, subset=None,
-               refine_iterations: int = 0) -> dict:
+               refine_iterations: int = 0, confidence: float = 0.0, trial_block: int = 128,
+               want_trials: bool = False) -> dict:
     return oracle.estimate(az, dop, off, elevation=el, num_hypotheses=H, tau=tau, seed=seed,
                            cond_eps=cond_eps, subset=subset, want_fragile=True,
-                           refine_iterations=refine_iterations)
+                           refine_iterations=refine_iterations, confidence=confidence,
+                           trial_block=trial_block, want_trials=want_trials)
 
 
 def compare(gpu: dict, orc: dict, off, *, subset=None, vel_tol: float = 1e-6, head_tol: float = 1e-6) -> dict:

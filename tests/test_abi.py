@@ -53,12 +53,18 @@ def test_create_without_gpu_reports_cuda_error():
 
 
 def test_params_layout_and_refine_range():
-    # rvh_params as declared in include/rvh.h: 40 bytes, refine_iterations last
-    assert ctypes.sizeof(rvh.rvh_params) == 40
+    # rvh_params as declared in include/rvh.h
+    assert ctypes.sizeof(rvh.rvh_params) == 56
     assert rvh.rvh_params.refine_iterations.offset == 36
+    assert rvh.rvh_params.confidence.offset == 40 and rvh.rvh_params.trial_block.offset == 48
     f = rvh.rvh_frame()
     r = rvh.rvh_result()
     for bad in (-1, 65):
         p = rvh.make_params(2, 8, 0.1, 1, refine_iterations=bad)
         assert rvh.rvh_estimate_noalloc(f, p, r, None) == rvh.RVH_EINVAL
         assert "refine_iterations" in rvh.rvh_last_error(None)
+    for conf, block in ((1.0, 0), (-0.5, 0), (float("nan"), 0), (0.9, 16), (0.9, 2048), (0.9, 100)):
+        p = rvh.make_params(2, 8, 0.1, 1, confidence=conf, trial_block=block)
+        assert rvh.rvh_estimate_noalloc(f, p, r, None) == rvh.RVH_EINVAL
+        msg = rvh.rvh_last_error(None)
+        assert "confidence" in msg or "trial_block" in msg, msg
