@@ -167,6 +167,27 @@ static int adaptive_stop(int32_t best, int32_t n, int k, int32_t m, double p) {
   return pow_uint(1.0 - ek, m) <= 1.0 - p;
 }
 
+static int cmp_double(const void* a, const void* b) {
+  double x = *(const double*)a, y = *(const double*)b;
+  return (x > y) - (x < y);
+}
+
+/* Median of v[0..n-1] (n >= 1); v is reordered.  Even n: the mean of the two
+ * middle values, 0.5 * (lo + hi). */
+static double median(double* v, int32_t n) {
+  qsort(v, (size_t)n, sizeof(double), cmp_double);
+  if (n & 1) return v[n / 2];
+  return 0.5 * (v[n / 2 - 1] + v[n / 2]);
+}
+
+/* Alg. 1 point-to-line test: perpendicular distance of (x, y) to
+ * y = m x + c, with aa = -m, bb = 1, cc = -c, evaluated as printed:
+ * distn = aa x + bb y + cc, distd = sqrt(aa^2 + bb^2), dist = |distn / distd|. */
+static int line_inlier(double m, double c, double distd, double x, double y, double thresh) {
+  double distn = (-m) * x + 1.0 * y + (-c);
+  return fabs(distn / distd) <= thresh;
+}
+
 static void write_invalid(int32_t out, double* vx, double* vy, double* vz, double* heading,
                           int32_t* inlier_count, int32_t* best, int32_t* status, int32_t bits) {
   vx[out] = NAN;
@@ -191,6 +212,7 @@ int oracle_estimate(const double* azimuth, const double* elevation, const double
   if (p->num_hypotheses < 1 || !(p->tau >= 0.0)) return -1;
   if (!(p->confidence >= 0.0 && p->confidence < 1.0)) return -1;
   if (p->confidence > 0.0 && p->trial_block < 1) return -1;
+  if (p->line_model && (k != 2 || p->refine_iterations != 0)) return -1;
   const int32_t H = p->num_hypotheses;
   const double tau = p->tau;
   const int32_t n_out = subset ? n_subset : n_clusters;
@@ -236,6 +258,36 @@ int oracle_estimate(const double* azimuth, const double* elevation, const double
       w[q] = doppler[o + q];
     }
 
+    /* Alg. 1 as printed (line_model): normalised (azimuth, Doppler) points
+     * and the cluster's MAD threshold (Eq. eq:MAD, read as med |y - med y|). */
+    double* xn = NULL;
+    double* yn = NULL;
+    double thresh = 0.0;
+    if (p->line_model) {
+      xn = (double*)malloc(sizeof(double) * (size_t)n);
+      yn = (double*)malloc(sizeof(double) * (size_t)n);
+      double tmin = azimuth[o], tmax = azimuth[o], vmin = w[0], vmax = w[0];
+      for (int32_t q = 1; q < n; ++q) {
+        double t = azimuth[o + q];
+        if (t < tmin) tmin = t;
+        if (t > tmax) tmax = t;
+        if (w[q] < vmin) vmin = w[q];
+        if (w[q] > vmax) vmax = w[q];
+      }
+      double rt = tmax > tmin ? 1.0 / (tmax - tmin) : 0.0;
+      double rv = vmax > vmin ? 1.0 / (vmax - vmin) : 0.0;
+      for (int32_t q = 0; q < n; ++q) {
+        xn[q] = (azimuth[o + q] - tmin) * rt;
+        yn[q] = (w[q] - vmin) * rv;
+      }
+      double* tmp = (double*)malloc(sizeof(double) * (size_t)n);
+      for (int32_t q = 0; q < n; ++q) tmp[q] = yn[q];
+      double med = median(tmp, n);
+      for (int32_t q = 0; q < n; ++q) tmp[q] = fabs(yn[q] - med);
+      thresh = median(tmp, n);
+      free(tmp);
+    }
+
     /* Alg. 1 for every trial h: draw the minimal set, solve it, count the
      * points within tau.  The winner is the first trial with the largest
      * count (Sec. III-A). */
@@ -253,6 +305,25 @@ int oracle_estimate(const double* azimuth, const double* elevation, const double
         int drawn = p->enumerate ? enumerate_subset(h, n, k, qs)
                                  : oracle_draw(p->seed, ci, h, n, k, qs);
         if (drawn != 0) break;
+        if (p->line_model) {
+          /* Alg. 1: slope and intercept through the two normalised seeds */
+          double dx = xn[qs[1]] - xn[qs[0]];
+          if (dx == 0.0) break;
+          double m = (yn[qs[1]] - yn[qs[0]]) / dx;
+          double c = yn[qs[0]] - m * xn[qs[0]];
+          double distd = sqrt(m * m + 1.0);
+          int32_t count = 0;
+          for (int32_t q = 0; q < n; ++q) count += line_inlier(m, c, distd, xn[q], yn[q], thresh);
+          counts[h] = count;
+          hyp_v[3 * h + 0] = m;
+          hyp_v[3 * h + 1] = c;
+          hyp_v[3 * h + 2] = distd;
+          if (count > best_count) {
+            best_count = count;
+            best = h;
+          }
+          break;
+        }
         double rhs[3] = {w[qs[0]], w[qs[1]], k == 3 ? w[qs[2]] : 0.0};
         double v[3] = {0.0, 0.0, 0.0};
         int ok = 0;
@@ -288,7 +359,7 @@ int oracle_estimate(const double* azimuth, const double* elevation, const double
       write_invalid(oi, vx, vy, vz, heading, inlier_count, best_hypothesis, status,
                     ORC_ALL_DEGENERATE);
       if (fragile) fragile[oi] = (uint8_t)frag;
-      free(a); free(w); free(counts); free(hyp_v); free(hyp_det);
+      free(a); free(w); free(counts); free(hyp_v); free(hyp_det); free(xn); free(yn);
       continue;
     }
 
@@ -296,7 +367,7 @@ int oracle_estimate(const double* azimuth, const double* elevation, const double
      * count whose margin |(|r| - tau)| is below what a few-ulp change of the
      * row values (another libm's cos/sin) can move it: the trial's velocity
      * moves by ~ulp * |v| / |det| and the residual by that times |a| <= 1. */
-    if (fragile) {
+    if (fragile && !p->line_model) {
       for (int32_t h = 0; h < trials && !frag; ++h) {
         if (counts[h] < 0 || counts[h] < best_count - 1) continue;
         const double* v = &hyp_v[3 * h];
@@ -318,7 +389,9 @@ int oracle_estimate(const double* azimuth, const double* elevation, const double
     double g[3] = {0, 0, 0};
     for (int32_t q = 0; q < n; ++q) {
       const double* aq = &a[3 * q];
-      if (!(fabs(residual(k, aq, w[q], vb)) <= tau)) continue;
+      int in = p->line_model ? line_inlier(vb[0], vb[1], vb[2], xn[q], yn[q], thresh)
+                             : fabs(residual(k, aq, w[q], vb)) <= tau;
+      if (!in) continue;
       mask[o + q] = 1;
       ++n_in;
       for (int r = 0; r < k; ++r) {
@@ -354,6 +427,7 @@ int oracle_estimate(const double* azimuth, const double* elevation, const double
       cnd = (k == 2 ? trace * trace : trace * trace * trace) / fabs(detG);
     } else {
       st |= ORC_LSQ_FALLBACK;
+      if (p->line_model) vout[0] = vout[1] = vout[2] = NAN;
     }
 
     /* Local optimisation rounds: re-threshold all points against the current
@@ -417,7 +491,7 @@ int oracle_estimate(const double* azimuth, const double* elevation, const double
     best_hypothesis[oi] = best;
     status[oi] = st;
     if (fragile) fragile[oi] = (uint8_t)frag;
-    free(a); free(w); free(counts); free(hyp_v); free(hyp_det);
+    free(a); free(w); free(counts); free(hyp_v); free(hyp_det); free(xn); free(yn);
   }
   return 0;
 }

@@ -42,7 +42,21 @@
  *     trials run and eps = best count / N the best inlier ratio so far (the
  *     standard bound on the chance that every trial drew an outlier).  The
  *     power is taken by binary exponentiation in a fixed order, so that any
- *     IEEE implementation decides the same way.
+ *     IEEE implementation decides the same way;
+ *   - line_model = 1 follows Alg. 1 as printed instead of the cosine model:
+ *     each point's (azimuth, Doppler) is normalised per cluster (the paper
+ *     does not define normalize(); here min-max scaling to [0, 1]:
+ *     x = (t - t_min) * (1 / (t_max - t_min)), 0 when the range is 0), a
+ *     trial fits the line y = m x + c through its two seed points (rejected
+ *     when they share x), and a point is an inlier when its perpendicular
+ *     distance |aa x + bb y + cc| / sqrt(aa^2 + bb^2), aa = -m, bb = 1,
+ *     cc = -c, evaluated left to right as printed, is within thresh[cluster];
+ *     the threshold is the median absolute deviation of the normalised
+ *     Doppler (Eq. eq:MAD prints the mean of signed deviations from the
+ *     median, which is not a dispersion; read as med(|y - med(y)|), medians
+ *     of even counts the mean of the two middle values).  The refine is
+ *     Eq. eq:LSQPerCluster on the winner's inliers as before; when it is
+ *     singular the outputs are NaN (a line has no velocity to fall back to).
  */
 #ifndef RVH_ORACLE_H
 #define RVH_ORACLE_H
@@ -67,6 +81,8 @@ typedef struct {
   int32_t refine_iterations; /* >= 0: re-threshold + re-fit rounds after the refine */
   double confidence;      /* 0: all H trials; in (0, 1): adaptive trial count */
   int32_t trial_block;    /* adaptive: trials between stopping checks (B >= 1) */
+  int32_t line_model;     /* 1: Alg. 1 as printed (2D only): normalised line fits,
+                             perpendicular distance, MAD threshold; tau unused */
 } orc_params;
 
 /* Philox4x32 with 10 rounds: out = Philox(ctr; key). */

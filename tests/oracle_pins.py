@@ -21,6 +21,12 @@ violation.  What pins what:
               (1 - eps^k)^m <= 1 - p, evaluated with Python's float power,
               holds where the count stopped and at no earlier block end;
               all-inlier clusters stop after one block
+  paper_line  Alg. 1 as printed (line fits in the normalised plane, MAD
+              threshold): exhaustive all-pairs counts against numpy (min/max
+              normalisation, np.median, the distance from the cross product
+              of the seed difference, an independent formula); the refine
+              is numpy.linalg.lstsq of the inliers; 2^m Doppler scaling is
+              exact; affine (azimuth, Doppler) data is all inliers
   local_opt   the re-threshold + re-fit rounds: one round's inlier set is
               numpy's re-threshold of the refined velocity, every result is
               numpy.linalg.lstsq of its own inlier set, a converged result is
@@ -406,5 +412,72 @@ def check_adaptive(L):
     assert o["trials_used"][0] == 32 and o["inlier_count"][0] == 50
 
 
+def _line_brute(th, dop):
+    """Alg. 1 by exhaustion with numpy: counts of every seed pair (lexicographic),
+    the MAD threshold, and the smallest decision margin."""
+    x = (th - th.min()) * (1.0 / (th.max() - th.min())) if th.max() > th.min() else np.zeros_like(th)
+    y = (dop - dop.min()) * (1.0 / (dop.max() - dop.min())) if dop.max() > dop.min() else np.zeros_like(dop)
+    T = np.median(np.abs(y - np.median(y)))
+    counts, margin = [], np.inf
+    for a, b in itertools.combinations(range(th.shape[0]), 2):
+        dx, dy = x[b] - x[a], y[b] - y[a]
+        if dx == 0.0:
+            counts.append(-1)
+            continue
+        d = np.abs(dx * (y[a] - y) - (x[a] - x) * dy) / math.hypot(dx, dy)
+        margin = min(margin, np.min(np.abs(d - T)))
+        counts.append(int((d <= T).sum()))
+    return np.array(counts), T, margin
+
+
+def check_paper_line(L):
+    rng = np.random.default_rng(31)
+    done = 0
+    while done < 20:
+        n = int(rng.integers(4, 12))
+        v = rng.uniform(-20, 20, 3)
+        th, _, dop = _noise_free(rng, n, 2, v)
+        dop = dop + rng.normal(0, 0.3, n)
+        bad = rng.random(n) < 0.3
+        dop[bad] = rng.uniform(-40, 40, int(bad.sum()))
+        th = th.astype(np.float32).astype(np.float64)
+        dop = dop.astype(np.float32).astype(np.float64)
+        counts, T, margin = _line_brute(th, dop)
+        if margin < 1e-9 or T == 0.0:
+            continue
+        o = _est(L, th, dop, [0, n], num_hypotheses=counts.shape[0], tau=0.1, seed=1, enumerate_subsets=True,
+                 want_counts=True, line_model=True)
+        assert np.array_equal(o["hyp_counts"][0], counts), (o["hyp_counts"][0], counts)
+        assert o["best_hypothesis"][0] == int(np.argmax(counts))
+        done += 1
+    # frames: refine = lstsq of the inliers; Doppler x 2^m exact; shapes of the outputs
+    w, f = _frame("stress2d", 64)
+    kw = dict(num_hypotheses=256, tau=w.tau, seed=5, line_model=True)
+    o = _est(L, f.azimuth, f.doppler, f.offsets, want_counts=True, **kw)
+    A = _rows(f)
+    dop = f.doppler.astype(np.float64)
+    checked = 0
+    for c in range(64):
+        s_, e_ = f.offsets[c], f.offsets[c + 1]
+        m = o["inlier_mask"][s_:e_].astype(bool)
+        assert m.sum() == o["inlier_count"][c] == o["hyp_counts"][c].max()
+        if o["status"][c] == 0:
+            ref = np.linalg.lstsq(A[s_:e_][m], dop[s_:e_][m], rcond=None)[0]
+            assert np.allclose([o["vx"][c], o["vy"][c]], ref, rtol=1e-9, atol=1e-9), c
+            checked += 1
+    assert checked >= 60
+    sc = _est(L, f.azimuth, dop * 4.0, f.offsets, want_counts=True, **kw)
+    assert np.array_equal(o["hyp_counts"], sc["hyp_counts"]) and np.array_equal(o["inlier_mask"], sc["inlier_mask"])
+    assert np.array_equal(o["vx"] * 4.0, sc["vx"]) and np.array_equal(o["vy"] * 4.0, sc["vy"])
+    # affine (azimuth, Doppler): every point lies on the seeds' line
+    th = np.linspace(-0.9, 0.8, 33)
+    lin = _est(L, th, 3.0 * th + 1.0, [0, 33], num_hypotheses=16, tau=0.1, seed=2, want_counts=True, line_model=True)
+    assert (lin["hyp_counts"][0] == 33).all() and lin["inlier_count"][0] == 33
+    # one azimuth for every point: every seed pair shares x
+    deg = _est(L, np.full(6, 0.3), np.arange(6.0), [0, 6], num_hypotheses=8, tau=0.1, seed=1, line_model=True)
+    assert deg["status"][0] == oracle.ALL_DEGENERATE
+
+
 ALL_CHECKS = [check_philox, check_draws, check_recovery, check_brute, check_symmetry,
-              check_rotation, check_lstsq, check_status, check_planted, check_local_opt, check_adaptive]
+              check_rotation, check_lstsq, check_status, check_planted, check_local_opt, check_adaptive,
+              check_paper_line]

@@ -30,7 +30,12 @@ MUTANTS = {
     "draw_skip_off_by_one": ("if (q1 >= q0) q1 += 1u;", "if (q1 > q0) q1 += 1u;"),
     "draw3_skip_order": ("if (q2 >= lo) q2 += 1u;\n    if (q2 >= hi) q2 += 1u;",
                          "if (q2 >= hi) q2 += 1u;\n    if (q2 >= lo) q2 += 1u;"),
-    "tiebreak_last": ("if (count > best_count) {", "if (count >= best_count) {"),
+    "tiebreak_last": ("        if (count > best_count) {\n          best_count = count;\n          best = h;\n        }\n"
+                      "      } while (0);",
+                      "        if (count >= best_count) {\n          best_count = count;\n          best = h;\n        }\n"
+                      "      } while (0);"),
+    "line_tiebreak_last": ("          if (count > best_count) {\n            best_count = count;",
+                           "          if (count >= best_count) {\n            best_count = count;"),
     "refine_wrong_product": ("G[r][c] = fma(aq[r], aq[c], G[r][c]);",
                              "G[r][c] = fma(aq[r], aq[r], G[r][c]);"),
     "refine_dropped_rhs": ("g[r] = fma(aq[r], w[q], g[r]);", "g[r] = aq[r] * w[q];"),
@@ -49,6 +54,13 @@ MUTANTS = {
                                     "adaptive_stop(best_count, n, k, trials - p->trial_block + 1, p->confidence))"),
     "adaptive_every_trial": ("trials % p->trial_block == 0 && trials < H", "trials < H"),
     "adaptive_pow_skips_bit": ("if (n & 1) r = r * b;", "if (n & 2) r = r * b;"),
+    "line_intercept_sign": ("double distn = (-m) * x + 1.0 * y + (-c);", "double distn = (-m) * x + 1.0 * y + c;"),
+    "line_distd_no_one": ("double distd = sqrt(m * m + 1.0);", "double distd = sqrt(m * m + 1e-300);"),
+    "line_mad_not_abs": ("for (int32_t q = 0; q < n; ++q) tmp[q] = fabs(yn[q] - med);",
+                         "for (int32_t q = 0; q < n; ++q) tmp[q] = yn[q] - med;"),
+    "line_norm_swapped_range": ("double rv = vmax > vmin ? 1.0 / (vmax - vmin) : 0.0;",
+                                "double rv = tmax > tmin ? 1.0 / (tmax - tmin) : 0.0;"),
+    "line_slope_inverted": ("double m = (yn[qs[1]] - yn[qs[0]]) / dx;", "double m = dx / (yn[qs[1]] - yn[qs[0]]);"),
 }
 
 
