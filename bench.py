@@ -258,7 +258,7 @@ def main():
     # the scoring schedule is picked by the library's autotuner on this workload (untimed)
     tuned = rvh.rvh_schedule()
     if not args.schedule:
-        ctx.check(rvh.rvh_autotune(ctx.handle, frame, params, res, 2, tuned), "rvh_autotune")
+        ctx.check(rvh.rvh_autotune(ctx.handle, frame, params, res, 7, tuned), "rvh_autotune")
 
     for _ in range(max(args.warmup, 3)):
         flush.fill_(1)

@@ -102,7 +102,29 @@ typedef struct {
                                 in (0, 1): adaptive trial count, see below */
   int32_t trial_block;       /* adaptive: trials between stopping checks, a multiple of 32
                                 in [32, 1024]; 0 selects 128.  Ignored when confidence is 0 */
+  int32_t hypothesis_model;  /* RVH_MODEL_VELOCITY_PROFILE (0) or RVH_MODEL_PAPER_LINE (1) */
 } rvh_params;
+
+/* Hypothesis models.
+ * RVH_MODEL_VELOCITY_PROFILE: trials are exact solves of Eq. LSQ_eq on
+ *   k = 2 (3) points, inliers |v_d - a.v| <= inlier_threshold (above).
+ * RVH_MODEL_PAPER_LINE: Alg. 1 as printed, 2D only.  Each cluster's
+ *   (azimuth, Doppler) points are normalised (the paper does not define
+ *   normalize(); here min-max scaling to [0, 1], x = (t - t_min) *
+ *   (1 / (t_max - t_min)), 0 for an empty range); a trial fits the line
+ *   y = m x + c through its two seed points (rejected when they share x);
+ *   a point is an inlier when its perpendicular distance |aa x + bb y + cc| /
+ *   sqrt(aa^2 + bb^2), aa = -m, bb = 1, cc = -c, evaluated in FP64 left to
+ *   right as printed, is at most the cluster's threshold: the median
+ *   absolute deviation of the normalised Doppler (Eq. eq:MAD prints the mean
+ *   of signed deviations from the median; read as med |y - med y|, the mean
+ *   of the two middle values for even counts).  inlier_threshold is unused.
+ *   The velocity is the least-squares refine of Eq. eq:LSQPerCluster on the
+ *   winner's inliers; when it is singular the velocity and heading are NaN
+ *   (RVH_STATUS_LSQ_FALLBACK).  Combines with the adaptive trial count, not
+ *   with refine_iterations (RVH_EINVAL). */
+#define RVH_MODEL_VELOCITY_PROFILE 0
+#define RVH_MODEL_PAPER_LINE 1
 
 /* Adaptive trial count (confidence p > 0).  Sec. III-A tunes max_trials to
  * the hardware and cites work on optimal RANSAC; here each cluster runs its
@@ -225,8 +247,10 @@ const char* rvh_last_error(rvh_ctx* ctx);
 
 /* ---- measurement and tuning ------------------------------------------------------ */
 typedef struct {
-  int64_t hypotheses;          /* trials run (sum over clusters with N >= k of the trials drawn) */
-  int64_t pair_evals;          /* trial x point evaluations in the scoring pass (sum of trials x N) */
+  int64_t hypotheses;          /* trials run: n_clusters x H for the plain method; with an extension
+                                  (adaptive count, local optimisation, line model) the kernel's count,
+                                  over clusters with N >= k, of the trials actually run */
+  int64_t pair_evals;          /* trial x point evaluations (n_points x H, or the kernel's sum of trials x N) */
   int64_t candidates;          /* trials re-scored exactly (upper bound reached the lead) */
   int64_t band_points;         /* point decisions taken in FP64 (inside the error band) */
   int64_t fp64_hypotheses;     /* trials whose conditioning or bound needed FP64 */
@@ -259,10 +283,12 @@ typedef struct {
 } rvh_schedule;
 
 /* Autotuner: runs the fused kernel on this frame with every scoring schedule
- * (points_per_warp in {1, 8, 32} x hyps_per_lane in {4, 8}), `reps` timed
- * runs each after one warm-up (CUDA events on the context's stream), and
- * keeps the fastest for frames of this model dimension and trial-count
- * bucket (floor(log2 H)); later calls pick it automatically unless
+ * (points_per_warp in {1, 8, 32} x hyps_per_lane in {4, 8}), the schedules
+ * taking turns for one untimed and then `reps` timed rounds (CUDA events on
+ * the context's stream), and keeps the one with the lowest median time for
+ * frames of this model dimension and trial-count bucket (floor(log2) of the
+ * trials scored together: H, or the adaptive trial_block); later calls pick
+ * it automatically unless
  * rvh_set_schedule fixed one.  `result` receives the frame's outputs.  When
  * the environment variable RVH_TUNE_CACHE names a file, choices are loaded
  * from it by rvh_create (entries keyed by GPU name, SM count, model and

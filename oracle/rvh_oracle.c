@@ -167,8 +167,10 @@ static int adaptive_stop(int32_t best, int32_t n, int k, int32_t m, double p) {
   return pow_uint(1.0 - ek, m) <= 1.0 - p;
 }
 
+/* Ascending order with NaN after every number. */
 static int cmp_double(const void* a, const void* b) {
   double x = *(const double*)a, y = *(const double*)b;
+  if (isnan(x) || isnan(y)) return isnan(x) - isnan(y);
   return (x > y) - (x < y);
 }
 
@@ -266,13 +268,13 @@ int oracle_estimate(const double* azimuth, const double* elevation, const double
     if (p->line_model) {
       xn = (double*)malloc(sizeof(double) * (size_t)n);
       yn = (double*)malloc(sizeof(double) * (size_t)n);
-      double tmin = azimuth[o], tmax = azimuth[o], vmin = w[0], vmax = w[0];
-      for (int32_t q = 1; q < n; ++q) {
-        double t = azimuth[o + q];
-        if (t < tmin) tmin = t;
-        if (t > tmax) tmax = t;
-        if (w[q] < vmin) vmin = w[q];
-        if (w[q] > vmax) vmax = w[q];
+      /* extremes over the numbers (NaN ignored) */
+      double tmin = INFINITY, tmax = -INFINITY, vmin = INFINITY, vmax = -INFINITY;
+      for (int32_t q = 0; q < n; ++q) {
+        tmin = fmin(tmin, azimuth[o + q]);
+        tmax = fmax(tmax, azimuth[o + q]);
+        vmin = fmin(vmin, w[q]);
+        vmax = fmax(vmax, w[q]);
       }
       double rt = tmax > tmin ? 1.0 / (tmax - tmin) : 0.0;
       double rv = vmax > vmin ? 1.0 / (vmax - vmin) : 0.0;
@@ -281,7 +283,7 @@ int oracle_estimate(const double* azimuth, const double* elevation, const double
         yn[q] = (w[q] - vmin) * rv;
       }
       double* tmp = (double*)malloc(sizeof(double) * (size_t)n);
-      for (int32_t q = 0; q < n; ++q) tmp[q] = yn[q];
+      for (int32_t q = 0; q < n; ++q) tmp[q] = fabs(yn[q]);  /* y >= 0; fabs makes NaN positive */
       double med = median(tmp, n);
       for (int32_t q = 0; q < n; ++q) tmp[q] = fabs(yn[q] - med);
       thresh = median(tmp, n);

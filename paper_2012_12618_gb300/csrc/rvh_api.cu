@@ -69,6 +69,10 @@ int check_args(const rvh_frame* f, const rvh_params* p, const rvh_result* r) {
   if (p->confidence > 0.0 && p->trial_block != 0 &&
       (p->trial_block < 32 || p->trial_block > 1024 || p->trial_block % 32 != 0))
     return fail(RVH_EINVAL, "trial_block must be 0 or a multiple of 32 in [32, 1024]");
+  if (p->hypothesis_model != RVH_MODEL_VELOCITY_PROFILE && p->hypothesis_model != RVH_MODEL_PAPER_LINE)
+    return fail(RVH_EINVAL, "hypothesis_model must be RVH_MODEL_VELOCITY_PROFILE or RVH_MODEL_PAPER_LINE");
+  if (p->hypothesis_model == RVH_MODEL_PAPER_LINE && (p->model_dim != 2 || p->refine_iterations != 0))
+    return fail(RVH_EINVAL, "hypothesis_model RVH_MODEL_PAPER_LINE needs model_dim 2 and refine_iterations 0");
   if (f->n_points > 0 && (!f->azimuth || !f->doppler)) return fail(RVH_EINVAL, "azimuth/doppler NULL");
   if (f->n_clusters > 0 && !f->cluster_offsets) return fail(RVH_EINVAL, "cluster_offsets NULL");
   if (f->n_clusters > 0 && (!r->vx || !r->vy || !r->heading || !r->inlier_count || !r->best_hypothesis || !r->status))
@@ -146,6 +150,7 @@ struct rvh_ctx {
   std::vector<char> gkey;
   int64_t graph_replays = 0;
   std::string tune_prefix;                    // "<gpu name>|<sms>|"
+  bool last_counts_trials = false;  // the last launch counted its trials on the device (extensions)
 };
 
 namespace rvh {
@@ -226,6 +231,7 @@ void fill_desc(rvh_ctx* ctx, FrameDesc& d, const rvh_frame& f, const rvh_params&
   d.lo_iters = p.refine_iterations;
   d.confidence = p.confidence;
   d.trial_block = p.confidence > 0.0 ? (p.trial_block ? p.trial_block : RVH_DEFAULT_TRIAL_BLOCK) : 0;
+  d.line_model = p.hypothesis_model == RVH_MODEL_PAPER_LINE ? 1 : 0;
   d.vx = out.vx;
   d.vy = out.vy;
   d.vz = out.vz;
@@ -454,8 +460,10 @@ int rvh_get_stats(rvh_ctx* ctx, rvh_stats* out) {
     RVH_CUDA(cudaEventSynchronize(ctx->last_done));
     unsigned long long h[12] = {0, 0, 0, 0, 0, 0, 0, 0, 0, 0, 0, 0};
     RVH_CUDA(cudaMemcpy(h, ctx->stats_d, sizeof(h), cudaMemcpyDeviceToHost));
-    ctx->last.hypotheses = (int64_t)h[10];
-    ctx->last.pair_evals = (int64_t)h[11];
+    if (ctx->last_counts_trials) {  // the kernel counted the trials it ran
+      ctx->last.hypotheses = (int64_t)h[10];
+      ctx->last.pair_evals = (int64_t)h[11];
+    }
     for (int k = 0; k < 6; ++k) ctx->last.phase_cycles[k] = (int64_t)h[4 + k];
     ctx->last.refined_hypotheses = (int64_t)h[3];
     ctx->last.graph_replays = ctx->graph_replays;
@@ -614,6 +622,11 @@ int rvh_estimate(rvh_ctx* ctx, const rvh_frame* frame, const rvh_params* params,
     rc = launch_batch(ctx, a, params->model_dim, s, ctx->ev0, ctx->ev1);
   }
   if (rc) return rc;
+  // plain launches run every trial of every cluster; launches with an
+  // extension (adaptive count, local optimisation, line model) count on the device
+  ctx->last.hypotheses = (int64_t)frame->n_clusters * params->num_hypotheses;
+  ctx->last.pair_evals = frame->n_points * (int64_t)params->num_hypotheses;
+  ctx->last_counts_trials = params->confidence > 0.0 || params->refine_iterations > 0 || params->hypothesis_model != 0;
   ctx->last.points_per_warp = a.pw;
   ctx->last.hyps_per_lane = a.hpl;
   ctx->have_launch = true;
@@ -627,8 +640,9 @@ int rvh_estimate_baseline(rvh_ctx* ctx, const rvh_frame* frame, const rvh_params
   if (!ctx) return fail(RVH_EINVAL, "ctx is NULL");
   int rc = check_args(frame, params, result);
   if (rc) return rc;
-  if (params->refine_iterations != 0 || params->confidence != 0.0)
-    return fail(RVH_EINVAL, "rvh_estimate_baseline runs the plain method (refine_iterations 0, confidence 0)");
+  if (params->refine_iterations != 0 || params->confidence != 0.0 || params->hypothesis_model != 0)
+    return fail(RVH_EINVAL,
+                "rvh_estimate_baseline runs the plain method (refine_iterations 0, confidence 0, hypothesis_model 0)");
   if (frame->n_clusters == 0) return RVH_OK;
   std::lock_guard<std::mutex> lk(ctx->mu);
   RVH_CUDA(cudaSetDevice(ctx->device));
@@ -686,23 +700,29 @@ int rvh_autotune(rvh_ctx* ctx, const rvh_frame* frame, const rvh_params* params,
   const int save_pw = ctx->pw_fixed, save_hpl = ctx->hpl_fixed;
   int bpw = 1, bhpl = 4;
   float bms = 1e30f;
-  for (auto& c : kCand) {
-    ctx->pw_fixed = c[0];
-    ctx->hpl_fixed = c[1];
-    float tot = 0.f;
-    for (int r = 0; r <= reps && rc == RVH_OK; ++r) {
+  // candidates take turns (round-robin over the repetitions, the first
+  // round untimed) so that drifting clocks or caches favour none of them;
+  // each is ranked by its median time
+  std::vector<std::vector<float>> times(6);
+  for (int r = 0; r <= reps && rc == RVH_OK; ++r) {
+    for (int ic = 0; ic < 6 && rc == RVH_OK; ++ic) {
+      ctx->pw_fixed = kCand[ic][0];
+      ctx->hpl_fixed = kCand[ic][1];
       rc = rvh_estimate(ctx, frame, params, result, nullptr);
       if (rc) break;
       rvh_stats st;
       rc = rvh_get_stats(ctx, &st);
-      if (r > 0) tot += st.kernel_ms;
+      if (r > 0) times[ic].push_back(st.kernel_ms);
     }
-    if (rc) break;
-    const float ms = tot / reps;
+  }
+  for (int ic = 0; ic < 6 && rc == RVH_OK; ++ic) {
+    std::vector<float>& t = times[ic];
+    std::sort(t.begin(), t.end());
+    const float ms = t.size() % 2 ? t[t.size() / 2] : 0.5f * (t[t.size() / 2 - 1] + t[t.size() / 2]);
     if (ms < bms) {
       bms = ms;
-      bpw = c[0];
-      bhpl = c[1];
+      bpw = kCand[ic][0];
+      bhpl = kCand[ic][1];
     }
   }
   ctx->pw_fixed = save_pw;

@@ -194,7 +194,7 @@ struct ClusterShared {
   int red_i[kWarps];
   float red_f[kWarps];
   double red_t[9];            // the normal-equation sums of the winner's inliers
-  unsigned long long ctr[6];  // exact counts, band points, fp64 trials, refined trials, trials run, pairs scored
+  unsigned long long ctr[4];  // exact counts, band points, fp64 trials, refined trials
   unsigned long long clk[6];  // cycles per stage (thread 0's view of the CTA)
   unsigned long long red_u[kWarps];
   double cv64[3];             // FP64 velocity of the trial being counted (when it has band points)
@@ -206,6 +206,10 @@ struct ClusterShared {
   float lo_tlo;
   int lo_ok;
   int stop;                   // adaptive trial count: enough trials have run
+  double ln_T;                // line model (Alg. 1): the cluster's MAD threshold
+  int sel_digit, sel_k;       // radix select: digit and rank inside it
+  float red4[4][kWarps];      // line model: min / max of azimuth and Doppler
+  unsigned long long runs[2];  // trials run, pairs scored
 };
 
 // Adaptive trial count: with `best` the best (count + 1, -index) key so far,
@@ -249,10 +253,176 @@ __device__ __forceinline__ void velocity_record(const double v[3], float wmax, T
   *tlo = __fsub_rd(tau.lo, b);
 }
 
+// ---- Alg. 1 as printed (line model, 2D): normalised (azimuth, Doppler) points,
+// line fits through two seed points, perpendicular-distance test against the
+// cluster's median absolute deviation.  The FP64 values of each point are
+// kept in its FP64 row slot (x, y, |y - med y|, -), which the 2D cosine
+// model does not use.
+
+// Alg. 1 point-to-line test in FP64, evaluated as printed: aa = -m, bb = 1,
+// cc = -c, distn = aa x + bb y + cc, distd = sqrt(aa^2 + bb^2) (passed in),
+// dist = |distn / distd| <= thresh.
+__device__ __forceinline__ bool line_in64(double m, double c, double distd, double x, double y, double thresh) {
+  const double distn = (-m) * x + y + (-c);
+  return fabs(distn / distd) <= thresh;
+}
+
+// FP64 line (m, c, distd) of trial h through its two normalised seed points;
+// false when they share x (no slope).
+__device__ __forceinline__ bool line_hyp64(const FrameDesc& a, const double4_32a* pre, int ci, int h, int N, double v[3]) {
+  int q[3];
+  draw_minimal_set<2>(a.key, a.cluster_base + ci, h, N, q);
+  const double4_32a p0 = pre[q[0]], p1 = pre[q[1]];
+  const double dx = p1.x - p0.x;
+  if (dx == 0.0) return false;
+  const double m = (p1.y - p0.y) / dx;
+  v[0] = m;
+  v[1] = p0.y - m * p0.x;
+  v[2] = sqrt(m * m + 1.0);
+  return true;
+}
+
+// FP32 scoring record of an FP64 line: (-m32, -c32, 0, thi) and tlo, such
+// that with rows (x32, 1, y32) the FP32 residual r32 = fmaf(-m32, x32,
+// fmaf(-c32, 1, y32)) satisfies |r32| <= tlo => inlier and |r32| > thi =>
+// outlier under line_in64.  With |x|, |y| <= 1 (normalised), rounding the
+// inputs and the arithmetic to FP32 moves the residual by at most
+// u (2.01 (1 + |c| + |m|) + 1.0001 |r|), the FP64 residual carries
+// 3 * 2^-53 (1 + |c| + |m|), and the FP64 quotient test is certain outside
+// T distd (1 -+ 2^-50); b below covers both sides with margin.
+__device__ __forceinline__ Hyp32 line_record(const double v[3], double T) {
+  Hyp32 h;
+  h.refined = 0;
+  h.nx = -__double2float_rn(v[0]);
+  h.ny = -__double2float_rn(v[1]);
+  h.nz = 0.0f;
+  const double td = T * v[2];
+  const double am = fabs(v[0]), ac = fabs(v[1]);
+  const double b = (0x1p-22 * (1.0 + ac + am + td) + 0x1p-50 * (1.0 + ac + am)) * (1.0 + 0x1p-20);
+  const double hi = td * (1.0 + 0x1p-50) + b, lo = td * (1.0 - 0x1p-50) - b;
+  if (!(hi < 1e30) || !(am < 1e30) || !(ac < 1e30)) {
+    h.kind = kHypExactOnly;
+    h.thi = __int_as_float(0x7f800000);
+    h.tlo = -1.0f;
+    return h;
+  }
+  h.thi = __double2float_ru(hi);
+  h.tlo = lo >= 0.0 ? __double2float_rd(lo) : -1.0f;
+  h.kind = kHypNormal;
+  return h;
+}
+
+// k-th smallest (0-based, k < N) of the keys |field| of the FP64 point slots
+// (field 1: y, field 2: |y - med y|) as 64-bit patterns of non-negative
+// doubles (monotone as integers; NaN sorts last), by radix digits of 8 bits
+// from the top.  hist: 256 ints of shared memory.  Exact: returns the key.
+template <int FIELD>
+__device__ unsigned long long block_select(const double4_32a* pre, int N, int k, int* hist, ClusterShared& cs) {
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+  unsigned long long prefix = 0ull, hmask = 0ull;
+  for (int shift = 56; shift >= 0; shift -= 8) {
+    hist[tid] = 0;  // kThreads == 256 bins
+    __syncthreads();
+    for (int j = tid; j < N; j += kThreads) {
+      const double4_32a p = pre[j];
+      const unsigned long long kb = (unsigned long long)__double_as_longlong(fabs(FIELD == 1 ? p.y : p.z));
+      if ((kb & hmask) == prefix) atomicAdd(&hist[(int)((kb >> shift) & 255ull)], 1);
+    }
+    __syncthreads();
+    if (warp == 0) {
+      int c[8], tot = 0;
+#pragma unroll
+      for (int i = 0; i < 8; ++i) {
+        c[i] = hist[8 * lane + i];
+        tot += c[i];
+      }
+      int incl = tot;
+#pragma unroll
+      for (int d = 1; d < 32; d <<= 1) {
+        const int t = __shfl_up_sync(0xffffffffu, incl, d);
+        if (lane >= d) incl += t;
+      }
+      const int excl = incl - tot;
+      if (excl <= k && k < incl) {
+        int kk = k - excl, d = 0;
+        while (d < 7 && kk >= c[d]) kk -= c[d++];
+        cs.sel_digit = 8 * lane + d;
+        cs.sel_k = kk;
+      }
+    }
+    __syncthreads();
+    prefix |= (unsigned long long)cs.sel_digit << shift;
+    hmask |= 0xFFull << shift;
+    k = cs.sel_k;
+  }
+  return prefix;
+}
+
+// Median of the keys (even N: 0.5 * (lower + upper middle)).
+template <int FIELD>
+__device__ double block_median(const double4_32a* pre, int N, int* hist, ClusterShared& cs) {
+  const double hi = __longlong_as_double((long long)block_select<FIELD>(pre, N, N / 2, hist, cs));
+  if (N & 1) return hi;
+  const double lo = __longlong_as_double((long long)block_select<FIELD>(pre, N, N / 2 - 1, hist, cs));
+  return 0.5 * (lo + hi);
+}
+
+// The line model's rows stage: min / max of azimuth and Doppler, normalised
+// FP64 points into the FP64 slots and FP32 rows (x, 1, y) into the scoring
+// rows, then the MAD threshold into cs.ln_T.  Normalisation (the paper's
+// normalize(), undefined there): min-max scaling, x = (t - t_min) *
+// (1 / (t_max - t_min)), 0 when the range is empty.  Out of line: runs once
+// per cluster.
+template <typename RV>
+__device__ __noinline__ void line_rows_and_threshold(const FrameDesc& a, const RV rows, double4_32a* pre, int64_t o,
+                                                     int N, int* hist, ClusterShared& cs) {
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+  const float inf = __int_as_float(0x7f800000);
+  float m4[4] = {inf, inf, inf, inf};  // min t, -max t, min v, -max v
+  for (int j = tid; j < N; j += kThreads) {
+    const float t = a.az[o + j], v = a.dop[o + j];
+    m4[0] = fminf(m4[0], t);
+    m4[1] = fminf(m4[1], -t);
+    m4[2] = fminf(m4[2], v);
+    m4[3] = fminf(m4[3], -v);
+  }
+#pragma unroll
+  for (int i = 0; i < 4; ++i) {
+#pragma unroll
+    for (int d = 16; d > 0; d >>= 1) m4[i] = fminf(m4[i], __shfl_xor_sync(0xffffffffu, m4[i], d));
+    if (lane == 0) cs.red4[i][warp] = m4[i];
+  }
+  __syncthreads();
+#pragma unroll
+  for (int i = 0; i < 4; ++i) {
+    float r = cs.red4[i][0];
+#pragma unroll
+    for (int w = 1; w < kWarps; ++w) r = fminf(r, cs.red4[i][w]);
+    m4[i] = r;
+  }
+  const double tmin = (double)m4[0], tmax = -(double)m4[1], vmin = (double)m4[2], vmax = -(double)m4[3];
+  const double rt = tmax > tmin ? 1.0 / (tmax - tmin) : 0.0;
+  const double rv = vmax > vmin ? 1.0 / (vmax - vmin) : 0.0;
+  for (int j = tid; j < N; j += kThreads) {
+    const double x = ((double)a.az[o + j] - tmin) * rt;
+    const double y = ((double)a.dop[o + j] - vmin) * rv;
+    pre[j] = make_double4_32a(x, y, 0.0, 0.0);
+    rows.put(j, make_float4(__double2float_rn(x), 1.0f, __double2float_rn(y), 0.0f));
+  }
+  __syncthreads();
+  // Eq. eq:MAD read as the median absolute deviation of the normalised Doppler
+  const double med = block_median<1>(pre, N, hist, cs);
+  for (int j = tid; j < N; j += kThreads) pre[j].z = fabs(pre[j].y - med);
+  __syncthreads();
+  const double T = block_median<2>(pre, N, hist, cs);
+  if (tid == 0) cs.ln_T = T;
+  __syncthreads();
+}
+
 // Exact count of one trial by the whole CTA: FP32 certainties, then an FP64
 // re-decision of the points inside the trial's error band.  When there are
 // band points the trial's FP64 velocity is left in cs.cv64 and *band > 0.
-template <int DIM, typename RV>
+template <int DIM, typename RV, bool EXT>
 __device__ int exact_count_block(const FrameDesc& a, const RV rows, const Rows64<DIM>& R,
                                  int ci, int h, int N, float4 hy, float tlo, ClusterShared& cs, int* band) {
   const int tid = threadIdx.x;
@@ -269,7 +439,12 @@ __device__ int exact_count_block(const FrameDesc& a, const RV rows, const Rows64
   __syncthreads();
   if (tid == 0) {
     double v[3] = {0.0, 0.0, 0.0};
-    hyp_f64<DIM>(a, R, ci, h, N, v);
+    if constexpr (EXT && DIM == 2) {
+      if (a.line_model) line_hyp64(a, R.pre, ci, h, N, v);
+      else hyp_f64<DIM>(a, R, ci, h, N, v);
+    } else {
+      hyp_f64<DIM>(a, R, ci, h, N, v);
+    }
     cs.cv64[0] = v[0];
     cs.cv64[1] = v[1];
     cs.cv64[2] = v[2];
@@ -278,13 +453,30 @@ __device__ int exact_count_block(const FrameDesc& a, const RV rows, const Rows64
   __syncthreads();
   const double v[3] = {cs.cv64[0], cs.cv64[1], cs.cv64[2]};
   unsigned long long lbin = 0;
-  for (int j = tid; j < N; j += kThreads) {
-    const float r = fabsf(resid_f32<DIM>(rows.at(j), hy.x, hy.y, hy.z));
-    if (!(r <= tlo) && !(r > hy.w)) {
-      const double4_32a s = R.at(j);
-      const double a64[3] = {s.x, s.y, s.z};
-      if (fabs(residual_f64<DIM>(a64, s.w, v)) <= a.tau) ++lbin;
+  auto cosine_band = [&]() {
+    for (int j = tid; j < N; j += kThreads) {
+      const float r = fabsf(resid_f32<DIM>(rows.at(j), hy.x, hy.y, hy.z));
+      if (!(r <= tlo) && !(r > hy.w)) {
+        const double4_32a s = R.at(j);
+        const double a64[3] = {s.x, s.y, s.z};
+        if (fabs(residual_f64<DIM>(a64, s.w, v)) <= a.tau) ++lbin;
+      }
     }
+  };
+  if constexpr (EXT && DIM == 2) {
+    if (a.line_model) {
+      for (int j = tid; j < N; j += kThreads) {
+        const float r = fabsf(resid_f32<DIM>(rows.at(j), hy.x, hy.y, hy.z));
+        if (!(r <= tlo) && !(r > hy.w)) {
+          const double4_32a p = R.pre[j];
+          if (line_in64(v[0], v[1], v[2], p.x, p.y, cs.ln_T)) ++lbin;
+        }
+      }
+    } else {
+      cosine_band();
+    }
+  } else {
+    cosine_band();
   }
   lbin = block_sum_u64(lbin, cs.red_u);
   return L + (int)lbin;
@@ -339,7 +531,7 @@ __device__ __forceinline__ bool solve_normal(const double* t, int n_in, double v
 // Final solve and heading of a cluster: the normal equations, with a
 // fallback to the winning minimal-set velocity, heading atan2(vy, vx).
 // One thread.
-template <int DIM>
+template <int DIM, bool EXT>
 __device__ __noinline__ void finish_cluster(const FrameDesc& a, const Rows64<DIM>& R, int ci, int N, int hstar, int n_in,
                                const double* t, const double* v64, bool has_v64) {
   double vout[3] = {v64[0], v64[1], v64[2]};
@@ -347,7 +539,15 @@ __device__ __noinline__ void finish_cluster(const FrameDesc& a, const Rows64<DIM
   const bool ok = solve_normal<DIM>(t, n_in, vout);
   if (!ok) {
     st |= RVH_STATUS_LSQ_FALLBACK;
-    if (!has_v64) hyp_f64<DIM>(a, R, ci, hstar, N, vout);
+    if constexpr (EXT && DIM == 2) {
+      if (a.line_model) {  // a line has no velocity to fall back to
+        vout[0] = vout[1] = vout[2] = __longlong_as_double(0x7ff8000000000000LL);
+      } else if (!has_v64) {
+        hyp_f64<DIM>(a, R, ci, hstar, N, vout);
+      }
+    } else {
+      if (!has_v64) hyp_f64<DIM>(a, R, ci, hstar, N, vout);
+    }
   }
   a.vx[ci] = vout[0];
   a.vy[ci] = vout[1];
@@ -400,7 +600,7 @@ __device__ __forceinline__ void accumulate_row(double* sums, const double4_32a& 
 // *changed receives the number of mask entries that differ from what the
 // mask held before.  The trial area of shared memory is free at this point
 // and holds the reduction.
-template <int DIM, typename RV>
+template <int DIM, typename RV, bool EXT>
 __device__ __forceinline__ int mask_and_sums(const FrameDesc& a, const RV rows, const Rows64<DIM>& R, int64_t o, int N,
                                              float4 hy, float tlo, const double v64[3], const Smem& S,
                                              ClusterShared& cs, bool count_changes, int* changed) {
@@ -410,23 +610,48 @@ __device__ __forceinline__ int mask_and_sums(const FrameDesc& a, const RV rows, 
 #pragma unroll
   for (int i = 0; i < NS; ++i) sums[i] = 0.0;
   int nin = 0, nch = 0;
-  for (int j = tid; j < N; j += kThreads) {
-    const float r = fabsf(resid_f32<DIM>(rows.at(j), hy.x, hy.y, hy.z));
-    bool in = r <= tlo;
-    const bool band = !in && !(r > hy.w);
-    if (in || band) {
-      const double4_32a s = R.at(j);
-      if (band) {
-        const double a64[3] = {s.x, s.y, s.z};
-        in = fabs(residual_f64<DIM>(a64, s.w, v64)) <= a.tau;
+  auto cosine_pass = [&]() {
+    for (int j = tid; j < N; j += kThreads) {
+      const float r = fabsf(resid_f32<DIM>(rows.at(j), hy.x, hy.y, hy.z));
+      bool in = r <= tlo;
+      const bool band = !in && !(r > hy.w);
+      if (in || band) {
+        const double4_32a s = R.at(j);
+        if (band) {
+          const double a64[3] = {s.x, s.y, s.z};
+          in = fabs(residual_f64<DIM>(a64, s.w, v64)) <= a.tau;
+        }
+        if (in) {
+          ++nin;
+          accumulate_row<DIM>(sums, s);
+        }
       }
-      if (in) {
-        ++nin;
-        accumulate_row<DIM>(sums, s);
-      }
+      if (count_changes) nch += (a.mask[o + j] != (in ? 1 : 0));
+      a.mask[o + j] = in ? 1 : 0;
     }
-    if (count_changes) nch += (a.mask[o + j] != (in ? 1 : 0));
-    a.mask[o + j] = in ? 1 : 0;
+  };
+  if constexpr (EXT && DIM == 2) {
+    if (a.line_model) {
+      // the line model decides its band points by Alg. 1's distance test
+      for (int j = tid; j < N; j += kThreads) {
+        const float r = fabsf(resid_f32<DIM>(rows.at(j), hy.x, hy.y, hy.z));
+        bool in = r <= tlo;
+        if (!in && !(r > hy.w)) {
+          const double4_32a p = R.pre[j];
+          in = line_in64(v64[0], v64[1], v64[2], p.x, p.y, cs.ln_T);
+        }
+        if (in) {
+          ++nin;
+          accumulate_row<DIM>(sums, R.at(j));
+        }
+        if (count_changes) nch += (a.mask[o + j] != (in ? 1 : 0));
+        a.mask[o + j] = in ? 1 : 0;
+      }
+    } else {
+      cosine_pass();
+    }
+  } else {
+    cosine_pass();
   }
   // Reduce the per-thread sums through shared memory: warp i sums sum i,
   // each lane a strided share of the threads that held points, then a
@@ -493,7 +718,7 @@ __device__ __noinline__ int local_opt_rounds(const FrameDesc& a, const RV rows, 
     const float ntlo = cs.lo_tlo;
     const double nv[3] = {cs.lo_v[0], cs.lo_v[1], cs.lo_v[2]};
     int changed = 0;
-    const int n2 = mask_and_sums<DIM, RV>(a, rows, R, o, N, nhy, ntlo, nv, S, cs, true, &changed);
+    const int n2 = mask_and_sums<DIM, RV, true>(a, rows, R, o, N, nhy, ntlo, nv, S, cs, true, &changed);
     if (changed == 0) break;  // same set, same sums
     if (tid == 0) {
       double vt[3];
@@ -501,7 +726,7 @@ __device__ __noinline__ int local_opt_rounds(const FrameDesc& a, const RV rows, 
     }
     __syncthreads();
     if (!cs.lo_ok) {
-      n_in = mask_and_sums<DIM, RV>(a, rows, R, o, N, gen_hy, gen_tlo, gen_v, S, cs, false, nullptr);
+      n_in = mask_and_sums<DIM, RV, true>(a, rows, R, o, N, gen_hy, gen_tlo, gen_v, S, cs, false, nullptr);
       break;
     }
     gen_hy = nhy;
@@ -547,19 +772,29 @@ __device__ void process_cluster(const FrameDesc& a, const Smem& S, ClusterShared
     }
   };
 
-  // a1: FP32 rows in shared memory (sincosf), FP64 rows in global scratch
+  // a1: FP32 rows in shared memory (sincosf), FP64 rows in global scratch;
+  // the line model of Alg. 1 normalises its points and computes its MAD
+  // threshold instead
   float wm = 0.0f;
-  for (int j = tid; j < N; j += kThreads) {
-    const float w = a.dop[o + j];
-    const float az = a.az[o + j];
-    const float el = DIM == 3 ? a.el[o + j] : 0.0f;
-    rows.put(j, row_f32<DIM>(az, el, w));
-    if (DIM == 3) {
-      double a64[3];
-      row_f64<DIM>(a.trig, az, el, a64);
-      R.pre[j] = make_double4_32a(a64[0], a64[1], a64[2], (double)w);
+  auto cosine_rows = [&]() {
+    for (int j = tid; j < N; j += kThreads) {
+      const float w = a.dop[o + j];
+      const float az = a.az[o + j];
+      const float el = DIM == 3 ? a.el[o + j] : 0.0f;
+      rows.put(j, row_f32<DIM>(az, el, w));
+      if (DIM == 3) {
+        double a64[3];
+        row_f64<DIM>(a.trig, az, el, a64);
+        R.pre[j] = make_double4_32a(a64[0], a64[1], a64[2], (double)w);
+      }
+      wm = fmaxf(wm, fabsf(w));
     }
-    wm = fmaxf(wm, fabsf(w));
+  };
+  if constexpr (EXT && DIM == 2) {
+    if (a.line_model) line_rows_and_threshold<RV>(a, rows, R.pre, o, N, S.U, cs);
+    else cosine_rows();
+  } else {
+    cosine_rows();
   }
   if constexpr (SMEM_ROWS) {
     // pad the last quad of the scoring pass: NaN Dopplers never count
@@ -580,40 +815,68 @@ __device__ void process_cluster(const FrameDesc& a, const Smem& S, ClusterShared
 
   // trials run in chunks of hchunk, or in the adaptive blocks of trial_block
   const int chunk = (EXT && a.trial_block > 0) ? a.trial_block : hchunk;
-  int trials_run = 0;
+  [[maybe_unused]] int trials_run = a.H;  // all of them, unless the adaptive count stops early
   for (int hc0 = 0; hc0 < a.H; hc0 += chunk) {
     const int nh = min(chunk, a.H - hc0);
     // a2 + a3: draw, FP32 solve (refined when ill-conditioned), bound
-    for (int hl = tid; hl < nh; hl += kThreads) {
-      int q[3];
-      draw_minimal_set<DIM>(a.key, a.cluster_base + ci, hc0 + hl, N, q);
-      const int q2 = DIM == 3 ? q[2] : q[0];
-      const float4 p0 = rows.at(q[0]), p1 = rows.at(q[1]), p2 = rows.at(q2);
-      const int qs[3] = {q[0], q[1], q2};
-      auto seed64 = [&](int i) { return R.at(qs[i]); };
-      // 2D minimal sets are mildly conditioned (|det| = |sin(t1 - t0)|): their
-      // wide bands are rare and cheaper than refining; 3D trials refine
-      Hyp32 hy = hyp_f32<DIM>(p0, p1, p2, seed64, DIM == 3, wmax, a.acc, a.rej, a.tau32);
-      if (hy.kind == kHypUndecided) {
-        ++n_fp64;
-        double v[3];
-        if (hyp_f64<DIM>(a, R, ci, hc0 + hl, N, v)) {
-          hy = hyp_f32<DIM>(p0, p1, p2, seed64, DIM == 3, wmax, 0.0f, 0.0f, a.tau32);
-          if (hy.kind != kHypNormal) {
-            hy.kind = kHypExactOnly;
-            hy.thi = __int_as_float(0x7f800000);
-            hy.tlo = -1.0f;
+    auto cosine_trials = [&]() {
+      for (int hl = tid; hl < nh; hl += kThreads) {
+        int q[3];
+        draw_minimal_set<DIM>(a.key, a.cluster_base + ci, hc0 + hl, N, q);
+        const int q2 = DIM == 3 ? q[2] : q[0];
+        const float4 p0 = rows.at(q[0]), p1 = rows.at(q[1]), p2 = rows.at(q2);
+        const int qs[3] = {q[0], q[1], q2};
+        auto seed64 = [&](int i) { return R.at(qs[i]); };
+        // 2D minimal sets are mildly conditioned (|det| = |sin(t1 - t0)|): their
+        // wide bands are rare and cheaper than refining; 3D trials refine
+        Hyp32 hy = hyp_f32<DIM>(p0, p1, p2, seed64, DIM == 3, wmax, a.acc, a.rej, a.tau32);
+        if (hy.kind == kHypUndecided) {
+          ++n_fp64;
+          double v[3];
+          if (hyp_f64<DIM>(a, R, ci, hc0 + hl, N, v)) {
+            hy = hyp_f32<DIM>(p0, p1, p2, seed64, DIM == 3, wmax, 0.0f, 0.0f, a.tau32);
+            if (hy.kind != kHypNormal) {
+              hy.kind = kHypExactOnly;
+              hy.thi = __int_as_float(0x7f800000);
+              hy.tlo = -1.0f;
+            }
+          } else {
+            hy.kind = kHypRejected;
           }
-        } else {
-          hy.kind = kHypRejected;
         }
+        if (hy.kind == kHypExactOnly) ++n_fp64;
+        n_ref += hy.refined;
+        S.hyp[hl] = make_float4(hy.nx, hy.ny, hy.nz, hy.kind == kHypRejected ? __int_as_float(0x7fc00000) : hy.thi);
+        S.tlo[hl] = hy.tlo;
+        S.kind[hl] = (int8_t)hy.kind;
+        S.U[hl] = hy.kind == kHypRejected ? -1 : (hy.kind == kHypExactOnly ? N : 0);
       }
-      if (hy.kind == kHypExactOnly) ++n_fp64;
-      n_ref += hy.refined;
-      S.hyp[hl] = make_float4(hy.nx, hy.ny, hy.nz, hy.kind == kHypRejected ? __int_as_float(0x7fc00000) : hy.thi);
-      S.tlo[hl] = hy.tlo;
-      S.kind[hl] = (int8_t)hy.kind;
-      S.U[hl] = hy.kind == kHypRejected ? -1 : (hy.kind == kHypExactOnly ? N : 0);
+    };
+    if constexpr (EXT && DIM == 2) {
+      if (a.line_model) {
+        for (int hl = tid; hl < nh; hl += kThreads) {
+          // Alg. 1: the line through the two normalised seed points, in FP64
+          double v[3];
+          Hyp32 hy;
+          if (line_hyp64(a, R.pre, ci, hc0 + hl, N, v)) {
+            hy = line_record(v, cs.ln_T);
+          } else {
+            hy.kind = kHypRejected;
+            hy.nx = hy.ny = hy.nz = 0.0f;
+            hy.tlo = -1.0f;
+            hy.thi = 0.0f;
+          }
+          if (hy.kind == kHypExactOnly) ++n_fp64;
+          S.hyp[hl] = make_float4(hy.nx, hy.ny, hy.nz, hy.kind == kHypRejected ? __int_as_float(0x7fc00000) : hy.thi);
+          S.tlo[hl] = hy.tlo;
+          S.kind[hl] = (int8_t)hy.kind;
+          S.U[hl] = hy.kind == kHypRejected ? -1 : (hy.kind == kHypExactOnly ? N : 0);
+        }
+      } else {
+        cosine_trials();
+      }
+    } else {
+      cosine_trials();
     }
     __syncthreads();
     stage_done(1);
@@ -649,7 +912,7 @@ __device__ void process_cluster(const FrameDesc& a, const Smem& S, ClusterShared
           const float4 hy = S.hyp[c];
           const float htlo = S.tlo[c];
           int B = 0;
-          const int C = exact_count_block<DIM, RV>(a, rows, R, ci, hc0 + c, N, hy, htlo, cs, &B);
+          const int C = exact_count_block<DIM, RV, EXT>(a, rows, R, ci, hc0 + c, N, hy, htlo, cs, &B);
           ++n_cand;
           if (tid == 0) {
             const unsigned long long k = best_key(C, hc0 + c);
@@ -675,21 +938,25 @@ __device__ void process_cluster(const FrameDesc& a, const Smem& S, ClusterShared
     }
     __syncthreads();
     stage_done(3);
-    trials_run = hc0 + nh;
     if constexpr (EXT) {
       // adaptive trial count: stop once the bound says enough trials have run
-      if (a.confidence > 0.0 && trials_run < a.H) {
-        if (tid == 0) cs.stop = adaptive_stop(cs.best, N, DIM, trials_run, a.confidence);
+      if (a.confidence > 0.0 && hc0 + nh < a.H) {
+        if (tid == 0) cs.stop = adaptive_stop(cs.best, N, DIM, hc0 + nh, a.confidence);
         __syncthreads();
-        if (cs.stop) break;
+        if (cs.stop) {
+          trials_run = hc0 + nh;
+          break;
+        }
       }
     }
   }
 
-  if (tid == 0) {
-    cs.ctr[0] += n_cand;
-    cs.ctr[4] += (unsigned long long)trials_run;
-    cs.ctr[5] += (unsigned long long)trials_run * (unsigned long long)N;
+  if (tid == 0) cs.ctr[0] += n_cand;
+  if constexpr (EXT) {
+    if (tid == 0) {
+      cs.runs[0] += (unsigned long long)trials_run;
+      cs.runs[1] += (unsigned long long)trials_run * (unsigned long long)N;
+    }
   }
   if (n_fp64) atomicAdd(&cs.ctr[2], n_fp64);
   if (n_ref) atomicAdd(&cs.ctr[3], n_ref);
@@ -710,7 +977,7 @@ __device__ void process_cluster(const FrameDesc& a, const Smem& S, ClusterShared
   const float wtlo = cs.win_tlo;
   const double v64[3] = {cs.win_v64[0], cs.win_v64[1], cs.win_v64[2]};
   constexpr int NS = DIM == 2 ? 5 : 9;
-  int n_in = mask_and_sums<DIM, RV>(a, rows, R, o, N, win, wtlo, v64, S, cs, false, nullptr);
+  int n_in = mask_and_sums<DIM, RV, EXT>(a, rows, R, o, N, win, wtlo, v64, S, cs, false, nullptr);
 
   if constexpr (EXT) {
     if (a.lo_iters > 0) n_in = local_opt_rounds<DIM, RV>(a, rows, R, o, N, win, wtlo, v64, wmax, n_in, S, cs);
@@ -758,7 +1025,10 @@ __global__ void __launch_bounds__(kThreads, RVH_MIN_BLOCKS) fused_kernel(const _
   p += (size_t)a.hchunk * sizeof(int);
   S.kind = reinterpret_cast<int8_t*>(p);
 
-  if (threadIdx.x < 6) cs.ctr[threadIdx.x] = 0ull;
+  if (threadIdx.x < 4) cs.ctr[threadIdx.x] = 0ull;
+  if constexpr (EXT) {
+    if (threadIdx.x < 2) cs.runs[threadIdx.x] = 0ull;
+  }
   if (threadIdx.x < 6) cs.clk[threadIdx.x] = 0ull;
   if (threadIdx.x == 0) fq_n = 0;
   // the queued clusters' solves and headings, one lane each
@@ -768,7 +1038,7 @@ __global__ void __launch_bounds__(kThreads, RVH_MIN_BLOCKS) fused_kernel(const _
       const FinishRec& q = fq[threadIdx.x];
       const FrameDesc& F = a.f[q.frame];
       const Rows64<DIM> R = {&F, q.o, F.rows64_g + q.o};
-      finish_cluster<DIM>(F, R, q.ci, q.N, q.hstar, q.n_in, q.t, q.v64, q.has_v64 != 0);
+      finish_cluster<DIM, EXT>(F, R, q.ci, q.N, q.hstar, q.n_in, q.t, q.v64, q.has_v64 != 0);
     }
     __syncthreads();
     if (threadIdx.x == 0) fq_n = 0;
@@ -816,7 +1086,9 @@ __global__ void __launch_bounds__(kThreads, RVH_MIN_BLOCKS) fused_kernel(const _
     if (v) atomicAdd(&a.stats[threadIdx.x], v);
   }
   if (threadIdx.x < 6 && a.stats) atomicAdd(&a.stats[4 + threadIdx.x], cs.clk[threadIdx.x]);
-  if (threadIdx.x < 2 && a.stats) atomicAdd(&a.stats[10 + threadIdx.x], cs.ctr[4 + threadIdx.x]);
+  if constexpr (EXT) {
+    if (threadIdx.x < 2 && a.stats) atomicAdd(&a.stats[10 + threadIdx.x], cs.runs[threadIdx.x]);
+  }
 }
 
 // Orders the batch's (frame, cluster) items by decreasing floor(log2(N * H))
@@ -883,7 +1155,8 @@ cudaError_t fused_occupancy(int dim, size_t smem, int* blocks_per_sm) {
 
 cudaError_t launch_fused(int dim, const FusedArgs& a, int grid, size_t smem, cudaStream_t s) {
   bool ext = false;
-  for (int f = 0; f < a.n_frames; ++f) ext = ext || a.f[f].lo_iters > 0 || a.f[f].confidence > 0.0;
+  for (int f = 0; f < a.n_frames; ++f)
+    ext = ext || a.f[f].lo_iters > 0 || a.f[f].confidence > 0.0 || a.f[f].line_model != 0;
   if (dim == 2) {
     if (ext) fused_kernel<2, true><<<grid, kThreads, smem, s>>>(a);
     else fused_kernel<2, false><<<grid, kThreads, smem, s>>>(a);

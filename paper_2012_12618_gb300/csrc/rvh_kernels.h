@@ -38,6 +38,7 @@ struct FrameDesc {
   int32_t lo_iters;          // local-optimisation rounds after the refine (0 = none)
   double confidence;         // adaptive trial count: p in (0, 1), 0 = all H trials
   int32_t trial_block;       // adaptive: trials per block between checks (0 = not adaptive)
+  int32_t line_model;        // 1: Alg. 1 as printed (normalised line fits, MAD threshold), 2D
   double* vx;
   double* vy;
   double* vz;

@@ -118,6 +118,10 @@ extern "C" int rvh_estimate_noalloc(const rvh_frame* f, const rvh_params* p, rvh
   if (p->confidence > 0.0 && p->trial_block != 0 &&
       (p->trial_block < 32 || p->trial_block > 1024 || p->trial_block % 32 != 0))
     return rvh::set_error(RVH_EINVAL, "trial_block must be 0 or a multiple of 32 in [32, 1024]");
+  if (p->hypothesis_model != RVH_MODEL_VELOCITY_PROFILE && p->hypothesis_model != RVH_MODEL_PAPER_LINE)
+    return rvh::set_error(RVH_EINVAL, "hypothesis_model must be RVH_MODEL_VELOCITY_PROFILE or RVH_MODEL_PAPER_LINE");
+  if (p->hypothesis_model == RVH_MODEL_PAPER_LINE && (p->model_dim != 2 || p->refine_iterations != 0))
+    return rvh::set_error(RVH_EINVAL, "hypothesis_model RVH_MODEL_PAPER_LINE needs model_dim 2 and refine_iterations 0");
   if (f->n_clusters == 0) return f->n_points == 0 ? RVH_OK : rvh::set_error(RVH_EINVAL, "points without clusters");
   const void* ptrs[11] = {f->azimuth, f->doppler, f->cluster_offsets, r->vx, r->vy, r->heading, r->inlier_count,
                           r->best_hypothesis, r->status, r->inlier_mask, p->model_dim == 3 ? f->elevation : f->azimuth};
@@ -159,6 +163,7 @@ extern "C" int rvh_estimate_noalloc(const rvh_frame* f, const rvh_params* p, rvh
   fd.lo_iters = p->refine_iterations;
   fd.confidence = p->confidence;
   fd.trial_block = p->confidence > 0.0 ? (p->trial_block ? p->trial_block : RVH_DEFAULT_TRIAL_BLOCK) : 0;
+  fd.line_model = p->hypothesis_model == RVH_MODEL_PAPER_LINE ? 1 : 0;
   fd.vx = r->vx;
   fd.vy = r->vy;
   fd.vz = r->vz;

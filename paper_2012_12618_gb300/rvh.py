@@ -14,6 +14,8 @@ import os
 from . import build as _build
 
 RVH_OK = 0
+RVH_MODEL_VELOCITY_PROFILE = 0
+RVH_MODEL_PAPER_LINE = 1
 RVH_PENDING = 1
 RVH_EINVAL = -1
 RVH_ENOMEM = -2
@@ -40,7 +42,8 @@ class rvh_params(ctypes.Structure):
     _fields_ = [("model_dim", ctypes.c_int32), ("num_hypotheses", ctypes.c_int32),
                 ("inlier_threshold", ctypes.c_double), ("seed", ctypes.c_uint64), ("cond_eps", ctypes.c_double),
                 ("first_cluster", ctypes.c_int32), ("refine_iterations", ctypes.c_int32),
-                ("confidence", ctypes.c_double), ("trial_block", ctypes.c_int32)]
+                ("confidence", ctypes.c_double), ("trial_block", ctypes.c_int32),
+                ("hypothesis_model", ctypes.c_int32)]
 
 
 class rvh_result(ctypes.Structure):
@@ -179,9 +182,9 @@ def make_frame(azimuth, doppler, offsets, elevation=None) -> rvh_frame:
 
 def make_params(model_dim: int, num_hypotheses: int, inlier_threshold: float, seed: int,
                 cond_eps: float = 0.0, first_cluster: int = 0, refine_iterations: int = 0,
-                confidence: float = 0.0, trial_block: int = 0) -> rvh_params:
+                confidence: float = 0.0, trial_block: int = 0, hypothesis_model: int = 0) -> rvh_params:
     return rvh_params(model_dim, num_hypotheses, inlier_threshold, seed & 0xFFFFFFFFFFFFFFFF, cond_eps,
-                      first_cluster, refine_iterations, confidence, trial_block)
+                      first_cluster, refine_iterations, confidence, trial_block, hypothesis_model)
 
 
 def make_result(out: dict) -> rvh_result:

@@ -23,7 +23,7 @@ def alloc_outputs(n_clusters: int, n_points: int, device: str):
 
 def run_rvh(ctx, az, dop, off, *, el=None, H: int, tau: float, seed: int, cond_eps: float = 0.0,
             baseline: bool = False, device: str = "cuda", stream=None, refine_iterations: int = 0,
-            confidence: float = 0.0, trial_block: int = 0) -> dict:
+            confidence: float = 0.0, trial_block: int = 0, line_model: bool = False) -> dict:
     """Runs rvh_estimate (or the baseline) through the C ABI and returns numpy outputs."""
     torch = torch_mod()
     from paper_2012_12618_gb300 import rvh
@@ -38,7 +38,7 @@ def run_rvh(ctx, az, dop, off, *, el=None, H: int, tau: float, seed: int, cond_e
     frame = rvh.make_frame(taz, tdop, toff, tel)
     params = rvh.make_params(3 if el is not None else 2, H, tau, seed, cond_eps,
                              refine_iterations=refine_iterations, confidence=confidence,
-                             trial_block=trial_block)
+                             trial_block=trial_block, hypothesis_model=1 if line_model else 0)
     res = rvh.make_result(outs)
     fn = rvh.rvh_estimate_baseline if baseline else rvh.rvh_estimate
     rc = fn(ctx.handle, frame, params, res, stream)
@@ -53,11 +53,11 @@ def run_rvh(ctx, az, dop, off, *, el=None, H: int, tau: float, seed: int, cond_e
 
 def run_oracle(az, dop, off, *, el=None, H: int, tau: float, seed: int, cond_eps=None, subset=None,
                refine_iterations: int = 0, confidence: float = 0.0, trial_block: int = 128,
-               want_trials: bool = False) -> dict:
+               want_trials: bool = False, line_model: bool = False) -> dict:
     return oracle.estimate(az, dop, off, elevation=el, num_hypotheses=H, tau=tau, seed=seed,
                            cond_eps=cond_eps, subset=subset, want_fragile=True,
                            refine_iterations=refine_iterations, confidence=confidence,
-                           trial_block=trial_block, want_trials=want_trials)
+                           trial_block=trial_block, want_trials=want_trials, line_model=line_model)
 
 
 def compare(gpu: dict, orc: dict, off, *, subset=None, vel_tol: float = 1e-6, head_tol: float = 1e-6) -> dict:

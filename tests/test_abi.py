@@ -57,6 +57,7 @@ def test_params_layout_and_refine_range():
     assert ctypes.sizeof(rvh.rvh_params) == 56
     assert rvh.rvh_params.refine_iterations.offset == 36
     assert rvh.rvh_params.confidence.offset == 40 and rvh.rvh_params.trial_block.offset == 48
+    assert rvh.rvh_params.hypothesis_model.offset == 52
     f = rvh.rvh_frame()
     r = rvh.rvh_result()
     for bad in (-1, 65):
@@ -68,3 +69,8 @@ def test_params_layout_and_refine_range():
         assert rvh.rvh_estimate_noalloc(f, p, r, None) == rvh.RVH_EINVAL
         msg = rvh.rvh_last_error(None)
         assert "confidence" in msg or "trial_block" in msg, msg
+    for dim, model, iters in ((2, 2, 0), (2, -1, 0), (3, 1, 0), (2, 1, 2)):
+        p = rvh.make_params(dim, 8, 0.1, 1, refine_iterations=iters, hypothesis_model=model)
+        assert rvh.rvh_estimate_noalloc(f, p, r, None) == rvh.RVH_EINVAL
+        msg = rvh.rvh_last_error(None)
+        assert "hypothesis_model" in msg or "model_dim" in msg, msg
