@@ -407,7 +407,8 @@ __device__ __noinline__ void line_rows_and_threshold(const FrameDesc& a, const R
     const double x = ((double)a.az[o + j] - tmin) * rt;
     const double y = ((double)a.dop[o + j] - vmin) * rv;
     pre[j] = make_double4_32a(x, y, 0.0, 0.0);
-    rows.put(j, make_float4(__double2float_rn(x), 1.0f, __double2float_rn(y), 0.0f));
+    const float y32 = __double2float_rn(y);
+    rows.put(j, make_float4(__double2float_rn(x), 1.0f, y32, y32 * kScoreScale));
   }
   __syncthreads();
   // Eq. eq:MAD read as the median absolute deviation of the normalised Doppler

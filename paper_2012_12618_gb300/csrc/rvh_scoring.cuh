@@ -81,6 +81,14 @@ __device__ __forceinline__ unsigned long long add2(unsigned long long a, unsigne
   asm("add.rn.f32x2 %0, %1, %2;" : "=l"(d) : "l"(a), "l"(b));
   return d;
 }
+// min(1, max(0, C - r^2)) in one saturated FMA (NaN gives 0).  With
+// C >= t^2 + 1 it is 1 whenever |r| <= t, and 0 once r^2 >= C; in between a
+// fraction, so sums of it bound the count of |r| <= t from above.
+__device__ __forceinline__ float sat_square(float r, float C) {
+  float e;
+  asm("{.reg .f32 n; neg.f32 n, %1; fma.rn.sat.f32 %0, n, %1, %2;}" : "=f"(e) : "f"(r), "f"(C));
+  return e;
+}
 // 1.0f if |r| <= t else 0.0f (false for NaN)
 __device__ __forceinline__ float in_band(float r, float t) {
   float e;
@@ -92,6 +100,11 @@ __device__ __forceinline__ float in_band(float r, float t) {
 // handles trial sub-group l / PW and point quads l % PW, l % PW + PW, ...;
 // the rows stage pads the last quad with NaN Dopplers, which never count.
 // Per element the arithmetic is resid_f32's: w + nz z + ny y + nx x by fmaf.
+// 2D evaluates it 2^20 times larger (the rows' fourth slot holds 2^20 w, the
+// velocity is scaled likewise, both exactly) and counts with the saturated
+// square test against C = 2^40 thi^2 + 1 rounded up, which keeps the count
+// on the FP32 pipe: U_h >= #{|r32| <= thi}, exceeding it only by points
+// whose squared residual lies within 2^-40 of thi^2.  3D counts with FSET.
 template <int DIM, int PW, int HPL>
 __device__ __forceinline__ void phase_a_tiles(const TileRows rows, int N, const Smem& S, int nh) {
   constexpr int NHL = 32 / PW;
@@ -108,18 +121,25 @@ __device__ __forceinline__ void phase_a_tiles(const TileRows rows, int N, const 
     for (int m = 0; m < HPL; ++m) {
       const int h = base + m;
       const float4 v = (h < nh) ? S.hyp[h] : make_float4(0.f, 0.f, 0.f, __int_as_float(0x7fc00000));
-      nx[m] = pack2(v.x, v.x);
-      ny[m] = pack2(v.y, v.y);
+      if (DIM == 2) {
+        const float sx = v.x * kScoreScale, sy = v.y * kScoreScale, st = v.w * kScoreScale;
+        nx[m] = pack2(sx, sx);
+        ny[m] = pack2(sy, sy);
+        th[m] = __fadd_ru(__fmul_ru(st, st), 1.0f);  // C = (2^20 thi)^2 + 1, rounded up
+      } else {
+        nx[m] = pack2(v.x, v.x);
+        ny[m] = pack2(v.y, v.y);
+        th[m] = v.w;
+      }
       nz[m] = pack2(v.z, v.z);
-      th[m] = v.w;
       acc[m] = 0ull;
     }
     for (int q = pl; q < nq; q += PW) {
-      const float4 c = rows.quad(q, 0), sn = rows.quad(q, 1), z = rows.quad(q, 2);
+      const float4 c = rows.quad(q, 0), sn = rows.quad(q, 1), z = rows.quad(q, DIM == 2 ? 3 : 2);
       const unsigned long long c01 = pack2(c.x, c.y), c23 = pack2(c.z, c.w);
       const unsigned long long s01 = pack2(sn.x, sn.y), s23 = pack2(sn.z, sn.w);
       unsigned long long w01, w23, z01 = 0ull, z23 = 0ull;
-      if (DIM == 2) {
+      if (DIM == 2) {  // 2^20 w
         w01 = pack2(z.x, z.y);
         w23 = pack2(z.z, z.w);
       } else {
@@ -142,8 +162,13 @@ __device__ __forceinline__ void phase_a_tiles(const TileRows rows, int N, const 
         float a0, a1, a2, a3;
         unpack2(r01, a0, a1);
         unpack2(r23, a2, a3);
-        acc[m] = add2(acc[m], pack2(in_band(a0, th[m]), in_band(a1, th[m])));
-        acc[m] = add2(acc[m], pack2(in_band(a2, th[m]), in_band(a3, th[m])));
+        if (DIM == 2) {
+          acc[m] = add2(acc[m], pack2(sat_square(a0, th[m]), sat_square(a1, th[m])));
+          acc[m] = add2(acc[m], pack2(sat_square(a2, th[m]), sat_square(a3, th[m])));
+        } else {
+          acc[m] = add2(acc[m], pack2(in_band(a0, th[m]), in_band(a1, th[m])));
+          acc[m] = add2(acc[m], pack2(in_band(a2, th[m]), in_band(a3, th[m])));
+        }
       }
     }
     float cnt[HPL];
@@ -151,7 +176,7 @@ __device__ __forceinline__ void phase_a_tiles(const TileRows rows, int N, const 
     for (int m = 0; m < HPL; ++m) {
       float lo, hi;
       unpack2(acc[m], lo, hi);
-      cnt[m] = lo + hi;  // exact: integers below 2^24
+      cnt[m] = lo + hi;  // integers below 2^24 (3D); 2D: at least the count (rounding is monotone)
 #pragma unroll
       for (int o = PW / 2; o > 0; o >>= 1) cnt[m] += __shfl_xor_sync(0xffffffffu, cnt[m], o);
     }
@@ -159,7 +184,7 @@ __device__ __forceinline__ void phase_a_tiles(const TileRows rows, int N, const 
 #pragma unroll
       for (int m = 0; m < HPL; ++m) {
         const int h = base + m;
-        if (h < nh && S.kind[h] == kHypNormal) S.U[h] = (int)cnt[m];
+        if (h < nh && S.kind[h] == kHypNormal) S.U[h] = (int)cnt[m];  // floor
       }
     }
   }
