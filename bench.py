@@ -210,7 +210,7 @@ def main():
                     help="local-optimisation rounds in the timed steps (default 0: the single-pass method)")
     ap.add_argument("--local-opt-steps", type=int, default=50,
                     help="steps of each extra measurement on the same frame: 2 local-optimisation rounds, "
-                         "and the adaptive trial count at confidence 0.99 (0 skips them)")
+                         "the adaptive trial count at confidence 0.99, and Alg. 1's line model (0 skips them)")
     args = ap.parse_args()
     if args.impl == "reference":
         return reference_arm(args)
@@ -336,6 +336,19 @@ def main():
                                        if clocks.get("sm_mhz") else None),
             "basis": "scoring-pass share of the per-CTA stage clocks x kernel time"}
 
+    # ---- serving: 64 radars x 20 frames/s (Poisson), mixed 2D/3D, continuous batching
+    # (right after the timed steps, before the other measurements churn the GPU)
+    serve = None
+    if args.serving_seconds > 0 and rank == 0:
+        from paper_2012_12618_gb300 import serving
+        spec = synth.ServingSpec(duration_s=args.serving_seconds, warmup_s=0.5)
+        sres = serving.run_load(ctx, spec, dev)
+        serve = sres.summary()
+        serve["config"] = (f"{spec.n_radars} radars x {spec.fps:g} frames/s Poisson, clusters "
+                           f"{spec.clusters_lo}..{spec.clusters_hi} per frame, sizes log-uniform "
+                           f"{spec.size_lo}..{spec.size_hi}; radars 0-31 2D H=256, 32-63 3D H=2048; "
+                           f"{spec.duration_s:g} s measured after {spec.warmup_s:g} s")
+
     # ---- local-optimisation rounds (refine_iterations = 2) on the same frame:
     # kernel time and how many mask entries the rounds change
     local_opt = None
@@ -385,6 +398,32 @@ def main():
                                                   .float().mean().item()),
                     "steps": args.local_opt_steps}
 
+    # ---- Alg. 1 as printed (line fits in the normalised plane, MAD threshold) on
+    # the same frame: kernel time and velocity error against the synthetic truth
+    paper_line = None
+    if args.local_opt_steps > 0 and args.refine_iterations == 0 and dim == 2:
+        pl_outs = rvh.alloc_outputs(nc, npts, dev)
+        pl_res = rvh.make_result(pl_outs)
+        pl_params = rvh.make_params(dim, w.num_hypotheses, w.tau, w.seed, hypothesis_model=rvh.RVH_MODEL_PAPER_LINE)
+        pl_ms = []
+        for i in range(3 + args.local_opt_steps):
+            flush.fill_(7)
+            ctx.check(rvh.rvh_estimate(ctx.handle, frame, pl_params, pl_res, sptr), "rvh_estimate(paper line)")
+            ctx.check(rvh.rvh_get_stats(ctx.handle, stats), "rvh_get_stats")
+            if i >= 3:
+                pl_ms.append(stats.kernel_ms)
+        torch.cuda.synchronize()
+
+        def verr(o):
+            return float(np.nanmedian(np.hypot(o["vx"].cpu().numpy() - f.truth_v[:, 0],
+                                               o["vy"].cpu().numpy() - f.truth_v[:, 1])))
+
+        pk = float(np.mean(pl_ms))
+        paper_line = {"kernel_ms": pk, "clusters_per_s": nc / (pk * 1e-3),
+                      "median_velocity_error_m_s": verr(pl_outs),
+                      "median_velocity_error_cosine_model_m_s": verr(outs),
+                      "inliers": int(pl_outs["inlier_count"].sum().item()), "steps": args.local_opt_steps}
+
     # ---- end to end through the C ABI with pinned host buffers (copies inside the timed region)
     h_az = torch.from_numpy(f.azimuth).pin_memory()
     h_el = None if f.elevation is None else torch.from_numpy(f.elevation).pin_memory()
@@ -427,18 +466,6 @@ def main():
                     "one launch per cluster", "ms_per_step": bms, "fused_speedup": value / ws / (nc / (bms * 1e-3)),
                     "identical_masks_and_winners": same}
 
-    # ---- serving: 64 radars x 20 frames/s (Poisson), mixed 2D/3D, continuous batching
-    serve = None
-    if args.serving_seconds > 0 and rank == 0:
-        from paper_2012_12618_gb300 import serving
-        spec = synth.ServingSpec(duration_s=args.serving_seconds, warmup_s=0.5)
-        sres = serving.run_load(ctx, spec, dev)
-        serve = sres.summary()
-        serve["config"] = (f"{spec.n_radars} radars x {spec.fps:g} frames/s Poisson, clusters "
-                           f"{spec.clusters_lo}..{spec.clusters_hi} per frame, sizes log-uniform "
-                           f"{spec.size_lo}..{spec.size_hi}; radars 0-31 2D H=256, 32-63 3D H=2048; "
-                           f"{spec.duration_s:g} s measured after {spec.warmup_s:g} s")
-
     # ---- the FP64 oracle on this host (rank 0, N = 1 only)
     cpu = cpu_all = None
     if rank == 0 and ws == 1 and not args.no_cpu_baseline:
@@ -472,6 +499,7 @@ def main():
             "serving": serve,
             "local_opt": local_opt,
             "adaptive": adaptive,
+            "paper_line": paper_line,
             "e2e": e2e,
             "clocks": clocks,
             "gpu_launches": launches,

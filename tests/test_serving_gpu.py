@@ -80,6 +80,46 @@ def test_results_same_alone_and_in_the_mix(torch):
         ctx.close()
 
 
+def test_extension_frames_same_alone_and_in_the_mix(torch):
+    """Frames that use the extensions (local optimisation, adaptive trial
+    count, Alg. 1's line model) batched with plain frames: a batch holding
+    any of them runs the extension instantiation of the kernel for all its
+    frames, and every result must still equal the frame's result alone."""
+    dev = torch.device("cuda", 0)
+    frames = _frames()
+    ext = {0: dict(refine_iterations=2), 1: dict(confidence=0.99, trial_block=64),
+           2: dict(hypothesis_model=rvh.RVH_MODEL_PAPER_LINE), 5: dict(confidence=0.999, refine_iterations=1)}
+    ctx = rvh.Context(0)
+    try:
+        inputs, alone = [], []
+        for i, (f, w, seed) in enumerate(frames):
+            kw = ext.get(i, {})
+            if kw.get("hypothesis_model") and w.model_dim != 2:
+                kw = {}
+            t = [torch.from_numpy(x).to(dev) if x is not None else None
+                 for x in (f.azimuth, f.elevation, f.doppler, f.offsets)]
+            frame = rvh.make_frame(t[0], t[2], t[3], t[1])
+            params = rvh.make_params(w.model_dim, w.num_hypotheses, w.tau, seed, **kw)
+            outs = rvh.alloc_outputs(f.n_clusters, f.n_points, dev)
+            ctx.check(rvh.rvh_estimate(ctx.handle, frame, params, rvh.make_result(outs), None), "estimate")
+            torch.cuda.synchronize()
+            alone.append(_np(outs, f.n_points))
+            inputs.append((frame, params, t))  # t keeps the device inputs alive
+        tickets = []
+        for i in range(len(frames)):
+            f = frames[i][0]
+            outs = rvh.alloc_outputs(f.n_clusters, f.n_points, dev)
+            tk = ctypes.c_uint64(0)
+            ctx.check(rvh.rvh_submit(ctx.handle, inputs[i][0], inputs[i][1], rvh.make_result(outs), tk), "submit")
+            tickets.append((i, tk.value, outs))
+        for i, tk, outs in tickets:
+            assert rvh.rvh_wait(ctx.handle, tk, 30_000_000) == rvh.RVH_OK, rvh.rvh_last_error(None)
+            torch.cuda.synchronize()
+            _same(_np(outs, frames[i][0].n_points), alone[i])
+    finally:
+        ctx.close()
+
+
 def test_poll_semantics(torch):
     dev = torch.device("cuda", 0)
     f, w, seed = _frames()[0]
