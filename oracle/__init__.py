@@ -136,3 +136,23 @@ def estimate(azimuth, doppler, offsets, *, elevation=None, num_hypotheses: int, 
     if want_trials:
         out["trials_used"] = trials
     return out
+
+
+def dbscan(features, eps: float, min_pts: int, _lib=None) -> dict:
+    """DBSCAN of the rows of `features` ([n, dim], dim 1..4, widened to FP64
+    exactly): labels (cluster ids numbered by smallest core index, -1 noise),
+    core flags and the cluster count."""
+    f = np.ascontiguousarray(features, dtype=np.float64)
+    if f.ndim == 1:
+        f = f[:, None]
+    n, dim = f.shape
+    labels = np.zeros(n, np.int32)
+    core = np.zeros(n, np.uint8)
+    nc = ctypes.c_int32(0)
+    L = _lib or lib()
+    L.oracle_dbscan.restype = ctypes.c_int
+    rc = L.oracle_dbscan(_p(f), ctypes.c_int64(n), ctypes.c_int32(dim), ctypes.c_double(eps),
+                         ctypes.c_int32(min_pts), _p(labels), _p(core), ctypes.byref(nc))
+    if rc != 0:
+        raise ValueError("oracle_dbscan rejected its arguments")
+    return {"labels": labels, "core": core.astype(bool), "n_clusters": int(nc.value)}

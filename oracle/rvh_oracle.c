@@ -497,3 +497,71 @@ int oracle_estimate(const double* azimuth, const double* elevation, const double
   }
   return 0;
 }
+
+/* ---------------------------------------------------------------------------
+ * DBSCAN (Ester, Kriegel, Sander, Xu, KDD'96), the clustering that precedes
+ * the estimator in Fig. 1.  Brute force over all pairs: plain and O(n^2).
+ * ------------------------------------------------------------------------- */
+
+/* Squared Euclidean distance, accumulated in FP64 over the components in order. */
+static double feat_dist2(const double* a, const double* b, int32_t dim) {
+  double s = 0.0;
+  for (int32_t k = 0; k < dim; ++k) {
+    double d = a[k] - b[k];
+    s = s + d * d;
+  }
+  return s;
+}
+
+int oracle_dbscan(const double* feat, int64_t n, int32_t dim, double eps, int32_t min_pts,
+                  int32_t* labels, uint8_t* core, int32_t* n_clusters) {
+  if (n < 0 || dim < 1 || dim > 4 || !(eps >= 0.0) || min_pts < 1 || !labels || !n_clusters) return -1;
+  if (n > 0 && !feat) return -1;
+  const double eps2 = eps * eps;
+  uint8_t* is_core = (uint8_t*)calloc((size_t)(n > 0 ? n : 1), 1);
+  int64_t* stack = (int64_t*)malloc(sizeof(int64_t) * (size_t)(n > 0 ? n : 1));
+  /* core points: at least min_pts neighbours, the point itself included */
+  for (int64_t p = 0; p < n; ++p) {
+    int64_t count = 0;
+    for (int64_t q = 0; q < n && count < min_pts; ++q)
+      if (feat_dist2(&feat[p * dim], &feat[q * dim], dim) <= eps2) ++count;
+    is_core[p] = count >= min_pts;
+    labels[p] = -1;
+  }
+  /* clusters: grow each from its lowest-index unlabelled core point over the
+   * core-to-core neighbour relation */
+  int32_t c = 0;
+  for (int64_t p = 0; p < n; ++p) {
+    if (!is_core[p] || labels[p] != -1) continue;
+    int64_t top = 0;
+    labels[p] = c;
+    stack[top++] = p;
+    while (top > 0) {
+      int64_t u = stack[--top];
+      for (int64_t q = 0; q < n; ++q) {
+        if (!is_core[q] || labels[q] != -1) continue;
+        if (feat_dist2(&feat[u * dim], &feat[q * dim], dim) <= eps2) {
+          labels[q] = c;
+          stack[top++] = q;
+        }
+      }
+    }
+    ++c;
+  }
+  /* border points: the cluster of the lowest-index core neighbour */
+  for (int64_t p = 0; p < n; ++p) {
+    if (is_core[p]) continue;
+    for (int64_t q = 0; q < n; ++q) {
+      if (is_core[q] && feat_dist2(&feat[p * dim], &feat[q * dim], dim) <= eps2) {
+        labels[p] = labels[q];
+        break;
+      }
+    }
+  }
+  if (core)
+    for (int64_t p = 0; p < n; ++p) core[p] = is_core[p];
+  *n_clusters = c;
+  free(is_core);
+  free(stack);
+  return 0;
+}

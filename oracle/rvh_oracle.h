@@ -109,6 +109,14 @@ int oracle_estimate(const double* azimuth, const double* elevation, const double
                     int32_t* inlier_count, int32_t* best_hypothesis, int32_t* status,
                     uint8_t* mask, int32_t* hyp_counts, uint8_t* fragile, int32_t* trials_used);
 
+/* DBSCAN over n feature vectors of `dim` (1..4) FP64 components (row-major):
+ * the clustering stage of Fig. 1 that forms the clusters the estimator takes.
+ * labels[n] receives cluster ids 0..n_clusters-1 (numbered in the order of
+ * their smallest core-point index) or -1 for noise; core[n] (optional)
+ * receives 1 for core points.  Returns 0, or -1 on invalid arguments. */
+int oracle_dbscan(const double* feat, int64_t n, int32_t dim, double eps, int32_t min_pts,
+                  int32_t* labels, uint8_t* core, int32_t* n_clusters);
+
 #ifdef __cplusplus
 }
 #endif

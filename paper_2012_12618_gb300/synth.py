@@ -210,3 +210,97 @@ def serving_frame(spec: ServingSpec, radar: int, frame_no: int) -> tuple[Frame, 
     nc = int(rng.integers(spec.clusters_lo, spec.clusters_hi + 1))
     sizes = draw_sizes(rng, nc, "loguniform", spec.size_lo, spec.size_hi)
     return make_frame(w, sizes=sizes, gen_seed=fseed + 1), w
+
+
+# ---- raw scenes for the clustering stage (Fig. 1: point cloud -> clusters) -----------------
+
+@dataclasses.dataclass
+class Scene:
+    """An unclustered radar point cloud: objects plus clutter, in random order."""
+    x: np.ndarray            # [n] m, FP32 (longitudinal)
+    y: np.ndarray            # [n] m, FP32 (lateral)
+    azimuth: np.ndarray      # [n] rad, FP32, atan2(y, x)
+    doppler: np.ndarray      # [n] m/s, FP32
+    object_id: np.ndarray    # [n] int, the object a point came from, -1 for clutter
+    truth_v: np.ndarray      # [n_objects, 2] true (vx, vy)
+
+    @property
+    def n_points(self) -> int:
+        return int(self.x.shape[0])
+
+    def features(self) -> np.ndarray:
+        """[n, 2] FP32 feature vectors (x, y) for DBSCAN."""
+        return np.stack([self.x, self.y], axis=1)
+
+
+@dataclasses.dataclass(frozen=True)
+class SceneSpec:
+    name: str
+    n_objects: int
+    size_lo: int = 8
+    size_hi: int = 1024
+    range_lo: float = 5.0      # m
+    range_hi: float = 300.0   # field of view: centres on 10 m cells within range_lo + 10 .. range_hi
+    spread_lo: float = 0.3     # per-object position spread (sigma, m)
+    spread_hi: float = 1.2
+    clutter_frac: float = 0.03
+    outlier_frac: float = 0.20
+    noise_sigma: float = 0.05
+    speed_max: float = 40.0
+    eps: float = 1.0           # DBSCAN radius (m) the scene is drawn for
+    min_pts: int = 4
+    gen_seed: int = 9
+
+
+SCENES = {
+    "scene_small": SceneSpec("scene_small", 48, size_hi=128, range_hi=120.0, gen_seed=9),
+    "scene": SceneSpec("scene", 512, range_hi=400.0, gen_seed=10),
+}
+
+
+def make_scene(s: SceneSpec, *, n_objects: int | None = None, gen_seed: int | None = None) -> Scene:
+    """Objects at separated positions in the field of view (azimuth +-60 deg,
+    centres on a jittered 10 m grid), each a Gaussian blob of points whose Doppler follows
+    the velocity profile of Eq. (LSQ_eq) with noise and micro-Doppler
+    outliers, plus uniformly scattered clutter; points shuffled."""
+    rng = np.random.default_rng(s.gen_seed if gen_seed is None else gen_seed)
+    n_obj = s.n_objects if n_objects is None else n_objects
+    # centres on a jittered grid of cells inside the +-60 deg wedge, so that
+    # blobs (3 sigma <= 3.6 m) stay more than eps apart
+    cell = 10.0
+    gx, gy = np.meshgrid(np.arange(0.0, s.range_hi, cell) + cell / 2,
+                         np.arange(-s.range_hi, s.range_hi, cell) + cell / 2, indexing="ij")
+    gr, ga = np.hypot(gx, gy), np.arctan2(gy, gx)
+    ok = (gr >= s.range_lo + cell) & (gr <= s.range_hi) & (np.abs(ga) <= 60.0 * DEG)
+    gx, gy = gx[ok], gy[ok]
+    if gx.shape[0] < n_obj:
+        raise ValueError("field of view too small for the number of objects")
+    pick = rng.choice(gx.shape[0], size=n_obj, replace=False)
+    cx = gx[pick] + rng.uniform(-0.1, 0.1, size=n_obj) * cell
+    cy = gy[pick] + rng.uniform(-0.1, 0.1, size=n_obj) * cell
+    sizes = draw_sizes(rng, n_obj, "loguniform", s.size_lo, s.size_hi)
+    oid = np.repeat(np.arange(n_obj), sizes)
+    spread = rng.uniform(s.spread_lo, s.spread_hi, size=n_obj)
+    px = cx[oid] + rng.normal(0.0, 1.0, size=oid.shape[0]) * spread[oid]
+    py = cy[oid] + rng.normal(0.0, 1.0, size=oid.shape[0]) * spread[oid]
+    speed = rng.uniform(0.0, s.speed_max, size=n_obj)
+    head = rng.uniform(0.0, 2.0 * math.pi, size=n_obj)
+    vx, vy = speed * np.cos(head), speed * np.sin(head)
+    theta = np.arctan2(py, px)
+    dop = vx[oid] * np.cos(theta) + vy[oid] * np.sin(theta) + rng.normal(0.0, s.noise_sigma, size=oid.shape[0])
+    out = rng.random(oid.shape[0]) < s.outlier_frac
+    dop[out] = rng.uniform(0.0, 2.0, size=int(out.sum())) * speed[oid[out]]
+    # clutter over the field of view
+    nclut = int(round(s.clutter_frac * oid.shape[0]))
+    r = np.exp(rng.uniform(math.log(s.range_lo), math.log(s.range_hi), size=nclut))
+    a = rng.uniform(-60.0 * DEG, 60.0 * DEG, size=nclut)
+    px = np.concatenate([px, r * np.cos(a)])
+    py = np.concatenate([py, r * np.sin(a)])
+    dop = np.concatenate([dop, rng.uniform(-s.speed_max, s.speed_max, size=nclut)])
+    oid = np.concatenate([oid, np.full(nclut, -1)])
+    perm = rng.permutation(oid.shape[0])
+    px32, py32 = px[perm].astype(np.float32), py[perm].astype(np.float32)
+    return Scene(x=px32, y=py32,
+                 azimuth=np.arctan2(py32.astype(np.float64), px32.astype(np.float64)).astype(np.float32),
+                 doppler=dop[perm].astype(np.float32), object_id=oid[perm],
+                 truth_v=np.stack([vx, vy], axis=1))

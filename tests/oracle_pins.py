@@ -27,6 +27,12 @@ violation.  What pins what:
               of the seed difference, an independent formula); the refine
               is numpy.linalg.lstsq of the inliers; 2^m Doppler scaling is
               exact; affine (azimuth, Doppler) data is all inliers
+  dbscan      the clustering stage: core points, noise and the partition of
+              core points equal scikit-learn's DBSCAN; border points join
+              their lowest-index core neighbour (numpy distance matrix);
+              cluster ids follow the smallest core index; min_pts = 1 gives
+              the connected components of the eps-graph (scipy); permuting
+              the input permutes the result
   local_opt   the re-threshold + re-fit rounds: one round's inlier set is
               numpy's re-threshold of the refined velocity, every result is
               numpy.linalg.lstsq of its own inlier set, a converged result is
@@ -478,6 +484,67 @@ def check_paper_line(L):
     assert deg["status"][0] == oracle.ALL_DEGENERATE
 
 
+def _canonical(labels):
+    """Partition as a set of frozensets of point indices (noise dropped)."""
+    out = {}
+    for i, l in enumerate(labels.tolist()):
+        if l >= 0:
+            out.setdefault(l, []).append(i)
+    return {frozenset(v) for v in out.values()}
+
+
+def check_dbscan(L):
+    pytest_sklearn = __import__("importlib").util.find_spec("sklearn") is not None
+    rng = np.random.default_rng(17)
+    cases = [(rng.uniform(0, 20, (400, 2)), 0.9, 4), (rng.normal(0, 3, (300, 3)), 1.1, 5),
+             (rng.uniform(0, 10, (250, 1)), 0.08, 3), (rng.uniform(0, 6, (200, 4)), 1.6, 6)]
+    w = synth.make_scene(synth.SCENES["scene_small"])
+    cases.append((w.features().astype(np.float64), 1.0, 4))
+    for f, eps, mp in cases:
+        f = f.astype(np.float32).astype(np.float64)
+        D = np.sqrt(((f[:, None, :] - f[None, :, :]) ** 2).sum(-1))
+        if np.min(np.abs(D - eps)) < 1e-9 * eps:
+            continue
+        o = oracle.dbscan(f, eps, mp, _lib=L)
+        lab, core = o["labels"], o["core"]
+        nb = D <= eps
+        assert np.array_equal(core, nb.sum(1) >= mp)
+        # numbering: cluster ids in the order of their smallest core index
+        firsts = [int(np.flatnonzero(core & (lab == c))[0]) for c in range(o["n_clusters"])]
+        assert firsts == sorted(firsts)
+        # border points: the lowest-index core neighbour's cluster; noise: no core neighbour
+        for p in np.flatnonzero(~core):
+            cn = np.flatnonzero(nb[p] & core)
+            assert lab[p] == (lab[cn[0]] if cn.size else -1), p
+        if pytest_sklearn:
+            from sklearn.cluster import DBSCAN
+            sk = DBSCAN(eps=eps, min_samples=mp).fit(f)
+            skcore = np.zeros(f.shape[0], bool)
+            skcore[sk.core_sample_indices_] = True
+            assert np.array_equal(core, skcore)
+            assert np.array_equal(lab == -1, sk.labels_ == -1)
+            assert _canonical(np.where(core, lab, -1)) == _canonical(np.where(core, sk.labels_, -1))
+        # permuting the points permutes the partition of the core points
+        perm = rng.permutation(f.shape[0])
+        op = oracle.dbscan(f[perm], eps, mp, _lib=L)
+        back = np.empty_like(perm)
+        back[perm] = np.arange(perm.shape[0])
+        assert np.array_equal(op["core"][back], core)
+        assert _canonical(np.where(core, op["labels"][back], -1)) == _canonical(np.where(core, lab, -1))
+    # min_pts = 1: every point is core; clusters = connected components of the eps-graph
+    from scipy.sparse.csgraph import connected_components
+    f = rng.uniform(0, 12, (300, 2)).astype(np.float32).astype(np.float64)
+    D = np.sqrt(((f[:, None, :] - f[None, :, :]) ** 2).sum(-1))
+    o = oracle.dbscan(f, 0.7, 1, _lib=L)
+    ncc, cc = connected_components(D <= 0.7, directed=False)
+    assert o["core"].all() and o["n_clusters"] == ncc
+    assert _canonical(o["labels"]) == _canonical(cc)
+    # eps = 0: only coincident points are neighbours
+    g = np.repeat(np.arange(5.0)[:, None], 3, axis=0)
+    o = oracle.dbscan(g, 0.0, 3, _lib=L)
+    assert o["n_clusters"] == 5 and o["core"].all()
+
+
 ALL_CHECKS = [check_philox, check_draws, check_recovery, check_brute, check_symmetry,
               check_rotation, check_lstsq, check_status, check_planted, check_local_opt, check_adaptive,
-              check_paper_line]
+              check_paper_line, check_dbscan]

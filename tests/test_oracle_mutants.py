@@ -61,6 +61,15 @@ MUTANTS = {
     "line_norm_swapped_range": ("double rv = vmax > vmin ? 1.0 / (vmax - vmin) : 0.0;",
                                 "double rv = tmax > tmin ? 1.0 / (tmax - tmin) : 0.0;"),
     "line_slope_inverted": ("double m = (yn[qs[1]] - yn[qs[0]]) / dx;", "double m = dx / (yn[qs[1]] - yn[qs[0]]);"),
+    "dbscan_strict_eps": ("if (feat_dist2(&feat[p * dim], &feat[q * dim], dim) <= eps2) ++count;",
+                          "if (feat_dist2(&feat[p * dim], &feat[q * dim], dim) < eps2 * 0.999) ++count;"),
+    "dbscan_self_not_counted": ("is_core[p] = count >= min_pts;", "is_core[p] = count > min_pts;"),
+    "dbscan_border_any_point": ("if (is_core[q] && feat_dist2(&feat[p * dim], &feat[q * dim], dim) <= eps2) {",
+                                "if (labels[q] >= 0 && feat_dist2(&feat[p * dim], &feat[q * dim], dim) <= eps2) {"),
+    "dbscan_dist_dropped_dim": ("for (int32_t k = 0; k < dim; ++k) {\n    double d = a[k] - b[k];",
+                                "for (int32_t k = 1; k < dim; ++k) {\n    double d = a[k] - b[k];"),
+    "dbscan_grow_through_border": ("        if (!is_core[q] || labels[q] != -1) continue;\n        if (feat_dist2(&feat[u * dim]",
+                                   "        if (labels[q] != -1) continue;\n        if (feat_dist2(&feat[u * dim]"),
 }
 
 
