@@ -223,6 +223,45 @@ int rvh_estimate_baseline(rvh_ctx* ctx, const rvh_frame* frame, const rvh_params
 #define RVH_NOALLOC_MAX_CLUSTERS 65536
 int rvh_estimate_noalloc(const rvh_frame* frame, const rvh_params* params, rvh_result* result, void* stream);
 
+/* ---- clustering stage ------------------------------------------------------------ */
+/* The clustering that precedes the estimator in Fig. 1 (the paper names NN,
+ * DBSCAN and grid DBSCAN): DBSCAN (Ester, Kriegel, Sander, Xu, KDD'96) over
+ * caller-chosen FP32 feature vectors, e.g. point positions.
+ *   - q is a neighbour of p (p itself included) when the squared Euclidean
+ *     distance of their feature vectors, accumulated in FP64 over the
+ *     components in order, is at most eps^2;
+ *   - p is a core point when it has at least min_pts neighbours;
+ *   - clusters are the connected components of core points under the
+ *     neighbour relation, numbered 0.. in the order of their smallest core
+ *     point index;
+ *   - a non-core point with a core neighbour joins the cluster of its
+ *     lowest-index core neighbour (DBSCAN itself leaves this to the visit
+ *     order); every other point is noise, label -1.
+ * features: [n_points * dim] row-major, dim in 1..4, device memory.
+ * labels [n_points], perm [n_points] and offsets [max_clusters + 1]: device
+ * memory, caller-owned.  perm lists the clustered points cluster by
+ * cluster, each cluster's points in increasing index order (noise omitted);
+ * offsets is its CSR: cluster c owns perm[offsets[c] .. offsets[c+1]-1], so
+ * offsets[n_clusters] is the number of clustered points.  *n_clusters (host
+ * memory) receives the cluster count.  n_points <= 4,194,304.  The call is
+ * ordered on `stream` (NULL: the context's stream) and returns after it has
+ * completed (it reads the cluster count back).  More than max_clusters
+ * clusters: RVH_EINVAL with *n_clusters and labels set, perm and offsets
+ * not written.  The context's memory budget covers the scratch (about
+ * 45 bytes per point plus 8 bytes per point rounded up to a power of two). */
+int rvh_cluster(rvh_ctx* ctx, const float* features, int64_t n_points, int32_t dim, double eps, int32_t min_pts,
+                int32_t* labels, int32_t* perm, int32_t* offsets, int32_t max_clusters, int32_t* n_clusters,
+                void* stream);
+
+/* Gathers up to three FP32 point arrays into cluster order: dst_k[j] =
+ * src_k[perm[j]] for j < m (a NULL src_k skips that array).  All pointers
+ * device memory; ordered on `stream` (NULL: the context's stream), returns
+ * once the work is enqueued.  With perm and offsets from rvh_cluster the
+ * gathered azimuth / elevation / Doppler arrays and offsets form the
+ * rvh_frame of the clustered points. */
+int rvh_gather(rvh_ctx* ctx, const int32_t* perm, int64_t m, const float* src0, float* dst0, const float* src1,
+               float* dst1, const float* src2, float* dst2, void* stream);
+
 /* ---- streaming (serving) -------------------------------------------------------- */
 /* Queues a frame for continuous batching.  Host inputs are copied into the
  * context's device pool before the call returns; device inputs must stay

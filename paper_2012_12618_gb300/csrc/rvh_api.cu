@@ -130,6 +130,8 @@ struct rvh_ctx {
   // scratch of rvh_estimate / rvh_estimate_baseline
   void* scratch = nullptr;
   size_t scratch_bytes = 0;
+  void* cl_scratch = nullptr;  // scratch of rvh_cluster
+  size_t cl_scratch_bytes = 0;
   cudaEvent_t last_done = nullptr;
   cudaEvent_t ev0 = nullptr, ev1 = nullptr;
   unsigned long long* stats_d = nullptr;
@@ -433,6 +435,7 @@ void rvh_destroy(rvh_ctx* ctx) {
   cudaStreamSynchronize(ctx->stream);
   if (ctx->gexec) cudaGraphExecDestroy(ctx->gexec);
   if (ctx->scratch) ctx_free(ctx, ctx->scratch, ctx->scratch_bytes);
+  if (ctx->cl_scratch) ctx_free(ctx, ctx->cl_scratch, ctx->cl_scratch_bytes);
   if (ctx->trig) ctx_free(ctx, ctx->trig, sizeof(double2) * kTrigSize);
   cudaEventDestroy(ctx->last_done);
   cudaEventDestroy(ctx->ev0);
@@ -442,6 +445,64 @@ void rvh_destroy(rvh_ctx* ctx) {
 }
 
 const char* rvh_last_error(rvh_ctx*) { return g_err.c_str(); }
+
+int rvh_cluster(rvh_ctx* ctx, const float* features, int64_t n_points, int32_t dim, double eps, int32_t min_pts,
+                int32_t* labels, int32_t* perm, int32_t* offsets, int32_t max_clusters, int32_t* n_clusters,
+                void* stream) {
+  if (!ctx) return fail(RVH_EINVAL, "ctx is NULL");
+  if (!n_clusters) return fail(RVH_EINVAL, "n_clusters is NULL");
+  if (dim < 1 || dim > 4) return fail(RVH_EINVAL, "dim must be 1..4");
+  if (!(eps >= 0.0) || !std::isfinite(eps)) return fail(RVH_EINVAL, "eps must be finite and >= 0");
+  if (min_pts < 1) return fail(RVH_EINVAL, "min_pts must be >= 1");
+  if (n_points < 0 || n_points > cluster_max_points())
+    return fail(RVH_EINVAL, "n_points out of range [0, " + std::to_string(cluster_max_points()) + "]");
+  if (max_clusters < 0) return fail(RVH_EINVAL, "max_clusters < 0");
+  *n_clusters = 0;
+  if (n_points == 0) return RVH_OK;
+  if (!is_device_ptr(features) || !is_device_ptr(labels) || !is_device_ptr(perm) || !is_device_ptr(offsets))
+    return fail(RVH_EINVAL, "features, labels, perm and offsets must be device memory");
+  std::lock_guard<std::mutex> lk(ctx->mu);
+  RVH_CUDA(cudaSetDevice(ctx->device));
+  cudaStream_t s = stream ? (cudaStream_t)stream : ctx->stream;
+  RVH_CUDA(cudaStreamWaitEvent(s, ctx->last_done, 0));
+  const size_t need = cluster_scratch_bytes(n_points);
+  if (need > ctx->cl_scratch_bytes) {
+    RVH_CUDA(cudaEventSynchronize(ctx->last_done));
+    if (ctx->cl_scratch) ctx_free(ctx, ctx->cl_scratch, ctx->cl_scratch_bytes);
+    ctx->cl_scratch = nullptr;
+    ctx->cl_scratch_bytes = 0;
+    int rc = ctx_alloc(ctx, &ctx->cl_scratch, need);
+    if (rc) return rc;
+    ctx->cl_scratch_bytes = need;
+  }
+  int nc = 0, err = 0;
+  RVH_CUDA(launch_cluster(features, n_points, dim, eps, min_pts, ctx->cl_scratch, labels, perm, offsets,
+                          max_clusters, &nc, &err, s));
+  RVH_CUDA(cudaEventRecord(ctx->last_done, s));
+  *n_clusters = nc;
+  if (err) return fail(RVH_ECUDA, "rvh_cluster: a union did not settle within its retry limit");
+  if (nc > max_clusters)
+    return fail(RVH_EINVAL, "rvh_cluster: " + std::to_string(nc) + " clusters exceed max_clusters " +
+                                std::to_string(max_clusters) + " (labels written, perm and offsets not)");
+  return RVH_OK;
+}
+
+int rvh_gather(rvh_ctx* ctx, const int32_t* perm, int64_t m, const float* src0, float* dst0, const float* src1,
+               float* dst1, const float* src2, float* dst2, void* stream) {
+  if (!ctx) return fail(RVH_EINVAL, "ctx is NULL");
+  if (m < 0 || m > 0x7fffffffLL) return fail(RVH_EINVAL, "m out of range");
+  if (m == 0) return RVH_OK;
+  if (!is_device_ptr(perm)) return fail(RVH_EINVAL, "perm must be device memory");
+  const float* srcs[3] = {src0, src1, src2};
+  float* dsts[3] = {dst0, dst1, dst2};
+  for (int k = 0; k < 3; ++k)
+    if (srcs[k] && (!is_device_ptr(srcs[k]) || !dsts[k] || !is_device_ptr(dsts[k])))
+      return fail(RVH_EINVAL, "each gathered array and its destination must be device memory");
+  RVH_CUDA(cudaSetDevice(ctx->device));
+  cudaStream_t s = stream ? (cudaStream_t)stream : ctx->stream;
+  RVH_CUDA(launch_gather(perm, m, src0, dst0, src1, dst1, src2, dst2, s));
+  return RVH_OK;
+}
 
 int rvh_set_schedule(rvh_ctx* ctx, int32_t pw, int32_t hpl) {
   if (!ctx) return fail(RVH_EINVAL, "ctx is NULL");

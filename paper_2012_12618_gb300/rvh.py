@@ -87,6 +87,9 @@ SIGNATURES = {
     "rvh_set_schedule": (ctypes.c_int, [_P, ctypes.c_int32, ctypes.c_int32]),
     "rvh_autotune": (ctypes.c_int, [_P, ctypes.POINTER(rvh_frame), ctypes.POINTER(rvh_params),
                                     ctypes.POINTER(rvh_result), ctypes.c_int32, ctypes.POINTER(rvh_schedule)]),
+    "rvh_cluster": (ctypes.c_int, [_P, _P, ctypes.c_int64, ctypes.c_int32, ctypes.c_double, ctypes.c_int32,
+                                   _P, _P, _P, ctypes.c_int32, ctypes.POINTER(ctypes.c_int32), _P]),
+    "rvh_gather": (ctypes.c_int, [_P, _P, ctypes.c_int64, _P, _P, _P, _P, _P, _P, _P]),
 }
 
 _lib = None
@@ -160,6 +163,17 @@ def rvh_set_schedule(ctx, points_per_warp: int, hyps_per_lane: int) -> int:
 def rvh_autotune(ctx, frame, params, result, reps: int, best) -> int:
     return load().rvh_autotune(ctx, ctypes.byref(frame), ctypes.byref(params), ctypes.byref(result), reps,
                                None if best is None else ctypes.byref(best))
+
+
+def rvh_cluster(ctx, features, n_points: int, dim: int, eps: float, min_pts: int, labels, perm, offsets,
+                max_clusters: int, n_clusters, stream=None) -> int:
+    return load().rvh_cluster(ctx, ptr(features), n_points, dim, eps, min_pts, ptr(labels), ptr(perm),
+                              ptr(offsets), max_clusters, ctypes.byref(n_clusters), stream)
+
+
+def rvh_gather(ctx, perm, m: int, src0, dst0, src1=None, dst1=None, src2=None, dst2=None, stream=None) -> int:
+    return load().rvh_gather(ctx, ptr(perm), m, ptr(src0), ptr(dst0), ptr(src1), ptr(dst1), ptr(src2),
+                             ptr(dst2), stream)
 
 
 # ---- marshalling helpers ---------------------------------------------------------------
