@@ -210,7 +210,8 @@ def main():
                     help="local-optimisation rounds in the timed steps (default 0: the single-pass method)")
     ap.add_argument("--local-opt-steps", type=int, default=50,
                     help="steps of each extra measurement on the same frame: 2 local-optimisation rounds, "
-                         "the adaptive trial count at confidence 0.99, and Alg. 1's line model (0 skips them)")
+                         "the adaptive trial count at confidence 0.99, Alg. 1's line model, and the clustering "
+                         "stage with the whole pipeline on a traffic scene (0 skips them)")
     args = ap.parse_args()
     if args.impl == "reference":
         return reference_arm(args)
@@ -424,6 +425,51 @@ def main():
                       "median_velocity_error_cosine_model_m_s": verr(outs),
                       "inliers": int(pl_outs["inlier_count"].sum().item()), "steps": args.local_opt_steps}
 
+    # ---- the clustering stage (Fig. 1) on an unclustered traffic scene: DBSCAN,
+    # then the whole pipeline cluster -> gather -> estimate (H = 1024, 2D)
+    clustering = None
+    if args.local_opt_steps > 0 and args.refine_iterations == 0 and dim == 2:
+        sc = synth.SCENES["scene"]
+        scene = synth.make_scene(sc)
+        n_s = scene.n_points
+        d_feat = torch.from_numpy(scene.features().reshape(-1).copy()).to(dev)
+        s_az, s_dop = torch.from_numpy(scene.azimuth).to(dev), torch.from_numpy(scene.doppler).to(dev)
+        c_lab = torch.empty(n_s, dtype=torch.int32, device=dev)
+        c_perm = torch.empty(n_s, dtype=torch.int32, device=dev)
+        c_off = torch.empty(n_s + 1, dtype=torch.int32, device=dev)
+        g_az = torch.empty(n_s, dtype=torch.float32, device=dev)
+        g_dop = torch.empty(n_s, dtype=torch.float32, device=dev)
+        ncl = ctypes.c_int32(0)
+        cl_ms, pipe_ms = [], []
+        for i in range(3 + args.local_opt_steps):
+            flush.fill_(8)
+            c0 = torch.cuda.Event(enable_timing=True)
+            c1 = torch.cuda.Event(enable_timing=True)
+            c2 = torch.cuda.Event(enable_timing=True)
+            c0.record(stream)
+            ctx.check(rvh.rvh_cluster(ctx.handle, d_feat, n_s, 2, sc.eps, sc.min_pts, c_lab, c_perm, c_off, n_s, ncl,
+                                      sptr), "rvh_cluster")
+            c1.record(stream)
+            m_s = int(c_off[ncl.value].item())
+            ctx.check(rvh.rvh_gather(ctx.handle, c_perm, m_s, s_az, g_az, s_dop, g_dop, stream=sptr), "rvh_gather")
+            cl_frame = rvh.make_frame(g_az[:m_s], g_dop[:m_s], c_off[:ncl.value + 1])
+            cl_outs = rvh.alloc_outputs(ncl.value, m_s, dev)
+            ctx.check(rvh.rvh_estimate(ctx.handle, cl_frame, rvh.make_params(2, w.num_hypotheses, w.tau, w.seed),
+                                       rvh.make_result(cl_outs), sptr), "rvh_estimate(scene)")
+            c2.record(stream)
+            c2.synchronize()
+            if i >= 3:
+                cl_ms.append(c0.elapsed_time(c1))
+                pipe_ms.append(c0.elapsed_time(c2))
+        ck, pk = float(np.mean(cl_ms)), float(np.mean(pipe_ms))
+        clustering = {"workload": f"scene: {sc.n_objects} objects, {n_s} points (x, y features), eps {sc.eps} m, "
+                                  f"min_pts {sc.min_pts}; estimate H={w.num_hypotheses}, tau={w.tau}",
+                      "n_clusters": int(ncl.value), "clustered_points": m_s,
+                      "dbscan_ms": ck, "dbscan_points_per_s": n_s / (ck * 1e-3),
+                      "pipeline_ms": pk, "pipeline_clusters_per_s": ncl.value / (pk * 1e-3),
+                      "note": "CUDA events on the stream; rvh_cluster reads its cluster count back (one sync)",
+                      "steps": args.local_opt_steps}
+
     # ---- end to end through the C ABI with pinned host buffers (copies inside the timed region)
     h_az = torch.from_numpy(f.azimuth).pin_memory()
     h_el = None if f.elevation is None else torch.from_numpy(f.elevation).pin_memory()
@@ -500,6 +546,7 @@ def main():
             "local_opt": local_opt,
             "adaptive": adaptive,
             "paper_line": paper_line,
+            "clustering": clustering,
             "e2e": e2e,
             "clocks": clocks,
             "gpu_launches": launches,

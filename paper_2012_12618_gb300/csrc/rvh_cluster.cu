@@ -38,6 +38,7 @@ struct ClusterArgs {
   int64_t n;
   int dim, gdim;      // components, gridded components (min(dim, 3))
   double eps2;        // eps^2 (FP64)
+  float in32, out32;  // FP32 prefilter: d2_32 <= in32 certainly a neighbour, > out32 certainly not
   double inv_cell;    // 1 / cell size
   int min_pts;
   uint32_t hmask;     // hash buckets - 1 (power of two)
@@ -80,6 +81,23 @@ __global__ void k_grid(ClusterArgs a) {
   a.next[i] = atomicExch(&a.head[cell_hash(x, y, z) & a.hmask], (int)i);
 }
 
+// The neighbour test.  An FP32 squared distance (differences and squares of
+// FP32 values, accumulated with fmaf) is within 8u relative of the exact one
+// for up to four components, and the FP64 one within 6 x 2^-53; outside
+// eps^2 (1 -+ 16u) the FP32 value decides alike, inside that band (and for
+// tiny values, where underflow voids the relative bound) the FP64 sum in
+// component order decides.
+__device__ __forceinline__ bool is_neighbour(const ClusterArgs& a, const float* fp, const float* fq) {
+  float s = 0.0f;
+  for (int k = 0; k < a.dim; ++k) {
+    const float d = fp[k] - fq[k];
+    s = fmaf(d, d, s);
+  }
+  if (s > a.out32) return false;  // also +inf
+  if (s <= a.in32 && s >= 0x1p-100f) return true;
+  return feat_dist2(fp, fq, a.dim) <= a.eps2;  // NaN: false
+}
+
 // Visits every point q within eps of point p (q = p included) until the
 // visitor returns false.  Cells of the 3^gdim neighbourhood; bucket lists are
 // filtered by exact cell coordinates (hash collisions) and by the distance.
@@ -96,7 +114,7 @@ __device__ __forceinline__ void for_neighbours(const ClusterArgs& a, int64_t p, 
         for (int q = a.head[cell_hash(x, y, z) & a.hmask]; q >= 0 && steps <= a.n; q = a.next[q], ++steps) {
           const int4 cq = a.cellc[q];
           if (cq.x != x || cq.y != y || cq.z != z) continue;
-          if (feat_dist2(fp, a.feat + (int64_t)q * a.dim, a.dim) <= a.eps2)
+          if (is_neighbour(a, fp, a.feat + (int64_t)q * a.dim))
             if (!visit(q)) return;
         }
       }
@@ -114,36 +132,49 @@ __global__ void k_core(ClusterArgs a) {
 // Root of x: parents always point to smaller indices, so the walk ends.
 // Inside the union kernel other SMs relink roots concurrently: the loads go
 // to L2 (ld.global.cg), where every compare-and-swap lands, never to a stale
-// L1 line.
-__device__ __forceinline__ int uf_find(const int* parent, int x) {
+// L1 line.  Path halving on the way (each visited node is pointed at its
+// grandparent, which is still one of its ancestors; a node that is not a
+// root never becomes one again, and links only ever touch roots) keeps the
+// trees shallow.
+__device__ __forceinline__ int uf_find(int* parent, int x) {
   int p = __ldcg(&parent[x]);
   while (p != x) {
-    x = p;
+    const int gp = __ldcg(&parent[p]);
+    if (gp != p) __stcg(&parent[x], gp);
+    x = gp;
     p = __ldcg(&parent[x]);
   }
   return x;
 }
 
+// Joins every core point with its lower-index core neighbours.  rp is p's
+// root as last seen: always an ancestor of p (roots only ever gain parents),
+// so a neighbour whose parent is rp, or whose root is rp, is already in p's
+// set.  Otherwise the larger of the two roots is linked under the smaller; a
+// failed compare-and-swap (another thread linked it first) refreshes both.
 __global__ void k_union(ClusterArgs a) {
   const int64_t p = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (p >= a.n || !a.core[p]) return;
+  int rp = uf_find(a.parent, (int)p);
   for_neighbours(a, p, [&](int q) {
     if (q >= p || !a.core[q]) return true;
-    for (int tries = 0;; ++tries) {
+    int rq = __ldcg(&a.parent[q]);
+    if (rq == rp) return true;
+    rq = uf_find(a.parent, rq);
+    for (int tries = 0; rq != rp; ++tries) {
       if (tries >= kUnionRetries) {
         atomicExch(a.err, 1);
         return false;
       }
-      int ra = uf_find(a.parent, (int)p), rb = uf_find(a.parent, q);
-      if (ra == rb) return true;
-      if (ra < rb) {
-        const int t = ra;
-        ra = rb;
-        rb = t;
+      const int hi = rq > rp ? rq : rp, lo = rq > rp ? rp : rq;
+      if (atomicCAS(&a.parent[hi], hi, lo) == hi) {
+        rp = lo;
+        break;
       }
-      // link the larger root under the smaller; retry if ra stopped being a root
-      if (atomicCAS(&a.parent[ra], ra, rb) == ra) return true;
+      rp = uf_find(a.parent, rp);
+      rq = uf_find(a.parent, rq);
     }
+    return true;
   });
 }
 
@@ -317,6 +348,19 @@ cudaError_t launch_cluster(const float* feat, int64_t n, int dim, double eps, in
   a.dim = dim;
   a.gdim = dim < 3 ? dim : 3;
   a.eps2 = eps * eps;
+  {
+    // FP32 certainty thresholds, rounded outward; 0 disables the in-test
+    const double lo = a.eps2 * (1.0 - 16.0 * 0x1p-24), hi = a.eps2 * (1.0 + 16.0 * 0x1p-24);
+    float l = (float)lo, h = (float)hi;
+    if ((double)l > lo) l = nextafterf(l, 0.0f);
+    if ((double)h < hi) h = nextafterf(h, __builtin_huge_valf());
+    a.in32 = l;
+    a.out32 = h;
+    if (!(hi < 1e37)) {  // radii beyond FP32 range: every test in FP64
+      a.in32 = -1.0f;
+      a.out32 = __builtin_huge_valf();
+    }
+  }
   // cells a little larger than eps: pairs within eps stay in adjacent cells
   // whatever the rounding of the cell coordinates
   a.inv_cell = eps > 0.0 ? 1.0 / (eps * (1.0 + 0x1p-10)) : 1.0;
