@@ -19,6 +19,7 @@
 
 #include "rvh.h"
 #include "rvh_kernels.h"
+#include "rvh_cluster.h"
 #include "rvh_runtime.h"
 
 namespace {

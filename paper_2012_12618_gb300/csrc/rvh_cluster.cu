@@ -24,7 +24,7 @@
 #include <cstdint>
 #include <cuda_runtime.h>
 
-#include "rvh_kernels.h"
+#include "rvh_cluster.h"
 
 namespace rvh {
 
