@@ -13,12 +13,20 @@
 // noise.  Every decision is an FP64 comparison made in the same operation
 // order everywhere, so the labels are exactly defined.
 //
-// GPU mapping: a hashed grid of cells slightly larger than eps over the first
-// min(dim, 3) components (linked lists built with atomic exchange), one
-// thread per point for neighbour counts, lock-free union-find over core-core
-// neighbour pairs that always links the larger root under the smaller (so a
-// component's root is its smallest core index), a device-wide scan for the
-// numbering, and a bitonic sort of (cluster, index) keys for the CSR order.
+// GPU mapping: the first min(dim, 3) components are cut into cells slightly
+// larger than eps, and cells are hashed to buckets by their coordinates
+// modulo a power-of-two table (x, y, z bits side by side), so the 3^g cells
+// around any cell land in 3^g distinct buckets and x - 1, x, x + 1 in
+// consecutive ones.  A counting sort lays the points out bucket by bucket
+// (features as float4 next to their original index): a point's candidates
+// are then a few contiguous spans, and the threads of a warp, which hold
+// neighbouring sorted points, scan the same spans.  One thread per sorted
+// point counts neighbours, then a lock-free union-find over core-core
+// neighbour pairs, on sorted positions so that a warp's parent loads
+// coincide, links the larger root under the smaller; an atomic minimum per
+// component gives its smallest core index, a device-wide scan numbers the
+// clusters, and a bitonic sort of (cluster,
+// index) keys, its short strides in shared memory, gives the CSR order.
 // Every loop is bounded by the input size; the union retry loop has an
 // explicit cap that raises an error flag instead of spinning.
 #include <cstdint>
@@ -32,37 +40,30 @@ namespace {
 
 constexpr int kCT = 256;                       // threads per block of the clustering kernels
 constexpr int kUnionRetries = 1 << 20;         // cap on one union's compare-and-swap retries
+constexpr int kSumsPerThread = 64;             // block sums per thread of the one-block scan
+constexpr int kBT = 1024;                      // threads of the shared-memory bitonic kernels
+constexpr int kBE = 2 * kBT;                   // keys per block of those kernels
 
 struct ClusterArgs {
-  const float* feat;  // [n * dim]
+  const float* feat;   // [n * dim] caller's features
   int64_t n;
-  int dim, gdim;      // components, gridded components (min(dim, 3))
-  double eps2;        // eps^2 (FP64)
-  float in32, out32;  // FP32 prefilter: d2_32 <= in32 certainly a neighbour, > out32 certainly not
-  double inv_cell;    // 1 / cell size
+  double eps2;         // eps^2 (FP64)
+  float in32, out32;   // FP32 prefilter: d2_32 <= in32 certainly a neighbour, > out32 certainly not
+  double inv_cell;     // 1 / cell size
   int min_pts;
-  uint32_t hmask;     // hash buckets - 1 (power of two)
-  int* head;          // [buckets] first point of each bucket, -1 empty
-  int* next;          // [n] next point in the bucket
-  int4* cellc;        // [n] cell coordinates (x, y, z, 0)
-  uint8_t* core;      // [n]
-  int* parent;        // [n] union-find
-  int* err;           // error flag
+  uint32_t xmask, ymask, zmask;  // table bits per gridded component (each >= 2 bits)
+  int ysh, zsh;                  // bucket = x | y << ysh | z << zsh
+  int* count;          // [buckets] points per bucket
+  int* start;          // [buckets + 1] first sorted position of each bucket
+  int2* bslot;         // [n] (bucket, slot within the bucket) of each point
+  float4* sfeat;       // [n] features in sorted order, zero-padded to four
+  int* sidx;           // [n] original index of each sorted position
+  uint8_t* score;      // [n] core flag by sorted position
+  uint8_t* core;       // [n] core flag by original index
+  int* parent;         // [n] union-find over sorted positions
+  int* cmin;           // [n] by root position: the component's smallest original core index
+  int* err;            // error flag
 };
-
-__device__ __forceinline__ uint32_t cell_hash(int x, int y, int z) {
-  return ((uint32_t)x * 73856093u) ^ ((uint32_t)y * 19349663u) ^ ((uint32_t)z * 83492791u);
-}
-
-// Squared Euclidean distance accumulated in FP64 over the components in order.
-__device__ __forceinline__ double feat_dist2(const float* a, const float* b, int dim) {
-  double s = 0.0;
-  for (int k = 0; k < dim; ++k) {
-    const double d = (double)a[k] - (double)b[k];
-    s = s + d * d;
-  }
-  return s;
-}
 
 __device__ __forceinline__ int cell_coord(float v, double inv_cell) {
   const double c = floor((double)v * inv_cell);
@@ -70,66 +71,223 @@ __device__ __forceinline__ int cell_coord(float v, double inv_cell) {
   return c >= 1073741823.0 ? 1073741823 : (c <= -1073741823.0 ? -1073741823 : (c == c ? (int)c : 0));
 }
 
-__global__ void k_grid(ClusterArgs a) {
-  const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-  if (i >= a.n) return;
-  const float* f = a.feat + i * a.dim;
-  const int x = cell_coord(f[0], a.inv_cell);
-  const int y = a.gdim > 1 ? cell_coord(f[1], a.inv_cell) : 0;
-  const int z = a.gdim > 2 ? cell_coord(f[2], a.inv_cell) : 0;
-  a.cellc[i] = make_int4(x, y, z, 0);
-  a.next[i] = atomicExch(&a.head[cell_hash(x, y, z) & a.hmask], (int)i);
+__device__ __forceinline__ uint32_t row_bucket(const ClusterArgs& a, int y, int z) {
+  return (((uint32_t)y & a.ymask) << a.ysh) | (((uint32_t)z & a.zmask) << a.zsh);
+}
+
+template <int DIM>
+__device__ __forceinline__ float4 load_feat(const float* f) {
+  return make_float4(f[0], DIM > 1 ? f[1] : 0.0f, DIM > 2 ? f[2] : 0.0f, DIM > 3 ? f[3] : 0.0f);
+}
+
+template <int DIM>
+__device__ __forceinline__ float comp(const float4& v, int k) {
+  return k == 0 ? v.x : (k == 1 ? v.y : (k == 2 ? v.z : v.w));
 }
 
 // The neighbour test.  An FP32 squared distance (differences and squares of
 // FP32 values, accumulated with fmaf) is within 8u relative of the exact one
 // for up to four components, and the FP64 one within 6 x 2^-53; outside
 // eps^2 (1 -+ 16u) the FP32 value decides alike, inside that band (and for
-// tiny values, where underflow voids the relative bound) the FP64 sum in
-// component order decides.
-__device__ __forceinline__ bool is_neighbour(const ClusterArgs& a, const float* fp, const float* fq) {
+// tiny values, where underflow voids the relative bound) the FP64 sum of
+// squared differences, accumulated over the components in order, decides.
+template <int DIM>
+__device__ __forceinline__ bool is_neighbour(const ClusterArgs& a, const float4& fp, const float4& fq) {
   float s = 0.0f;
-  for (int k = 0; k < a.dim; ++k) {
-    const float d = fp[k] - fq[k];
+#pragma unroll
+  for (int k = 0; k < DIM; ++k) {
+    const float d = comp<DIM>(fp, k) - comp<DIM>(fq, k);
     s = fmaf(d, d, s);
   }
   if (s > a.out32) return false;  // also +inf
   if (s <= a.in32 && s >= 0x1p-100f) return true;
-  return feat_dist2(fp, fq, a.dim) <= a.eps2;  // NaN: false
+  double s64 = 0.0;
+#pragma unroll
+  for (int k = 0; k < DIM; ++k) {
+    const double d = (double)comp<DIM>(fp, k) - (double)comp<DIM>(fq, k);
+    s64 = s64 + d * d;
+  }
+  return s64 <= a.eps2;  // NaN: false
 }
 
-// Visits every point q within eps of point p (q = p included) until the
-// visitor returns false.  Cells of the 3^gdim neighbourhood; bucket lists are
-// filtered by exact cell coordinates (hash collisions) and by the distance.
-template <typename Visit>
-__device__ __forceinline__ void for_neighbours(const ClusterArgs& a, int64_t p, Visit visit) {
-  const int4 c = a.cellc[p];
-  const float* fp = a.feat + p * a.dim;
-  const int ry = a.gdim > 1 ? 1 : 0, rz = a.gdim > 2 ? 1 : 0;
-  for (int dx = -1; dx <= 1; ++dx)
-    for (int dy = -ry; dy <= ry; ++dy)
-      for (int dz = -rz; dz <= rz; ++dz) {
-        const int x = c.x + dx, y = c.y + dy, z = c.z + dz;
-        int64_t steps = 0;
-        for (int q = a.head[cell_hash(x, y, z) & a.hmask]; q >= 0 && steps <= a.n; q = a.next[q], ++steps) {
-          const int4 cq = a.cellc[q];
-          if (cq.x != x || cq.y != y || cq.z != z) continue;
-          if (is_neighbour(a, fp, a.feat + (int64_t)q * a.dim))
-            if (!visit(q)) return;
+struct Cell {
+  int x, y, z;
+};
+
+template <int DIM>
+__device__ __forceinline__ Cell cell_of(const ClusterArgs& a, const float4& f) {
+  constexpr int G = DIM < 3 ? DIM : 3;
+  return Cell{cell_coord(f.x, a.inv_cell), G > 1 ? cell_coord(f.y, a.inv_cell) : 0,
+              G > 2 ? cell_coord(f.z, a.inv_cell) : 0};
+}
+
+__device__ __forceinline__ uint32_t bucket_of(const ClusterArgs& a, const Cell& c) {
+  return row_bucket(a, c.y, c.z) | ((uint32_t)c.x & a.xmask);
+}
+
+// Calls span(begin, end) for the sorted-position ranges, cut at limit, that
+// hold the points of the 3^g cells around cell c, until span returns false.
+// The ranges depend only on c's bucket, and each point lies in at most one:
+// the cells' buckets are distinct.  Returns false when span stopped the walk.
+template <int DIM, typename Span>
+__device__ __forceinline__ bool for_spans(const ClusterArgs& a, const Cell& c, int limit, Span span) {
+  constexpr int G = DIM < 3 ? DIM : 3;
+  constexpr int RY = G > 1 ? 1 : 0, RZ = G > 2 ? 1 : 0;
+  for (int dz = -RZ; dz <= RZ; ++dz)
+    for (int dy = -RY; dy <= RY; ++dy) {
+      const uint32_t row = row_bucket(a, c.y + dy, c.z + dz);
+      const uint32_t bx = (uint32_t)(c.x - 1) & a.xmask;
+      if (bx + 2 <= a.xmask) {  // x - 1 .. x + 1 without wrap: one range of three buckets
+        if (!span(a.start[row + bx], min(a.start[row + bx + 3], limit))) return false;
+      } else {
+        for (int dx = -1; dx <= 1; ++dx) {
+          const uint32_t b = row + ((uint32_t)(c.x + dx) & a.xmask);
+          if (!span(a.start[b], min(a.start[b + 1], limit))) return false;
         }
       }
+    }
+  return true;
 }
 
+// One thread walks its candidates kChunk at a time: chunk(t0, end) handles
+// positions t0 .. min(t0 + kChunk, end) - 1, issuing their loads together.
+constexpr int kChunk = 8;
+template <int DIM, typename Chunk>
+__device__ __forceinline__ bool for_chunks(const ClusterArgs& a, const Cell& c, int limit, Chunk chunk) {
+  return for_spans<DIM>(a, c, limit, [&](int b, int e) {
+    for (int t0 = b; t0 < e; t0 += kChunk)
+      if (!chunk(t0, e)) return false;
+    return true;
+  });
+}
+
+constexpr unsigned kFull = 0xffffffffu;
+constexpr int kMaxGroups = 4;  // bucket groups per warp that still share walks
+
+// The lanes of a warp in one bucket share their candidates.  Such a group
+// walks them 32 at a time: lane l fetches the features of candidate base + l
+// and tag = fetch(t) (a parent or an index), then every lane sees each
+// candidate of the tile through shuffles, in order, as use(t, features, tag).
+// more() is a warp vote that can end the walk after a tile.  All arguments
+// are warp-uniform; every lane runs the whole walk.
+template <int DIM, typename Fetch, typename Use, typename More>
+__device__ __forceinline__ void warp_walk(const ClusterArgs& a, const Cell& c, int limit, Fetch fetch, Use use,
+                                          More more) {
+  const int lane = threadIdx.x & 31;
+  for_spans<DIM>(a, c, limit, [&](int b, int e) {
+    for (int base = b; base < e; base += 32) {
+      const int cnt = min(32, e - base);
+      float4 fl = make_float4(0.0f, 0.0f, 0.0f, 0.0f);
+      int tag = 0;
+      if (lane < cnt) {
+        fl = a.sfeat[base + lane];
+        tag = fetch(base + lane);
+      }
+      for (int j = 0; j < cnt; ++j) {
+        float4 fq = make_float4(0.0f, 0.0f, 0.0f, 0.0f);
+        fq.x = __shfl_sync(kFull, fl.x, j);
+        if (DIM > 1) fq.y = __shfl_sync(kFull, fl.y, j);
+        if (DIM > 2) fq.z = __shfl_sync(kFull, fl.z, j);
+        if (DIM > 3) fq.w = __shfl_sync(kFull, fl.w, j);
+        use(base + j, fq, __shfl_sync(kFull, tag, j));
+      }
+      if (!more()) return false;
+    }
+    return true;
+  });
+}
+
+// Splits the warp into groups of lanes with equal buckets and runs
+// group(cell, mine) once per group (mine: this lane belongs to it), cell
+// being the group's cell.  A warp with more than kMaxGroups groups runs
+// nothing and gets false: its lanes walk alone.
+template <typename Group>
+__device__ __forceinline__ bool for_groups(const ClusterArgs& a, const Cell& c, Group group) {
+  const int lane = threadIdx.x & 31;
+  const unsigned peers = __match_any_sync(kFull, bucket_of(a, c));
+  const unsigned leaders = __ballot_sync(kFull, (peers & ((1u << lane) - 1u)) == 0u);
+  if (__popc(leaders) > kMaxGroups) return false;
+  for (unsigned l = leaders; l; l &= l - 1u) {
+    const int lead = __ffs(l) - 1;
+    const unsigned members = __shfl_sync(kFull, peers, lead);
+    const Cell cg{__shfl_sync(kFull, c.x, lead), __shfl_sync(kFull, c.y, lead), __shfl_sync(kFull, c.z, lead)};
+    group(cg, members, ((members >> lane) & 1u) != 0u);
+  }
+  return true;
+}
+
+template <int DIM>
+__device__ __forceinline__ uint32_t point_bucket(const ClusterArgs& a, const float4& f) {
+  return bucket_of(a, cell_of<DIM>(a, f));
+}
+
+// bucket and slot of every point (the slot order within a bucket is
+// arbitrary; no result depends on it)
+template <int DIM>
+__global__ void k_grid(ClusterArgs a) {
+  const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= a.n) return;
+  const uint32_t b = point_bucket<DIM>(a, load_feat<DIM>(a.feat + i * DIM));
+  a.bslot[i] = make_int2((int)b, atomicAdd(&a.count[b], 1));
+}
+
+// start[b] = exclusive scan of the counts; start[buckets] = n
+__global__ void k_starts(ClusterArgs a, const int* excl, const int* block_sum, int64_t buckets) {
+  const int64_t b = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (b < buckets) a.start[b] = excl[b] + block_sum[b / kCT];
+  if (b == buckets) a.start[b] = (int)a.n;
+}
+
+template <int DIM>
+__global__ void k_scatter(ClusterArgs a) {
+  const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= a.n) return;
+  const int2 bs = a.bslot[i];
+  const int pos = a.start[bs.x] + bs.y;
+  a.sfeat[pos] = load_feat<DIM>(a.feat + i * DIM);
+  a.sidx[pos] = (int)i;
+}
+
+// Neighbour counts (stopping at min_pts), one thread per sorted position.
+// Lanes past the end take the warp's first point, so they join its group.
+template <int DIM>
 __global__ void k_core(ClusterArgs a) {
-  const int64_t p = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-  if (p >= a.n) return;
+  const int64_t s = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  const int64_t s0 = s - (threadIdx.x & 31);
+  if (s0 >= a.n) return;  // the whole warp
+  const bool live = s < a.n;
+  const float4 fp = a.sfeat[live ? s : s0];
+  const Cell c = cell_of<DIM>(a, fp);
   int count = 0;
-  for_neighbours(a, p, [&](int) { return ++count < a.min_pts; });
-  a.core[p] = count >= a.min_pts;
-  a.parent[p] = (int)p;
+  const bool shared = for_groups(a, c, [&](const Cell& cg, unsigned, bool mine) {
+    const bool want = mine && live;
+    warp_walk<DIM>(
+        a, cg, 0x7fffffff, [](int) { return 0; },
+        [&](int, const float4& fq, int) {
+          if (want && count < a.min_pts && is_neighbour<DIM>(a, fp, fq)) ++count;
+        },
+        [&] { return __any_sync(kFull, want && count < a.min_pts); });
+  });
+  if (!live) return;
+  if (!shared)
+    for_chunks<DIM>(a, c, 0x7fffffff, [&](int t0, int e) {
+      float4 fq[kChunk];
+#pragma unroll
+      for (int u = 0; u < kChunk; ++u) fq[u] = a.sfeat[t0 + u < e ? t0 + u : t0];
+#pragma unroll
+      for (int u = 0; u < kChunk; ++u)
+        if (t0 + u < e && is_neighbour<DIM>(a, fp, fq[u])) ++count;
+      return count < a.min_pts;
+    });
+  const bool core = count >= a.min_pts;
+  const int p = a.sidx[s];
+  a.score[s] = core;
+  a.core[p] = core;
+  a.parent[s] = (int)s;
+  a.cmin[s] = 0x7fffffff;
 }
 
-// Root of x: parents always point to smaller indices, so the walk ends.
+// Root of x: parents always point to smaller positions, so the walk ends.
 // Inside the union kernel other SMs relink roots concurrently: the loads go
 // to L2 (ld.global.cg), where every compare-and-swap lands, never to a stale
 // L1 line.  Path halving on the way (each visited node is pointed at its
@@ -147,59 +305,191 @@ __device__ __forceinline__ int uf_find(int* parent, int x) {
   return x;
 }
 
-// Joins every core point with its lower-index core neighbours.  rp is p's
-// root as last seen: always an ancestor of p (roots only ever gain parents),
-// so a neighbour whose parent is rp, or whose root is rp, is already in p's
-// set.  Otherwise the larger of the two roots is linked under the smaller; a
-// failed compare-and-swap (another thread linked it first) refreshes both.
-__global__ void k_union(ClusterArgs a) {
-  const int64_t p = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-  if (p >= a.n || !a.core[p]) return;
-  int rp = uf_find(a.parent, (int)p);
-  for_neighbours(a, p, [&](int q) {
-    if (q >= p || !a.core[q]) return true;
-    int rq = __ldcg(&a.parent[q]);
-    if (rq == rp) return true;
-    rq = uf_find(a.parent, rq);
-    for (int tries = 0; rq != rp; ++tries) {
-      if (tries >= kUnionRetries) {
-        atomicExch(a.err, 1);
-        return false;
-      }
-      const int hi = rq > rp ? rq : rp, lo = rq > rp ? rp : rq;
-      if (atomicCAS(&a.parent[hi], hi, lo) == hi) {
-        rp = lo;
-        break;
-      }
-      rp = uf_find(a.parent, rp);
-      rq = uf_find(a.parent, rq);
+// Joins the sets of a core point (root as last seen: rp) and of a core
+// neighbour whose ancestor pt was read at some moment.  rp is always an
+// ancestor of the point (roots only ever gain parents), so pt == rp, or a
+// common root, means the two already share a set.  Otherwise the larger
+// root is linked under the smaller; a failed compare-and-swap (another
+// thread linked it first) refreshes both.  False when the retry cap ran out.
+__device__ __forceinline__ bool uf_union(const ClusterArgs& a, int& rp, int pt) {
+  if (pt == rp) return true;
+  int rq = uf_find(a.parent, pt);
+  for (int tries = 0; rq != rp; ++tries) {
+    if (tries >= kUnionRetries) {
+      atomicExch(a.err, 1);
+      return false;
     }
+    const int hi = rq > rp ? rq : rp, lo = rq > rp ? rp : rq;
+    if (atomicCAS(&a.parent[hi], hi, lo) == hi) {
+      rp = lo;
+      break;
+    }
+    rp = uf_find(a.parent, rp);
+    rq = uf_find(a.parent, rq);
+  }
+  return true;
+}
+
+// Joins every core point with its core neighbours at lower sorted positions
+// (each core-core pair once).  A shared walk fetches, per tile, an ancestor
+// of each core candidate two links up (after k_compress mostly its root).
+// Each lane keeps its root rp and an alias, the last ancestor it merged (a
+// value that is in its set for good); candidates whose ancestor is either
+// already share the set.  A vote skips those when every member lane holds
+// the same pair, and only the others are shuffled through the lanes.  A
+// group's walk ends at its last lane's position.
+template <int DIM>
+__global__ void k_union(ClusterArgs a) {
+  const int64_t s = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  const int lane = threadIdx.x & 31;
+  const int64_t s0 = s - lane;
+  if (s0 >= a.n) return;
+  const bool live = s < a.n;
+  const bool act = live && a.score[s];
+  if (!__any_sync(kFull, act)) return;
+  const float4 fp = a.sfeat[live ? s : s0];
+  const Cell c = cell_of<DIM>(a, fp);
+  int rp = act ? uf_find(a.parent, (int)s) : 0;
+  int alias = rp;
+  bool ok = true;
+  const bool shared = for_groups(a, c, [&](const Cell& cg, unsigned members, bool mine) {
+    const unsigned wanting = __ballot_sync(kFull, mine && act);
+    if (!wanting) return;
+    const int64_t last = s0 + 31 - __clz(members);
+    const int limit = (int)(last < a.n ? last : a.n - 1);  // candidates below the group's last position
+    for_spans<DIM>(a, cg, limit, [&](int b, int e) {
+      for (int base = b; base < e; base += 32) {
+        const int cnt = min(32, e - base);
+        int tag = -1;
+        if (lane < cnt && a.score[base + lane]) tag = __ldcg(&a.parent[__ldcg(&a.parent[base + lane])]);
+        const bool want = ((wanting >> lane) & 1u) && ok;
+        const int first = __ffs(wanting) - 1;
+        const int common = __shfl_sync(kFull, rp, first), common_alias = __shfl_sync(kFull, alias, first);
+        const bool same = __all_sync(kFull, !want || (rp == common && alias == common_alias));
+        unsigned todo = __ballot_sync(kFull, tag >= 0 && (!same || (tag != common && tag != common_alias)));
+        if (!todo) continue;
+        float4 fl = make_float4(0.0f, 0.0f, 0.0f, 0.0f);
+        if (lane < cnt) fl = a.sfeat[base + lane];
+        for (; todo; todo &= todo - 1u) {
+          const int j = __ffs(todo) - 1;
+          float4 fq = make_float4(0.0f, 0.0f, 0.0f, 0.0f);
+          fq.x = __shfl_sync(kFull, fl.x, j);
+          if (DIM > 1) fq.y = __shfl_sync(kFull, fl.y, j);
+          if (DIM > 2) fq.z = __shfl_sync(kFull, fl.z, j);
+          if (DIM > 3) fq.w = __shfl_sync(kFull, fl.w, j);
+          const int pt = __shfl_sync(kFull, tag, j);
+          if (want && ok && base + j < s && pt != rp && pt != alias && is_neighbour<DIM>(a, fp, fq)) {
+            ok = uf_union(a, rp, pt);
+            alias = pt;
+          }
+        }
+      }
+      return true;
+    });
+  });
+  if (!act || shared) return;
+  for_chunks<DIM>(a, c, (int)s, [&](int t0, int e) {
+    int tag[kChunk];
+#pragma unroll
+    for (int u = 0; u < kChunk; ++u) tag[u] = t0 + u < e && a.score[t0 + u] ? __ldcg(&a.parent[t0 + u]) : -1;
+#pragma unroll
+    for (int u = 0; u < kChunk; ++u)
+      if (tag[u] >= 0 && tag[u] != rp && tag[u] != alias && is_neighbour<DIM>(a, fp, a.sfeat[t0 + u])) {
+        if (!uf_union(a, rp, tag[u])) return false;
+        alias = tag[u];
+      }
     return true;
   });
+}
+
+// A cheap first linking pass (the sampling idea of Afforest, Sutton et al.,
+// IPDPS'18): every core point joins the core neighbours among the kNear
+// positions just before it, mostly points of its own cell.  After k_compress
+// most points of a dense cell share one root, and the full walk of k_union
+// then meets pairs whose parent already is the root.  Any subset of the
+// core-core edges may be linked early: the components are the same.
+constexpr int kNear = 4;
+template <int DIM>
+__global__ void k_union_near(ClusterArgs a) {
+  const int64_t s = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (s >= a.n || !a.score[s]) return;
+  const float4 fp = a.sfeat[s];
+  int rp = uf_find(a.parent, (int)s);
+  const int64_t lo = s > kNear ? s - kNear : 0;
+  for (int64_t t = s - 1; t >= lo; --t)
+    if (a.score[t] && is_neighbour<DIM>(a, fp, a.sfeat[t]))
+      if (!uf_union(a, rp, __ldcg(&a.parent[t]))) return;
+}
+
+// points every core point's parent at its root (no links meanwhile)
+__global__ void k_compress(ClusterArgs a) {
+  const int64_t s = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (s >= a.n || !a.score[s]) return;
+  a.parent[s] = uf_find(a.parent, (int)s);
+}
+
+// the smallest original core index of each component, at its root
+__global__ void k_cmin(ClusterArgs a) {
+  const int64_t s = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (s >= a.n || !a.score[s]) return;
+  atomicMin(&a.cmin[uf_find(a.parent, (int)s)], a.sidx[s]);
 }
 
 // Core points: root = the component's smallest core index; border points:
-// the root of their lowest-index core neighbour; noise: -1.
+// their lowest-index core neighbour (resolved to its root in k_label);
+// noise: -1.  Written by original index.
+template <int DIM>
 __global__ void k_roots(ClusterArgs a, int* root) {
-  const int64_t p = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-  if (p >= a.n) return;
-  if (a.core[p]) {
-    root[p] = uf_find(a.parent, (int)p);
-    return;
-  }
+  const int64_t s = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  const int64_t s0 = s - (threadIdx.x & 31);
+  if (s0 >= a.n) return;
+  const bool live = s < a.n;
+  const bool act = live && !a.score[s];
+  if (live && !act) root[a.sidx[s]] = a.cmin[uf_find(a.parent, (int)s)];
+  if (!__any_sync(kFull, act)) return;
+  const float4 fp = a.sfeat[live ? s : s0];
+  const Cell c = cell_of<DIM>(a, fp);
   int best = 0x7fffffff;
-  for_neighbours(a, p, [&](int q) {
-    if (a.core[q] && q < best) best = q;
-    return true;
+  const bool shared = for_groups(a, c, [&](const Cell& cg, unsigned, bool mine) {
+    const bool want = mine && act;
+    if (!__any_sync(kFull, want)) return;
+    warp_walk<DIM>(
+        a, cg, 0x7fffffff, [&](int t) { return a.score[t] ? a.sidx[t] : 0x7fffffff; },
+        [&](int, const float4& fq, int q) {
+          if (want && q < best && is_neighbour<DIM>(a, fp, fq)) best = q;
+        },
+        [] { return true; });
   });
-  root[p] = best == 0x7fffffff ? -1 : best;  // resolved to its root in k_label
+  if (!act) return;
+  if (!shared)
+    for_chunks<DIM>(a, c, 0x7fffffff, [&](int t0, int e) {
+      int q[kChunk];
+#pragma unroll
+      for (int u = 0; u < kChunk; ++u) q[u] = t0 + u < e && a.score[t0 + u] ? a.sidx[t0 + u] : 0x7fffffff;
+#pragma unroll
+      for (int u = 0; u < kChunk; ++u)
+        if (q[u] < best && is_neighbour<DIM>(a, fp, a.sfeat[t0 + u])) best = q[u];
+      return true;
+    });
+  root[a.sidx[s]] = best == 0x7fffffff ? -1 : best;
 }
 
-// ---- device-wide exclusive scan of root flags (cluster numbering) ----------------
-__global__ void k_scan_blocks(const ClusterArgs a, const int* root, int* flag_scan, int* block_sum) {
+// ---- device-wide exclusive scan (bucket starts; cluster numbering) -----------------
+struct CountValue {
+  const int* count;
+  __device__ int operator()(int64_t i) const { return count[i]; }
+};
+struct RootFlag {  // 1 for the root (smallest core index) of each component
+  const uint8_t* core;
+  const int* root;
+  __device__ int operator()(int64_t i) const { return core[i] && root[i] == (int)i ? 1 : 0; }
+};
+
+template <typename Value>
+__global__ void k_scan_blocks(Value value, int64_t len, int* excl, int* block_sum) {
   __shared__ int s[kCT];
   const int64_t i = (int64_t)blockIdx.x * kCT + threadIdx.x;
-  const int v = (i < a.n && a.core[i] && root[i] == (int)i) ? 1 : 0;
+  const int v = i < len ? value(i) : 0;
   s[threadIdx.x] = v;
   __syncthreads();
   for (int d = 1; d < kCT; d <<= 1) {
@@ -208,12 +498,11 @@ __global__ void k_scan_blocks(const ClusterArgs a, const int* root, int* flag_sc
     s[threadIdx.x] += t;
     __syncthreads();
   }
-  if (i < a.n) flag_scan[i] = s[threadIdx.x] - v;  // exclusive within the block
+  if (i < len) excl[i] = s[threadIdx.x] - v;  // exclusive within the block
   if (threadIdx.x == kCT - 1) block_sum[blockIdx.x] = s[kCT - 1];
 }
 
 // One block: exclusive scan of the block sums (nb <= kCT * kSumsPerThread).
-constexpr int kSumsPerThread = 64;
 __global__ void k_scan_sums(int* block_sum, int nb, int* total) {
   __shared__ int s[kCT];
   int loc[kSumsPerThread];
@@ -237,7 +526,7 @@ __global__ void k_scan_sums(int* block_sum, int nb, int* total) {
     if (idx < nb) block_sum[idx] = base;
     base += loc[k];
   }
-  if (threadIdx.x == kCT - 1) *total = s[kCT - 1];
+  if (threadIdx.x == kCT - 1 && total) *total = s[kCT - 1];
 }
 
 // labels and the sort keys (cluster << 32 | index; noise sorts last)
@@ -259,17 +548,58 @@ __global__ void k_label(ClusterArgs a, const int* root, const int* flag_scan, co
   keys[i] = ((unsigned long long)(uint32_t)(lab >= 0 ? lab : 0x7fffffff) << 32) | (unsigned long long)i;
 }
 
-__global__ void k_bitonic(unsigned long long* keys, int64_t n_pad, int64_t j, int64_t k) {
-  const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-  if (i >= n_pad) return;
-  const int64_t l = i ^ j;
-  if (l <= i) return;
-  const unsigned long long x = keys[i], y = keys[l];
-  const bool up = (i & k) == 0;
+// ---- bitonic sort of the keys (n_pad a power of two) -------------------------------
+// Step j of stage k compares i and i + j for every i with bit j clear, in
+// ascending order where bit k of i is clear; pair number t maps to that i.
+__device__ __forceinline__ int64_t pair_low(int64_t t, int64_t j) { return ((t & ~(j - 1)) << 1) | (t & (j - 1)); }
+
+__device__ __forceinline__ void cmp_swap(unsigned long long* v, int64_t i, int64_t l, bool up) {
+  const unsigned long long x = v[i], y = v[l];
   if ((x > y) == up) {
-    keys[i] = y;
-    keys[l] = x;
+    v[i] = y;
+    v[l] = x;
   }
+}
+
+// steps j = j0 .. 1 of stage k on one block's keys in shared memory
+__device__ __forceinline__ void smem_steps(unsigned long long* sk, int64_t base, int len, int j0, int64_t k) {
+  for (int j = j0; j > 0; j >>= 1) {
+    const int t = threadIdx.x;
+    if (2 * t < len) {
+      const int i = (int)pair_low(t, j);
+      cmp_swap(sk, i, i + j, ((base + i) & k) == 0);
+    }
+    __syncthreads();
+  }
+}
+
+// stages k = 2 .. min(kBE, n_pad), each block on its own kBE keys
+__global__ void __launch_bounds__(kBT) k_bitonic_block(unsigned long long* keys, int64_t n_pad) {
+  __shared__ unsigned long long sk[kBE];
+  const int64_t base = (int64_t)blockIdx.x * kBE;
+  const int len = n_pad < kBE ? (int)n_pad : kBE;
+  for (int e = threadIdx.x; e < len; e += kBT) sk[e] = keys[base + e];
+  __syncthreads();
+  for (int k = 2; k <= len; k <<= 1) smem_steps(sk, base, len, k >> 1, k);
+  for (int e = threadIdx.x; e < len; e += kBT) keys[base + e] = sk[e];
+}
+
+// steps j = kBE / 2 .. 1 of a stage k > kBE: pairs stay within a block's keys
+__global__ void __launch_bounds__(kBT) k_bitonic_tail(unsigned long long* keys, int64_t k) {
+  __shared__ unsigned long long sk[kBE];
+  const int64_t base = (int64_t)blockIdx.x * kBE;
+  for (int e = threadIdx.x; e < kBE; e += kBT) sk[e] = keys[base + e];
+  __syncthreads();
+  smem_steps(sk, base, kBE, kBE / 2, k);
+  for (int e = threadIdx.x; e < kBE; e += kBT) keys[base + e] = sk[e];
+}
+
+// one step j >= kBE of stage k, one thread per pair
+__global__ void k_bitonic_step(unsigned long long* keys, int64_t n_pad, int64_t j, int64_t k) {
+  const int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (2 * t >= n_pad) return;
+  const int64_t i = pair_low(t, j);
+  cmp_swap(keys, i, i + j, (i & k) == 0);
 }
 
 __global__ void k_csr(const unsigned long long* keys, int64_t n, int n_clustered, int* perm, int* offsets,
@@ -305,15 +635,41 @@ __global__ void k_gather(const int* perm, int64_t m, const float* s0, float* d0,
 
 inline unsigned grid_for(int64_t n) { return (unsigned)((n + kCT - 1) / kCT); }
 
+// buckets: a power of two >= n and >= 64 (two bits or more per gridded
+// component); n_pad: the bitonic length, a power of two >= n
+void table_sizes(int64_t n, int64_t* buckets, int64_t* n_pad) {
+  int64_t b = 64, p = 1;
+  while (b < n) b <<= 1;
+  while (p < n) p <<= 1;
+  *buckets = b;
+  *n_pad = p;
+}
+
+template <int DIM>
+void launch_grid_phase(ClusterArgs& a, int64_t buckets, int* excl, int* block_sum, int* root, cudaStream_t s) {
+  const unsigned nbb = grid_for(buckets);
+  k_grid<DIM><<<grid_for(a.n), kCT, 0, s>>>(a);
+  k_scan_blocks<<<nbb, kCT, 0, s>>>(CountValue{a.count}, buckets, excl, block_sum);
+  k_scan_sums<<<1, kCT, 0, s>>>(block_sum, (int)nbb, nullptr);
+  k_starts<<<grid_for(buckets + 1), kCT, 0, s>>>(a, excl, block_sum, buckets);
+  k_scatter<DIM><<<grid_for(a.n), kCT, 0, s>>>(a);
+  k_core<DIM><<<grid_for(a.n), kCT, 0, s>>>(a);
+  k_union_near<DIM><<<grid_for(a.n), kCT, 0, s>>>(a);
+  k_compress<<<grid_for(a.n), kCT, 0, s>>>(a);
+  k_union<DIM><<<grid_for(a.n), kCT, 0, s>>>(a);
+  k_cmin<<<grid_for(a.n), kCT, 0, s>>>(a);
+  k_roots<DIM><<<grid_for(a.n), kCT, 0, s>>>(a, root);
+}
+
 }  // namespace
 
 size_t cluster_scratch_bytes(int64_t n) {
-  int64_t buckets = 1, pad = 1;
-  while (buckets < 2 * n) buckets <<= 1;
-  while (pad < n) pad <<= 1;
-  const int64_t nb = (n + kCT - 1) / kCT;
-  // ten sub-buffers, each start rounded up to 256 bytes
-  return (size_t)buckets * 4 + (size_t)n * (4 + 16 + 1 + 4 + 4 + 4) + (size_t)nb * 4 + (size_t)pad * 8 + 64 + 10 * 256;
+  int64_t buckets, pad;
+  table_sizes(n, &buckets, &pad);
+  const int64_t nbb = (buckets + kCT - 1) / kCT;
+  // thirteen sub-buffers, each start rounded up to 256 bytes
+  return (size_t)pad * 8 + (size_t)buckets * 12 + 4 + (size_t)nbb * 4 + (size_t)n * (8 + 16 + 4 + 1 + 1 + 4 + 4) +
+         64 + 13 * 256;
 }
 
 int64_t cluster_max_points() { return (int64_t)kCT * kSumsPerThread * kCT; }
@@ -321,10 +677,9 @@ int64_t cluster_max_points() { return (int64_t)kCT * kSumsPerThread * kCT; }
 cudaError_t launch_cluster(const float* feat, int64_t n, int dim, double eps, int min_pts, void* scratch,
                            int* labels, int* perm, int* offsets, int max_clusters, int* n_clusters_host,
                            int* err_host, cudaStream_t s) {
-  int64_t buckets = 1, pad = 1;
-  while (buckets < 2 * n) buckets <<= 1;
-  while (pad < n) pad <<= 1;
-  const int64_t nb = (n + kCT - 1) / kCT;
+  int64_t buckets, pad;
+  table_sizes(n, &buckets, &pad);
+  const int64_t nbb = (buckets + kCT - 1) / kCT;
   char* b = (char*)scratch;
   auto take = [&](size_t bytes) {
     char* p = b;
@@ -332,21 +687,23 @@ cudaError_t launch_cluster(const float* feat, int64_t n, int dim, double eps, in
     return p;
   };
   unsigned long long* keys = (unsigned long long*)take((size_t)pad * 8);
-  int4* cellc = (int4*)take((size_t)n * 16);
-  int* head = (int*)take((size_t)buckets * 4);
-  int* next = (int*)take((size_t)n * 4);
+  float4* sfeat = (float4*)take((size_t)n * 16);
+  int2* bslot = (int2*)take((size_t)n * 8);
+  int* count = (int*)take((size_t)buckets * 4);
+  int* start = (int*)take((size_t)buckets * 4 + 4);
+  // the bucket scan, then the component minima, then the root-flag scan (n <= buckets)
+  int* excl = (int*)take((size_t)buckets * 4);
+  int* block_sum = (int*)take((size_t)nbb * 4);
+  int* sidx = (int*)take((size_t)n * 4);
   int* parent = (int*)take((size_t)n * 4);
   int* root = (int*)take((size_t)n * 4);
-  int* flag_scan = (int*)take((size_t)n * 4);
-  int* block_sum = (int*)take((size_t)nb * 4);
+  uint8_t* score = (uint8_t*)take((size_t)n);
   uint8_t* core = (uint8_t*)take((size_t)n);
   int* small = (int*)take(64);  // err, total, noise
 
   ClusterArgs a;
   a.feat = feat;
   a.n = n;
-  a.dim = dim;
-  a.gdim = dim < 3 ? dim : 3;
   a.eps2 = eps * eps;
   {
     // FP32 certainty thresholds, rounded outward; 0 disables the in-test
@@ -365,26 +722,49 @@ cudaError_t launch_cluster(const float* feat, int64_t n, int dim, double eps, in
   // whatever the rounding of the cell coordinates
   a.inv_cell = eps > 0.0 ? 1.0 / (eps * (1.0 + 0x1p-10)) : 1.0;
   a.min_pts = min_pts;
-  a.hmask = (uint32_t)(buckets - 1);
-  a.head = head;
-  a.next = next;
-  a.cellc = cellc;
+  {
+    int bits = 0;
+    while ((int64_t{1} << bits) < buckets) ++bits;
+    const int g = dim < 3 ? dim : 3;
+    const int lx = (bits + g - 1) / g;
+    const int ly = g > 1 ? (bits - lx + g - 2) / (g - 1) : 0;
+    const int lz = bits - lx - ly;
+    a.xmask = (1u << lx) - 1u;
+    a.ymask = (1u << ly) - 1u;
+    a.zmask = (1u << lz) - 1u;
+    a.ysh = lx;
+    a.zsh = lx + ly;
+  }
+  a.count = count;
+  a.start = start;
+  a.bslot = bslot;
+  a.sfeat = sfeat;
+  a.sidx = sidx;
+  a.score = score;
   a.core = core;
   a.parent = parent;
+  a.cmin = excl;
   a.err = small;
 
   cudaError_t e;
-  if ((e = cudaMemsetAsync(head, 0xff, (size_t)buckets * 4, s)) != cudaSuccess) return e;
+  if ((e = cudaMemsetAsync(count, 0, (size_t)buckets * 4, s)) != cudaSuccess) return e;
   if ((e = cudaMemsetAsync(small, 0, 64, s)) != cudaSuccess) return e;
-  k_grid<<<grid_for(n), kCT, 0, s>>>(a);
-  k_core<<<grid_for(n), kCT, 0, s>>>(a);
-  k_union<<<grid_for(n), kCT, 0, s>>>(a);
-  k_roots<<<grid_for(n), kCT, 0, s>>>(a, root);
-  k_scan_blocks<<<(unsigned)nb, kCT, 0, s>>>(a, root, flag_scan, block_sum);
+  switch (dim) {
+    case 1: launch_grid_phase<1>(a, buckets, excl, block_sum, root, s); break;
+    case 2: launch_grid_phase<2>(a, buckets, excl, block_sum, root, s); break;
+    case 3: launch_grid_phase<3>(a, buckets, excl, block_sum, root, s); break;
+    case 4: launch_grid_phase<4>(a, buckets, excl, block_sum, root, s); break;
+    default: return cudaErrorInvalidValue;
+  }
+  const int64_t nb = (n + kCT - 1) / kCT;
+  k_scan_blocks<<<(unsigned)nb, kCT, 0, s>>>(RootFlag{core, root}, n, excl, block_sum);
   k_scan_sums<<<1, kCT, 0, s>>>(block_sum, (int)nb, small + 1);
-  k_label<<<grid_for(pad), kCT, 0, s>>>(a, root, flag_scan, block_sum, labels, keys, pad);
-  for (int64_t k = 2; k <= pad; k <<= 1)
-    for (int64_t j = k >> 1; j > 0; j >>= 1) k_bitonic<<<grid_for(pad), kCT, 0, s>>>(keys, pad, j, k);
+  k_label<<<grid_for(pad), kCT, 0, s>>>(a, root, excl, block_sum, labels, keys, pad);
+  k_bitonic_block<<<(unsigned)(pad > kBE ? pad / kBE : 1), kBT, 0, s>>>(keys, pad);
+  for (int64_t k = 2 * kBE; k <= pad; k <<= 1) {
+    for (int64_t j = k >> 1; j >= kBE; j >>= 1) k_bitonic_step<<<grid_for(pad / 2), kCT, 0, s>>>(keys, pad, j, k);
+    k_bitonic_tail<<<(unsigned)(pad / kBE), kBT, 0, s>>>(keys, k);
+  }
   k_count_noise<<<grid_for(n), kCT, 0, s>>>(labels, n, small + 2);
   if ((e = cudaGetLastError()) != cudaSuccess) return e;
   int h[3] = {0, 0, 0};
