@@ -19,14 +19,17 @@
 // around any cell land in 3^g distinct buckets and x - 1, x, x + 1 in
 // consecutive ones.  A counting sort lays the points out bucket by bucket
 // (features as float4 next to their original index): a point's candidates
-// are then a few contiguous spans, and the threads of a warp, which hold
-// neighbouring sorted points, scan the same spans.  One thread per sorted
-// point counts neighbours, then a lock-free union-find over core-core
-// neighbour pairs, on sorted positions so that a warp's parent loads
-// coincide, links the larger root under the smaller; an atomic minimum per
-// component gives its smallest core index, a device-wide scan numbers the
-// clusters, and a bitonic sort of (cluster,
-// index) keys, its short strides in shared memory, gives the CSR order.
+// are then a few contiguous spans.  One thread per sorted point; lanes of a
+// warp in one bucket walk their common spans together (coalesced tiles,
+// shuffles), other lanes walk alone with batched loads.  Neighbour counts;
+// then a lock-free union-find over core-core neighbour pairs on sorted
+// positions (a near-neighbour linking pass and a compression first, so the
+// full pass mostly meets pairs that already share a root) that links the
+// larger root under the smaller; an atomic minimum per component gives its
+// smallest core index; a device-wide scan numbers the clusters.  The CSR:
+// per-cluster counts, offsets by a scan, placement, and a shared-memory sort
+// of each cluster's indices (a global bitonic sort of (cluster, index) keys
+// when a cluster exceeds one block's capacity).
 // Every loop is bounded by the input size; the union retry loop has an
 // explicit cap that raises an error flag instead of spinning.
 #include <cstdint>
@@ -529,23 +532,89 @@ __global__ void k_scan_sums(int* block_sum, int nb, int* total) {
   if (threadIdx.x == kCT - 1 && total) *total = s[kCT - 1];
 }
 
-// labels and the sort keys (cluster << 32 | index; noise sorts last)
+// Labels, the points per cluster, the noise count and the sort keys of the
+// large-cluster path (cluster << 32 | index; noise sorts last).  One thread
+// per sorted position, so the lanes of a warp mostly share a cluster and
+// add to its count once.
 __global__ void k_label(ClusterArgs a, const int* root, const int* flag_scan, const int* block_sum, int* labels,
-                        unsigned long long* keys, int64_t n_pad) {
-  const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-  if (i >= n_pad) return;
-  if (i >= a.n) {
-    keys[i] = ~0ull;
-    return;
+                        int* counts, int* noise, unsigned long long* keys, int64_t n_pad) {
+  const int64_t s = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  int lab = -2;  // past the end
+  if (s < a.n) {
+    const int i = a.sidx[s];
+    lab = -1;
+    int r = root[i];
+    if (r >= 0) {
+      if (!a.core[i]) r = root[r];  // a border point's core neighbour -> its root
+      lab = flag_scan[r] + block_sum[r / kCT];
+    }
+    labels[i] = lab;
+    keys[i] = ((unsigned long long)(uint32_t)(lab >= 0 ? lab : 0x7fffffff) << 32) | (unsigned long long)i;
+  } else if (s < n_pad) {
+    keys[s] = ~0ull;
   }
-  int lab = -1;
-  int r = root[i];
-  if (r >= 0) {
-    if (!a.core[i]) r = root[r];  // a border point's core neighbour -> its root
-    lab = flag_scan[r] + block_sum[r / kCT];
-  }
-  labels[i] = lab;
-  keys[i] = ((unsigned long long)(uint32_t)(lab >= 0 ? lab : 0x7fffffff) << 32) | (unsigned long long)i;
+  const unsigned peers = __match_any_sync(kFull, lab);
+  const int lane = threadIdx.x & 31;
+  if (lab >= 0 && (peers & ((1u << lane) - 1u)) == 0u) atomicAdd(&counts[lab], __popc(peers));
+  const unsigned nz = __ballot_sync(kFull, lab == -1);
+  if (lane == 0 && nz) atomicAdd(noise, __popc(nz));
+}
+
+// the largest cluster (clusters 0 .. *total - 1)
+__global__ void k_maxcount(const int* counts, int64_t n, const int* total, int* maxc) {
+  const int64_t c = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  const int v = c < n && c < *total ? counts[c] : 0;
+  const int m = __reduce_max_sync(kFull, v);
+  if ((threadIdx.x & 31) == 0 && m > 0) atomicMax(maxc, m);
+}
+
+// ---- the CSR: clusters placed by offsets, each cluster's indices sorted -----------
+__global__ void k_offsets(const int* excl, const int* block_sum, int n_clusters, int n_clustered, int* offsets) {
+  const int64_t c = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (c < n_clusters) offsets[c] = excl[c] + block_sum[c / kCT];
+  if (c == n_clusters) offsets[c] = n_clustered;
+}
+
+// places each clustered point in its cluster's range (in no particular
+// order: k_segsort orders it); by sorted position, one atomic per cluster
+// and warp
+__global__ void k_place(const int* sidx, const int* labels, int64_t n, const int* offsets, int* cursor, int* perm) {
+  const int64_t s = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  const int i = s < n ? sidx[s] : -1;
+  const int lab = i >= 0 ? labels[i] : -1;
+  const unsigned peers = __match_any_sync(kFull, lab);
+  const int lane = threadIdx.x & 31, lead = __ffs(peers) - 1;
+  int base = 0;
+  if (lab >= 0 && lane == lead) base = atomicAdd(&cursor[lab], __popc(peers));
+  base = __shfl_sync(kFull, base, lead);
+  if (lab >= 0) perm[offsets[lab] + base + __popc(peers & ((1u << lane) - 1u))] = i;
+}
+
+constexpr int kSegT = 256;    // threads per cluster of the segment sort
+constexpr int kSegMax = 2048;  // largest cluster the segment sort takes
+
+// one block per cluster: bitonic sort of its indices (<= kSegMax) in shared memory
+__global__ void __launch_bounds__(kSegT) k_segsort(int* perm, const int* offsets) {
+  __shared__ int v[kSegMax];
+  const int b = offsets[blockIdx.x], len = offsets[blockIdx.x + 1] - b;
+  if (len <= 1) return;  // the whole block
+  int p2 = 2;
+  while (p2 < len) p2 <<= 1;
+  for (int e = threadIdx.x; e < p2; e += kSegT) v[e] = e < len ? perm[b + e] : 0x7fffffff;
+  __syncthreads();
+  for (int k = 2; k <= p2; k <<= 1)
+    for (int j = k >> 1; j > 0; j >>= 1) {
+      for (int t = threadIdx.x; t < p2 / 2; t += kSegT) {
+        const int i = (int)(((t & ~(j - 1)) << 1) | (t & (j - 1))), l = i + j;
+        const int x = v[i], y = v[l];
+        if ((x > y) == ((i & k) == 0)) {
+          v[i] = y;
+          v[l] = x;
+        }
+      }
+      __syncthreads();
+    }
+  for (int e = threadIdx.x; e < len; e += kSegT) perm[b + e] = v[e];
 }
 
 // ---- bitonic sort of the keys (n_pad a power of two) -------------------------------
@@ -614,13 +683,6 @@ __global__ void k_csr(const unsigned long long* keys, int64_t n, int n_clustered
   perm[j] = (int)(kj & 0xffffffffull);
   if (j == 0 || (int)(keys[j - 1] >> 32) != c) offsets[c] = (int)j;
   (void)n;
-}
-
-__global__ void k_count_noise(const int* labels, int64_t n, int* noise) {
-  const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-  const bool nz = i < n && labels[i] < 0;
-  const unsigned b = __ballot_sync(0xffffffffu, nz);
-  if ((threadIdx.x & 31) == 0 && b) atomicAdd(noise, __popc(b));
 }
 
 __global__ void k_gather(const int* perm, int64_t m, const float* s0, float* d0, const float* s1, float* d1,
@@ -756,25 +818,42 @@ cudaError_t launch_cluster(const float* feat, int64_t n, int dim, double eps, in
     case 4: launch_grid_phase<4>(a, buckets, excl, block_sum, root, s); break;
     default: return cudaErrorInvalidValue;
   }
+  // per-cluster counts and placement cursors in the bucket slots (dead after k_scatter)
+  int* counts = (int*)bslot;
+  int* cursor = counts + n;
+  if ((e = cudaMemsetAsync(counts, 0, (size_t)n * 8, s)) != cudaSuccess) return e;
   const int64_t nb = (n + kCT - 1) / kCT;
   k_scan_blocks<<<(unsigned)nb, kCT, 0, s>>>(RootFlag{core, root}, n, excl, block_sum);
   k_scan_sums<<<1, kCT, 0, s>>>(block_sum, (int)nb, small + 1);
-  k_label<<<grid_for(pad), kCT, 0, s>>>(a, root, excl, block_sum, labels, keys, pad);
-  k_bitonic_block<<<(unsigned)(pad > kBE ? pad / kBE : 1), kBT, 0, s>>>(keys, pad);
-  for (int64_t k = 2 * kBE; k <= pad; k <<= 1) {
-    for (int64_t j = k >> 1; j >= kBE; j >>= 1) k_bitonic_step<<<grid_for(pad / 2), kCT, 0, s>>>(keys, pad, j, k);
-    k_bitonic_tail<<<(unsigned)(pad / kBE), kBT, 0, s>>>(keys, k);
-  }
-  k_count_noise<<<grid_for(n), kCT, 0, s>>>(labels, n, small + 2);
+  k_label<<<grid_for(pad), kCT, 0, s>>>(a, root, excl, block_sum, labels, counts, small + 2, keys, pad);
+  k_maxcount<<<grid_for(n), kCT, 0, s>>>(counts, n, small + 1, small + 3);
   if ((e = cudaGetLastError()) != cudaSuccess) return e;
-  int h[3] = {0, 0, 0};
+  int h[4] = {0, 0, 0, 0};  // err, clusters, noise, largest cluster
   if ((e = cudaMemcpyAsync(h, small, sizeof(h), cudaMemcpyDeviceToHost, s)) != cudaSuccess) return e;
   if ((e = cudaStreamSynchronize(s)) != cudaSuccess) return e;
   *err_host = h[0];
   *n_clusters_host = h[1];
   if (h[0] || h[1] > max_clusters) return cudaSuccess;  // the caller reports it; no CSR written
-  const int n_clustered = (int)(n - h[2]);
-  k_csr<<<grid_for((int64_t)n_clustered + 1), kCT, 0, s>>>(keys, n, n_clustered, perm, offsets, h[1]);
+  const int nc = h[1], n_clustered = (int)(n - h[2]);
+  if (h[3] <= kSegMax) {
+    if (nc > 0) {
+      const int64_t nbc = (nc + kCT - 1) / kCT;
+      k_scan_blocks<<<(unsigned)nbc, kCT, 0, s>>>(CountValue{counts}, nc, excl, block_sum);
+      k_scan_sums<<<1, kCT, 0, s>>>(block_sum, (int)nbc, nullptr);
+    }
+    k_offsets<<<grid_for((int64_t)nc + 1), kCT, 0, s>>>(excl, block_sum, nc, n_clustered, offsets);
+    if (nc > 0) {
+      k_place<<<grid_for(n), kCT, 0, s>>>(sidx, labels, n, offsets, cursor, perm);
+      k_segsort<<<(unsigned)nc, kSegT, 0, s>>>(perm, offsets);
+    }
+  } else {  // a cluster too large for one block: sort all (cluster, index) keys
+    k_bitonic_block<<<(unsigned)(pad > kBE ? pad / kBE : 1), kBT, 0, s>>>(keys, pad);
+    for (int64_t k = 2 * kBE; k <= pad; k <<= 1) {
+      for (int64_t j = k >> 1; j >= kBE; j >>= 1) k_bitonic_step<<<grid_for(pad / 2), kCT, 0, s>>>(keys, pad, j, k);
+      k_bitonic_tail<<<(unsigned)(pad / kBE), kBT, 0, s>>>(keys, k);
+    }
+    k_csr<<<grid_for((int64_t)n_clustered + 1), kCT, 0, s>>>(keys, n, n_clustered, perm, offsets, nc);
+  }
   return cudaGetLastError();
 }
 

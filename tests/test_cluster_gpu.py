@@ -106,6 +106,18 @@ def test_edge_cases(torch, ctx):
     assert (off == -7).all()
 
 
+@pytest.mark.parametrize("long_chain", [2048, 2049])
+def test_csr_paths(torch, ctx, long_chain):
+    # chains of points 1 apart (eps 1.0, min_pts 2), shuffled: the largest
+    # cluster at and just past one block's sort capacity (2048 points)
+    chains = [np.stack([np.arange(k, dtype=np.float64), np.full(k, 10.0 * c)], 1)
+              for c, k in enumerate([long_chain, 700, 2047, 1])]
+    f = np.concatenate(chains)
+    f = f[np.random.default_rng(long_chain).permutation(f.shape[0])]
+    lab = _check(torch, ctx, f, 1.0, 2)
+    assert np.bincount(lab[lab >= 0]).max() == long_chain
+
+
 def test_deterministic(torch, ctx):
     s = synth.make_scene(synth.SCENES["scene"], n_objects=256, gen_seed=22)
     a = _cluster(torch, ctx, s.features(), 1.0, 4)
