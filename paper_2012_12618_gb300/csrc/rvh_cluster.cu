@@ -65,6 +65,7 @@ struct ClusterArgs {
   uint8_t* core;       // [n] core flag by original index
   int* parent;         // [n] union-find over sorted positions
   int* cmin;           // [n] by root position: the component's smallest original core index
+  int* broot;          // [buckets] root shared by a bucket's core points, -1 mixed, kNoCore none
   int* err;            // error flag
 };
 
@@ -136,8 +137,10 @@ template <int DIM, typename Span>
 __device__ __forceinline__ bool for_spans(const ClusterArgs& a, const Cell& c, int limit, Span span) {
   constexpr int G = DIM < 3 ? DIM : 3;
   constexpr int RY = G > 1 ? 1 : 0, RZ = G > 2 ? 1 : 0;
-  for (int dz = -RZ; dz <= RZ; ++dz)
-    for (int dy = -RY; dy <= RY; ++dy) {
+  // the cell's own row first (the early exit of the neighbour count comes sooner)
+  for (int iz = 0; iz <= 2 * RZ; ++iz)
+    for (int iy = 0; iy <= 2 * RY; ++iy) {
+      const int dz = iz == 2 ? -1 : iz, dy = iy == 2 ? -1 : iy;
       const uint32_t row = row_bucket(a, c.y + dy, c.z + dz);
       const uint32_t bx = (uint32_t)(c.x - 1) & a.xmask;
       if (bx + 2 <= a.xmask) {  // x - 1 .. x + 1 without wrap: one range of three buckets
@@ -155,6 +158,8 @@ __device__ __forceinline__ bool for_spans(const ClusterArgs& a, const Cell& c, i
 // One thread walks its candidates kChunk at a time: chunk(t0, end) handles
 // positions t0 .. min(t0 + kChunk, end) - 1, issuing their loads together.
 constexpr int kChunk = 8;
+constexpr int kNoCore = (int)0xfefefefe;  // bucket root before any core point (memset pattern 0xfe)
+constexpr int kOwnCap = 64;  // own-bucket candidates a thread counts before the shared walk
 template <int DIM, typename Chunk>
 __device__ __forceinline__ bool for_chunks(const ClusterArgs& a, const Cell& c, int limit, Chunk chunk) {
   return for_spans<DIM>(a, c, limit, [&](int b, int e) {
@@ -164,59 +169,58 @@ __device__ __forceinline__ bool for_chunks(const ClusterArgs& a, const Cell& c, 
   });
 }
 
-constexpr unsigned kFull = 0xffffffffu;
-constexpr int kMaxGroups = 4;  // bucket groups per warp that still share walks
-
-// The lanes of a warp in one bucket share their candidates.  Such a group
-// walks them 32 at a time: lane l fetches the features of candidate base + l
-// and tag = fetch(t) (a parent or an index), then every lane sees each
-// candidate of the tile through shuffles, in order, as use(t, features, tag).
-// more() is a warp vote that can end the walk after a tile.  All arguments
-// are warp-uniform; every lane runs the whole walk.
-template <int DIM, typename Fetch, typename Use, typename More>
-__device__ __forceinline__ void warp_walk(const ClusterArgs& a, const Cell& c, int limit, Fetch fetch, Use use,
-                                          More more) {
-  const int lane = threadIdx.x & 31;
-  for_spans<DIM>(a, c, limit, [&](int b, int e) {
-    for (int base = b; base < e; base += 32) {
-      const int cnt = min(32, e - base);
-      float4 fl = make_float4(0.0f, 0.0f, 0.0f, 0.0f);
-      int tag = 0;
-      if (lane < cnt) {
-        fl = a.sfeat[base + lane];
-        tag = fetch(base + lane);
-      }
-      for (int j = 0; j < cnt; ++j) {
-        float4 fq = make_float4(0.0f, 0.0f, 0.0f, 0.0f);
-        fq.x = __shfl_sync(kFull, fl.x, j);
-        if (DIM > 1) fq.y = __shfl_sync(kFull, fl.y, j);
-        if (DIM > 2) fq.z = __shfl_sync(kFull, fl.z, j);
-        if (DIM > 3) fq.w = __shfl_sync(kFull, fl.w, j);
-        use(base + j, fq, __shfl_sync(kFull, tag, j));
-      }
-      if (!more()) return false;
+// Calls bucket(b) for the 3^g distinct buckets around cell c, the cell's own
+// row first, until bucket returns false.
+template <int DIM, typename Bucket>
+__device__ __forceinline__ bool for_buckets(const ClusterArgs& a, const Cell& c, Bucket bucket) {
+  constexpr int G = DIM < 3 ? DIM : 3;
+  constexpr int RY = G > 1 ? 1 : 0, RZ = G > 2 ? 1 : 0;
+  for (int iz = 0; iz <= 2 * RZ; ++iz)
+    for (int iy = 0; iy <= 2 * RY; ++iy) {
+      const int dz = iz == 2 ? -1 : iz, dy = iy == 2 ? -1 : iy;
+      const uint32_t row = row_bucket(a, c.y + dy, c.z + dz);
+      for (int dx = -1; dx <= 1; ++dx)
+        if (!bucket(row + ((uint32_t)(c.x + dx) & a.xmask))) return false;
     }
+  return true;
+}
+
+// the number of candidates of cell c (the sizes of its ranges)
+template <int DIM>
+__device__ __forceinline__ int cand_count(const ClusterArgs& a, const Cell& c) {
+  int n = 0;
+  for_spans<DIM>(a, c, 0x7fffffff, [&](int b, int e) {
+    n += e - b;
+    return true;
+  });
+  return n;
+}
+
+constexpr int kAloneMax = 64;  // a point with at most this many candidates walks them alone
+
+constexpr unsigned kFull = 0xffffffffu;
+
+// The whole warp walks the candidates of one point (cell cl, warp-uniform)
+// kCoopW * 32 at a time: tile(base, end) runs on every lane, lane l taking
+// positions base + 32 w + l below end, and returns a warp-uniform verdict
+// (false ends the walk).  For the few points that need a long walk alone.
+constexpr int kCoopW = 4;
+template <int DIM, typename Tile>
+__device__ __forceinline__ void coop_walk(const ClusterArgs& a, const Cell& cl, Tile tile) {
+  for_spans<DIM>(a, cl, 0x7fffffff, [&](int b, int e) {
+    for (int base = b; base < e; base += 32 * kCoopW)
+      if (!tile(base, e)) return false;
     return true;
   });
 }
 
-// Splits the warp into groups of lanes with equal buckets and runs
-// group(cell, mine) once per group (mine: this lane belongs to it), cell
-// being the group's cell.  A warp with more than kMaxGroups groups runs
-// nothing and gets false: its lanes walk alone.
-template <typename Group>
-__device__ __forceinline__ bool for_groups(const ClusterArgs& a, const Cell& c, Group group) {
-  const int lane = threadIdx.x & 31;
-  const unsigned peers = __match_any_sync(kFull, bucket_of(a, c));
-  const unsigned leaders = __ballot_sync(kFull, (peers & ((1u << lane) - 1u)) == 0u);
-  if (__popc(leaders) > kMaxGroups) return false;
-  for (unsigned l = leaders; l; l &= l - 1u) {
-    const int lead = __ffs(l) - 1;
-    const unsigned members = __shfl_sync(kFull, peers, lead);
-    const Cell cg{__shfl_sync(kFull, c.x, lead), __shfl_sync(kFull, c.y, lead), __shfl_sync(kFull, c.z, lead)};
-    group(cg, members, ((members >> lane) & 1u) != 0u);
-  }
-  return true;
+__device__ __forceinline__ float4 shfl4(const float4& v, int src) {
+  return make_float4(__shfl_sync(kFull, v.x, src), __shfl_sync(kFull, v.y, src), __shfl_sync(kFull, v.z, src),
+                     __shfl_sync(kFull, v.w, src));
+}
+
+__device__ __forceinline__ Cell shfl_cell(const Cell& c, int src) {
+  return Cell{__shfl_sync(kFull, c.x, src), __shfl_sync(kFull, c.y, src), __shfl_sync(kFull, c.z, src)};
 }
 
 template <int DIM>
@@ -252,36 +256,62 @@ __global__ void k_scatter(ClusterArgs a) {
 }
 
 // Neighbour counts (stopping at min_pts), one thread per sorted position.
-// Lanes past the end take the warp's first point, so they join its group.
+// First each thread counts within its own bucket, which settles the points
+// of dense cells (the count only needs to reach min_pts, and a subset of
+// the neighbours is enough); the warp then walks the full neighbourhood of
+// each point still short of min_pts together, counting by ballots.  Lanes
+// past the end take the last point.
 template <int DIM>
 __global__ void k_core(ClusterArgs a) {
   const int64_t s = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-  const int64_t s0 = s - (threadIdx.x & 31);
-  if (s0 >= a.n) return;  // the whole warp
+  const int lane = threadIdx.x & 31;
+  if (s - lane >= a.n) return;  // the whole warp
   const bool live = s < a.n;
-  const float4 fp = a.sfeat[live ? s : s0];
+  const float4 fp = a.sfeat[live ? s : a.n - 1];
   const Cell c = cell_of<DIM>(a, fp);
   int count = 0;
-  const bool shared = for_groups(a, c, [&](const Cell& cg, unsigned, bool mine) {
-    const bool want = mine && live;
-    warp_walk<DIM>(
-        a, cg, 0x7fffffff, [](int) { return 0; },
-        [&](int, const float4& fq, int) {
-          if (want && count < a.min_pts && is_neighbour<DIM>(a, fp, fq)) ++count;
-        },
-        [&] { return __any_sync(kFull, want && count < a.min_pts); });
-  });
-  if (!live) return;
-  if (!shared)
+  if (live) {
+    const uint32_t bk = bucket_of(a, c);
+    const int b = a.start[bk], e = min(a.start[bk + 1], b + kOwnCap);
+    for (int t0 = b; t0 < e && count < a.min_pts; t0 += kChunk) {
+      float4 fq[kChunk];
+#pragma unroll
+      for (int u = 0; u < kChunk; ++u) fq[u] = a.sfeat[min(t0 + u, e - 1)];
+#pragma unroll
+      for (int u = 0; u < kChunk; ++u)
+        if (t0 + u < e && is_neighbour<DIM>(a, fp, fq[u])) ++count;
+    }
+  }
+  const bool need = live && count < a.min_pts;
+  const bool alone = need && cand_count<DIM>(a, c) <= kAloneMax;
+  if (alone) {  // a sparse neighbourhood: walk it alone
+    count = 0;
     for_chunks<DIM>(a, c, 0x7fffffff, [&](int t0, int e) {
       float4 fq[kChunk];
 #pragma unroll
-      for (int u = 0; u < kChunk; ++u) fq[u] = a.sfeat[t0 + u < e ? t0 + u : t0];
+      for (int u = 0; u < kChunk; ++u) fq[u] = a.sfeat[min(t0 + u, e - 1)];
 #pragma unroll
       for (int u = 0; u < kChunk; ++u)
         if (t0 + u < e && is_neighbour<DIM>(a, fp, fq[u])) ++count;
       return count < a.min_pts;
     });
+  }
+  for (unsigned big = __ballot_sync(kFull, need && !alone); big; big &= big - 1u) {
+    const int l = __ffs(big) - 1;
+    const float4 fl = shfl4(fp, l);
+    int n_found = 0;  // warp-uniform
+    coop_walk<DIM>(a, shfl_cell(c, l), [&](int base, int e) {
+      float4 fq[kCoopW];
+#pragma unroll
+      for (int w = 0; w < kCoopW; ++w) fq[w] = a.sfeat[min(base + 32 * w + lane, e - 1)];
+#pragma unroll
+      for (int w = 0; w < kCoopW; ++w)
+        n_found += __popc(__ballot_sync(kFull, base + 32 * w + lane < e && is_neighbour<DIM>(a, fl, fq[w])));
+      return n_found < a.min_pts;
+    });
+    if (lane == l) count = n_found;
+  }
+  if (!live) return;
   const bool core = count >= a.min_pts;
   const int p = a.sidx[s];
   a.score[s] = core;
@@ -334,73 +364,58 @@ __device__ __forceinline__ bool uf_union(const ClusterArgs& a, int& rp, int pt) 
 }
 
 // Joins every core point with its core neighbours at lower sorted positions
-// (each core-core pair once).  A shared walk fetches, per tile, an ancestor
-// of each core candidate two links up (after k_compress mostly its root).
-// Each lane keeps its root rp and an alias, the last ancestor it merged (a
-// value that is in its set for good); candidates whose ancestor is either
-// already share the set.  A vote skips those when every member lane holds
-// the same pair, and only the others are shuffled through the lanes.  A
-// group's walk ends at its last lane's position.
+// (each core-core pair once), one thread per point, bucket by bucket.  rp is
+// the point's root as last seen and alias the last ancestor it merged: both
+// stay in its set for good.  A bucket whose core points all had root rb
+// after the compression needs no look at all when rb is rp or alias, and
+// otherwise only its first core neighbour: one link to rb joins them all.
+// A bucket with mixed roots is walked candidate by candidate.
 template <int DIM>
 __global__ void k_union(ClusterArgs a) {
   const int64_t s = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-  const int lane = threadIdx.x & 31;
-  const int64_t s0 = s - lane;
-  if (s0 >= a.n) return;
-  const bool live = s < a.n;
-  const bool act = live && a.score[s];
-  if (!__any_sync(kFull, act)) return;
-  const float4 fp = a.sfeat[live ? s : s0];
-  const Cell c = cell_of<DIM>(a, fp);
-  int rp = act ? uf_find(a.parent, (int)s) : 0;
+  if (s >= a.n || !a.score[s]) return;
+  const float4 fp = a.sfeat[s];
+  int rp = uf_find(a.parent, (int)s);
   int alias = rp;
-  bool ok = true;
-  const bool shared = for_groups(a, c, [&](const Cell& cg, unsigned members, bool mine) {
-    const unsigned wanting = __ballot_sync(kFull, mine && act);
-    if (!wanting) return;
-    const int64_t last = s0 + 31 - __clz(members);
-    const int limit = (int)(last < a.n ? last : a.n - 1);  // candidates below the group's last position
-    for_spans<DIM>(a, cg, limit, [&](int b, int e) {
-      for (int base = b; base < e; base += 32) {
-        const int cnt = min(32, e - base);
-        int tag = -1;
-        if (lane < cnt && a.score[base + lane]) tag = __ldcg(&a.parent[__ldcg(&a.parent[base + lane])]);
-        const bool want = ((wanting >> lane) & 1u) && ok;
-        const int first = __ffs(wanting) - 1;
-        const int common = __shfl_sync(kFull, rp, first), common_alias = __shfl_sync(kFull, alias, first);
-        const bool same = __all_sync(kFull, !want || (rp == common && alias == common_alias));
-        unsigned todo = __ballot_sync(kFull, tag >= 0 && (!same || (tag != common && tag != common_alias)));
-        if (!todo) continue;
-        float4 fl = make_float4(0.0f, 0.0f, 0.0f, 0.0f);
-        if (lane < cnt) fl = a.sfeat[base + lane];
-        for (; todo; todo &= todo - 1u) {
-          const int j = __ffs(todo) - 1;
-          float4 fq = make_float4(0.0f, 0.0f, 0.0f, 0.0f);
-          fq.x = __shfl_sync(kFull, fl.x, j);
-          if (DIM > 1) fq.y = __shfl_sync(kFull, fl.y, j);
-          if (DIM > 2) fq.z = __shfl_sync(kFull, fl.z, j);
-          if (DIM > 3) fq.w = __shfl_sync(kFull, fl.w, j);
-          const int pt = __shfl_sync(kFull, tag, j);
-          if (want && ok && base + j < s && pt != rp && pt != alias && is_neighbour<DIM>(a, fp, fq)) {
-            ok = uf_union(a, rp, pt);
-            alias = pt;
-          }
+  for_buckets<DIM>(a, cell_of<DIM>(a, fp), [&](uint32_t b) {
+    const int rb = a.broot[b];
+    if (rb == kNoCore || rb == rp || rb == alias) return true;
+    const int lo = a.start[b], hi = min(a.start[b + 1], (int)s);
+    if (rb >= 0) {
+      bool found = false;
+      for (int t0 = lo; t0 < hi && !found; t0 += kChunk) {
+        bool sc[kChunk];
+        float4 fq[kChunk];
+#pragma unroll
+        for (int u = 0; u < kChunk; ++u) {
+          sc[u] = a.score[min(t0 + u, hi - 1)];
+          fq[u] = a.sfeat[min(t0 + u, hi - 1)];
         }
+#pragma unroll
+        for (int u = 0; u < kChunk; ++u)
+          if (t0 + u < hi && sc[u] && is_neighbour<DIM>(a, fp, fq[u])) found = true;
+      }
+      if (found) {
+        if (!uf_union(a, rp, rb)) return false;
+        alias = rb;
       }
       return true;
-    });
-  });
-  if (!act || shared) return;
-  for_chunks<DIM>(a, c, (int)s, [&](int t0, int e) {
-    int tag[kChunk];
+    }
+    for (int t0 = lo; t0 < hi; t0 += kChunk) {
+      bool sc[kChunk];
+      int tag[kChunk];
 #pragma unroll
-    for (int u = 0; u < kChunk; ++u) tag[u] = t0 + u < e && a.score[t0 + u] ? __ldcg(&a.parent[t0 + u]) : -1;
-#pragma unroll
-    for (int u = 0; u < kChunk; ++u)
-      if (tag[u] >= 0 && tag[u] != rp && tag[u] != alias && is_neighbour<DIM>(a, fp, a.sfeat[t0 + u])) {
-        if (!uf_union(a, rp, tag[u])) return false;
-        alias = tag[u];
+      for (int u = 0; u < kChunk; ++u) {
+        sc[u] = a.score[min(t0 + u, hi - 1)];
+        tag[u] = __ldcg(&a.parent[min(t0 + u, hi - 1)]);
       }
+#pragma unroll
+      for (int u = 0; u < kChunk; ++u)
+        if (t0 + u < hi && sc[u] && tag[u] != rp && tag[u] != alias && is_neighbour<DIM>(a, fp, a.sfeat[t0 + u])) {
+          if (!uf_union(a, rp, tag[u])) return false;
+          alias = tag[u];
+        }
+    }
     return true;
   });
 }
@@ -431,6 +446,24 @@ __global__ void k_compress(ClusterArgs a) {
   a.parent[s] = uf_find(a.parent, (int)s);
 }
 
+// Per bucket, the root its core points share, or -1 (mixed): each core
+// point walks to its root (no links meanwhile; parents read here are all
+// ancestors), points its own parent there, and marks its bucket.
+template <int DIM>
+__global__ void k_bucket_roots(ClusterArgs a) {
+  const int64_t s = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (s >= a.n || !a.score[s]) return;
+  int x = (int)s, p = __ldcg(&a.parent[x]);
+  while (p != x) {
+    x = p;
+    p = __ldcg(&a.parent[x]);
+  }
+  __stcg(&a.parent[s], x);
+  int* slot = &a.broot[point_bucket<DIM>(a, a.sfeat[s])];
+  const int old = atomicCAS(slot, kNoCore, x);
+  if (old != kNoCore && old != x && old != -1) atomicExch(slot, -1);
+}
+
 // the smallest original core index of each component, at its root
 __global__ void k_cmin(ClusterArgs a) {
   const int64_t s = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
@@ -440,41 +473,60 @@ __global__ void k_cmin(ClusterArgs a) {
 
 // Core points: root = the component's smallest core index; border points:
 // their lowest-index core neighbour (resolved to its root in k_label);
-// noise: -1.  Written by original index.
+// noise: -1.  Written by original index.  Non-core points are few: the warp
+// walks the neighbourhood of each together and takes the minimum.
 template <int DIM>
 __global__ void k_roots(ClusterArgs a, int* root) {
   const int64_t s = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-  const int64_t s0 = s - (threadIdx.x & 31);
-  if (s0 >= a.n) return;
+  const int lane = threadIdx.x & 31;
+  if (s - lane >= a.n) return;
   const bool live = s < a.n;
-  const bool act = live && !a.score[s];
-  if (live && !act) root[a.sidx[s]] = a.cmin[uf_find(a.parent, (int)s)];
-  if (!__any_sync(kFull, act)) return;
-  const float4 fp = a.sfeat[live ? s : s0];
-  const Cell c = cell_of<DIM>(a, fp);
-  int best = 0x7fffffff;
-  const bool shared = for_groups(a, c, [&](const Cell& cg, unsigned, bool mine) {
-    const bool want = mine && act;
-    if (!__any_sync(kFull, want)) return;
-    warp_walk<DIM>(
-        a, cg, 0x7fffffff, [&](int t) { return a.score[t] ? a.sidx[t] : 0x7fffffff; },
-        [&](int, const float4& fq, int q) {
-          if (want && q < best && is_neighbour<DIM>(a, fp, fq)) best = q;
-        },
-        [] { return true; });
-  });
-  if (!act) return;
-  if (!shared)
-    for_chunks<DIM>(a, c, 0x7fffffff, [&](int t0, int e) {
-      int q[kChunk];
+  const bool core = live && a.score[s];
+  if (core) root[a.sidx[s]] = a.cmin[uf_find(a.parent, (int)s)];
+  const bool need = live && !core;
+  bool alone = false;
+  if (need) {
+    const float4 fp = a.sfeat[s];
+    const Cell c = cell_of<DIM>(a, fp);
+    alone = cand_count<DIM>(a, c) <= kAloneMax;
+    if (alone) {  // a sparse neighbourhood: walk it alone
+      int best = 0x7fffffff;
+      for_chunks<DIM>(a, c, 0x7fffffff, [&](int t0, int e) {
+        bool sc[kChunk];
+        int q[kChunk];
 #pragma unroll
-      for (int u = 0; u < kChunk; ++u) q[u] = t0 + u < e && a.score[t0 + u] ? a.sidx[t0 + u] : 0x7fffffff;
+        for (int u = 0; u < kChunk; ++u) {
+          sc[u] = a.score[min(t0 + u, e - 1)];
+          q[u] = a.sidx[min(t0 + u, e - 1)];
+        }
 #pragma unroll
-      for (int u = 0; u < kChunk; ++u)
-        if (q[u] < best && is_neighbour<DIM>(a, fp, a.sfeat[t0 + u])) best = q[u];
+        for (int u = 0; u < kChunk; ++u)
+          if (t0 + u < e && sc[u] && q[u] < best && is_neighbour<DIM>(a, fp, a.sfeat[t0 + u])) best = q[u];
+        return true;
+      });
+      root[a.sidx[s]] = best == 0x7fffffff ? -1 : best;
+    }
+  }
+  for (unsigned big = __ballot_sync(kFull, need && !alone); big; big &= big - 1u) {
+    const int l = __ffs(big) - 1;
+    const int64_t sl = s - lane + l;
+    const float4 fl = a.sfeat[sl];
+    int best = 0x7fffffff;  // warp-uniform
+    coop_walk<DIM>(a, cell_of<DIM>(a, fl), [&](int base, int e) {
+      int mine = 0x7fffffff;
+#pragma unroll
+      for (int w = 0; w < kCoopW; ++w) {
+        const int t = base + 32 * w + lane, tc = min(t, e - 1);
+        const bool sc = a.score[tc];
+        const int q = a.sidx[tc];
+        const float4 fq = a.sfeat[tc];
+        if (t < e && sc && q < mine && is_neighbour<DIM>(a, fl, fq)) mine = q;
+      }
+      best = min(best, __reduce_min_sync(kFull, mine));
       return true;
     });
-  root[a.sidx[s]] = best == 0x7fffffff ? -1 : best;
+    if (lane == l) root[a.sidx[s]] = best == 0x7fffffff ? -1 : best;
+  }
 }
 
 // ---- device-wide exclusive scan (bucket starts; cluster numbering) -----------------
@@ -708,7 +760,8 @@ void table_sizes(int64_t n, int64_t* buckets, int64_t* n_pad) {
 }
 
 template <int DIM>
-void launch_grid_phase(ClusterArgs& a, int64_t buckets, int* excl, int* block_sum, int* root, cudaStream_t s) {
+cudaError_t launch_grid_phase(ClusterArgs& a, int64_t buckets, int* excl, int* block_sum, int* root,
+                              cudaStream_t s) {
   const unsigned nbb = grid_for(buckets);
   k_grid<DIM><<<grid_for(a.n), kCT, 0, s>>>(a);
   k_scan_blocks<<<nbb, kCT, 0, s>>>(CountValue{a.count}, buckets, excl, block_sum);
@@ -718,9 +771,14 @@ void launch_grid_phase(ClusterArgs& a, int64_t buckets, int* excl, int* block_su
   k_core<DIM><<<grid_for(a.n), kCT, 0, s>>>(a);
   k_union_near<DIM><<<grid_for(a.n), kCT, 0, s>>>(a);
   k_compress<<<grid_for(a.n), kCT, 0, s>>>(a);
+  // the bucket counts are consumed by now: their memory holds the bucket roots
+  const cudaError_t e = cudaMemsetAsync(a.broot, 0xfe, (size_t)buckets * 4, s);
+  if (e != cudaSuccess) return e;
+  k_bucket_roots<DIM><<<grid_for(a.n), kCT, 0, s>>>(a);
   k_union<DIM><<<grid_for(a.n), kCT, 0, s>>>(a);
   k_cmin<<<grid_for(a.n), kCT, 0, s>>>(a);
   k_roots<DIM><<<grid_for(a.n), kCT, 0, s>>>(a, root);
+  return cudaSuccess;
 }
 
 }  // namespace
@@ -806,18 +864,20 @@ cudaError_t launch_cluster(const float* feat, int64_t n, int dim, double eps, in
   a.core = core;
   a.parent = parent;
   a.cmin = excl;
+  a.broot = count;
   a.err = small;
 
   cudaError_t e;
   if ((e = cudaMemsetAsync(count, 0, (size_t)buckets * 4, s)) != cudaSuccess) return e;
   if ((e = cudaMemsetAsync(small, 0, 64, s)) != cudaSuccess) return e;
   switch (dim) {
-    case 1: launch_grid_phase<1>(a, buckets, excl, block_sum, root, s); break;
-    case 2: launch_grid_phase<2>(a, buckets, excl, block_sum, root, s); break;
-    case 3: launch_grid_phase<3>(a, buckets, excl, block_sum, root, s); break;
-    case 4: launch_grid_phase<4>(a, buckets, excl, block_sum, root, s); break;
+    case 1: e = launch_grid_phase<1>(a, buckets, excl, block_sum, root, s); break;
+    case 2: e = launch_grid_phase<2>(a, buckets, excl, block_sum, root, s); break;
+    case 3: e = launch_grid_phase<3>(a, buckets, excl, block_sum, root, s); break;
+    case 4: e = launch_grid_phase<4>(a, buckets, excl, block_sum, root, s); break;
     default: return cudaErrorInvalidValue;
   }
+  if (e != cudaSuccess) return e;
   // per-cluster counts and placement cursors in the bucket slots (dead after k_scatter)
   int* counts = (int*)bslot;
   int* cursor = counts + n;
