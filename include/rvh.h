@@ -247,8 +247,10 @@ int rvh_estimate_noalloc(const rvh_frame* frame, const rvh_params* params, rvh_r
  * ordered on `stream` (NULL: the context's stream) and returns after it has
  * completed (it reads the cluster count back).  More than max_clusters
  * clusters: RVH_EINVAL with *n_clusters and labels set, perm and offsets
- * not written.  The context's memory budget covers the scratch (about
- * 38 bytes per point plus 20 bytes per point rounded up to a power of two). */
+ * not written.  The context's memory budget covers the scratch: about 38
+ * bytes per point, 8 bytes per point rounded up to a power of two, and 12
+ * bytes per bucket of the cell table (a power of two >= 4 x n_points, at
+ * most 4,194,304 buckets). */
 int rvh_cluster(rvh_ctx* ctx, const float* features, int64_t n_points, int32_t dim, double eps, int32_t min_pts,
                 int32_t* labels, int32_t* perm, int32_t* offsets, int32_t max_clusters, int32_t* n_clusters,
                 void* stream);

@@ -749,11 +749,14 @@ __global__ void k_gather(const int* perm, int64_t m, const float* s0, float* d0,
 
 inline unsigned grid_for(int64_t n) { return (unsigned)((n + kCT - 1) / kCT); }
 
-// buckets: a power of two >= n and >= 64 (two bits or more per gridded
-// component); n_pad: the bitonic length, a power of two >= n
+// buckets: a power of two >= 4 n (fewer far cells sharing a bucket), at
+// least 64 (two bits or more per gridded component) and at most what the
+// one-block scan takes, which is >= n; n_pad: the bitonic length, a power of
+// two >= n
+constexpr int64_t kMaxBuckets = (int64_t)kCT * kSumsPerThread * kCT;
 void table_sizes(int64_t n, int64_t* buckets, int64_t* n_pad) {
   int64_t b = 64, p = 1;
-  while (b < n) b <<= 1;
+  while (b < 4 * n && b < kMaxBuckets) b <<= 1;
   while (p < n) p <<= 1;
   *buckets = b;
   *n_pad = p;
