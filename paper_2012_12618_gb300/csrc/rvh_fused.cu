@@ -71,6 +71,19 @@ __device__ __forceinline__ unsigned long long block_sum_u64(unsigned long long v
   return r;
 }
 
+__device__ __forceinline__ unsigned long long block_max_u64(unsigned long long v, unsigned long long* red) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) v = max(v, __shfl_xor_sync(0xffffffffu, v, o));
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  __syncthreads();
+  if (lane == 0) red[warp] = v;
+  __syncthreads();
+  unsigned long long r = red[0];
+#pragma unroll
+  for (int w = 1; w < kWarps; ++w) r = max(r, red[w]);
+  return r;
+}
+
 __device__ __forceinline__ float block_max_float(float v, float* red) {
 #pragma unroll
   for (int o = 16; o > 0; o >>= 1) v = fmaxf(v, __shfl_xor_sync(0xffffffffu, v, o));
@@ -210,6 +223,7 @@ struct ClusterShared {
   int sel_digit, sel_k;       // radix select: digit and rank inside it
   float red4[4][kWarps];      // line model: min / max of azimuth and Doppler
   unsigned long long runs[2];  // trials run, pairs scored
+  int nref;                   // 2D trials queued for refinement in the current chunk
 };
 
 // Adaptive trial count: with `best` the best (count + 1, -index) key so far,
@@ -808,6 +822,7 @@ __device__ void process_cluster(const FrameDesc& a, const Smem& S, ClusterShared
   if (tid == 0) {
     cs.best = 0ull;
     cs.wmax = wm;
+    cs.nref = 0;
   }
   __syncthreads();
   const float wmax = cs.wmax;
@@ -820,6 +835,14 @@ __device__ void process_cluster(const FrameDesc& a, const Smem& S, ClusterShared
   for (int hc0 = 0; hc0 < a.H; hc0 += chunk) {
     const int nh = min(chunk, a.H - hc0);
     // a2 + a3: draw, FP32 solve (refined when ill-conditioned), bound
+    // Trials with a wide band refine their velocity.  3D minimal sets are
+    // often ill-conditioned and refine on the spot above kRefineBand.  2D ones
+    // have |det| = |sin(t1 - t0)| and mostly narrow bands, whose few band
+    // points cost less than refining; those above tau / 32 (the seeds of a
+    // cluster of narrow azimuth extent, such as a far object) are queued and
+    // refined in a second pass, one per lane, so that a refining lane does not
+    // hold up a warp of trials that need none.
+    const float refine_band = DIM == 3 ? kRefineBand : a.tau32.hi * 0x1p-5f;
     auto cosine_trials = [&]() {
       for (int hl = tid; hl < nh; hl += kThreads) {
         int q[3];
@@ -828,14 +851,13 @@ __device__ void process_cluster(const FrameDesc& a, const Smem& S, ClusterShared
         const float4 p0 = rows.at(q[0]), p1 = rows.at(q[1]), p2 = rows.at(q2);
         const int qs[3] = {q[0], q[1], q2};
         auto seed64 = [&](int i) { return R.at(qs[i]); };
-        // 2D minimal sets are mildly conditioned (|det| = |sin(t1 - t0)|): their
-        // wide bands are rare and cheaper than refining; 3D trials refine
-        Hyp32 hy = hyp_f32<DIM>(p0, p1, p2, seed64, DIM == 3, wmax, a.acc, a.rej, a.tau32);
+        const float rb = DIM == 3 ? refine_band : __int_as_float(0x7f800000);
+        Hyp32 hy = hyp_f32<DIM>(p0, p1, p2, seed64, rb, wmax, a.acc, a.rej, a.tau32);
         if (hy.kind == kHypUndecided) {
           ++n_fp64;
           double v[3];
           if (hyp_f64<DIM>(a, R, ci, hc0 + hl, N, v)) {
-            hy = hyp_f32<DIM>(p0, p1, p2, seed64, DIM == 3, wmax, 0.0f, 0.0f, a.tau32);
+            hy = hyp_f32<DIM>(p0, p1, p2, seed64, rb, wmax, 0.0f, 0.0f, a.tau32);
             if (hy.kind != kHypNormal) {
               hy.kind = kHypExactOnly;
               hy.thi = __int_as_float(0x7f800000);
@@ -850,7 +872,42 @@ __device__ void process_cluster(const FrameDesc& a, const Smem& S, ClusterShared
         S.hyp[hl] = make_float4(hy.nx, hy.ny, hy.nz, hy.kind == kHypRejected ? __int_as_float(0x7fc00000) : hy.thi);
         S.tlo[hl] = hy.tlo;
         S.kind[hl] = (int8_t)hy.kind;
-        S.U[hl] = hy.kind == kHypRejected ? -1 : (hy.kind == kHypExactOnly ? N : 0);
+        if constexpr (DIM == 2) {
+          // the queue lives in U until the second pass has read it
+          if (hy.kind == kHypNormal && hy.thi - a.tau32.hi > refine_band) S.U[atomicAdd(&cs.nref, 1)] = hl;
+        } else {
+          S.U[hl] = hy.kind == kHypRejected ? -1 : (hy.kind == kHypExactOnly ? N : 0);
+        }
+      }
+      if constexpr (DIM == 2) {
+        __syncthreads();
+        const int nr = cs.nref;
+        for (int i = tid; i < nr; i += kThreads) {
+          const int hl = S.U[i];
+          int q[3];
+          draw_minimal_set<DIM>(a.key, a.cluster_base + ci, hc0 + hl, N, q);
+          const int qs[3] = {q[0], q[1], q[0]};
+          auto seed64 = [&](int k) { return R.at(qs[k]); };
+          // the trial was accepted in the first pass: no conditioning test
+          Hyp32 hy = hyp_f32<DIM>(rows.at(q[0]), rows.at(q[1]), rows.at(q[0]), seed64, refine_band, wmax, 0.0f,
+                                  0.0f, a.tau32);
+          if (hy.kind != kHypNormal) {
+            hy.kind = kHypExactOnly;
+            hy.thi = __int_as_float(0x7f800000);
+            hy.tlo = -1.0f;
+            ++n_fp64;
+          }
+          n_ref += hy.refined;
+          S.hyp[hl] = make_float4(hy.nx, hy.ny, hy.nz, hy.thi);
+          S.tlo[hl] = hy.tlo;
+          S.kind[hl] = (int8_t)hy.kind;
+        }
+        __syncthreads();
+        for (int hl = tid; hl < nh; hl += kThreads) {
+          const int k = S.kind[hl];
+          S.U[hl] = k == kHypRejected ? -1 : (k == kHypExactOnly ? N : 0);
+        }
+        if (tid == 0) cs.nref = 0;
       }
     };
     if constexpr (EXT && DIM == 2) {
@@ -887,55 +944,42 @@ __device__ void process_cluster(const FrameDesc& a, const Smem& S, ClusterShared
     __syncthreads();
     stage_done(2);
 
-    // a5 + a6: exact counts, in index order, of the trials whose upper bound
-    // can still win.  C_h <= U_h <= Umax, so the first trial (lowest index)
-    // whose exact count reaches Umax is the winner of the chunk; trials of
-    // earlier chunks have lower indices, so this chunk must beat the lead
-    // strictly.
-    int um = -1;
-    for (int hl = tid; hl < nh; hl += kThreads) um = max(um, S.U[hl]);
-    const int Umax = block_max_int(um, cs.red_i);
-    const int lead = (int)(cs.best >> 32) - 1;  // best exact count so far (-1 none)
-    if (Umax >= 0 && Umax > lead) {
-      for (int pass = 0; pass < 2; ++pass) {
-        int prev = -1;
-        bool done = false;
-        for (;;) {
-          const int cur = (int)(cs.best >> 32) - 1;
-          int c = 0x7fffffff;
-          for (int hl = tid; hl < nh; hl += kThreads) {
-            const int u = S.U[hl];
-            const bool pick = pass == 0 ? (u == Umax) : (u >= cur && u >= 0 && u < Umax);
-            if (hl > prev && pick) c = min(c, hl);
-          }
-          c = block_min_int(c, cs.red_i);
-          if (c == 0x7fffffff) break;
-          const float4 hy = S.hyp[c];
-          const float htlo = S.tlo[c];
-          int B = 0;
-          const int C = exact_count_block<DIM, RV, EXT>(a, rows, R, ci, hc0 + c, N, hy, htlo, cs, &B);
-          ++n_cand;
-          if (tid == 0) {
-            const unsigned long long k = best_key(C, hc0 + c);
-            if (k > cs.best) {
-              cs.best = k;
-              cs.win = hy;
-              cs.win_tlo = htlo;
-              cs.win_has_v64 = B > 0;
-              cs.win_v64[0] = cs.cv64[0];
-              cs.win_v64[1] = cs.cv64[1];
-              cs.win_v64[2] = cs.cv64[2];
-            }
-          }
-          __syncthreads();
-          if (pass == 0 && C == Umax) {
-            done = true;
-            break;
-          }
-          prev = c;
-        }
-        if (done) break;
+    // a5 + a6: exact counts of the trials whose upper bound can still win,
+    // best first: the trial with the highest key (U, then lowest index) is
+    // counted next, until no remaining key beats the lead.  C_h <= U_h, so a
+    // trial whose key (U_h, h) does not beat the lead cannot win with its
+    // exact count either, and the winner -- the highest exact count, the
+    // lowest index among equals -- is the one counting every trial would
+    // give.  Trials of earlier chunks have lower indices; the lead's key
+    // already ranks them.  A counted trial leaves the pool (U = -1).
+    for (;;) {
+      unsigned long long km = 0;
+      for (int hl = tid; hl < nh; hl += kThreads) {
+        const int u = S.U[hl];
+        if (u >= 0) km = max(km, best_key(u, hc0 + hl));
       }
+      km = block_max_u64(km, cs.red_u);
+      if (km <= cs.best) break;  // also km == 0: no trial left
+      const int c = (int)(0xFFFFFFFFu - (uint32_t)(km & 0xFFFFFFFFull)) - hc0;
+      const float4 hy = S.hyp[c];
+      const float htlo = S.tlo[c];
+      int B = 0;
+      const int C = exact_count_block<DIM, RV, EXT>(a, rows, R, ci, hc0 + c, N, hy, htlo, cs, &B);
+      ++n_cand;
+      if (tid == 0) {
+        S.U[c] = -1;
+        const unsigned long long k = best_key(C, hc0 + c);
+        if (k > cs.best) {
+          cs.best = k;
+          cs.win = hy;
+          cs.win_tlo = htlo;
+          cs.win_has_v64 = B > 0;
+          cs.win_v64[0] = cs.cv64[0];
+          cs.win_v64[1] = cs.cv64[1];
+          cs.win_v64[2] = cs.cv64[2];
+        }
+      }
+      __syncthreads();
     }
     __syncthreads();
     stage_done(3);

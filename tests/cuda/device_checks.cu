@@ -110,9 +110,9 @@ __global__ void k_filter(const double2* trig, int n_hyp, int pts_per_hyp, unsign
                               make_double4_32a(a1[0], a1[1], a1[2], (double)w[1]),
                               make_double4_32a(a2[0], a2[1], a2[2], DIM == 3 ? (double)w[2] : 0.0)};
   // odd trials run without the refinement step, even ones with it when it applies
-  const bool refine = (gid & 1) == 0;
+  const float refine_band = (gid & 1) == 0 ? kRefineBand : __int_as_float(0x7f800000);
   auto seed64 = [&](int i) { return s64[i]; };
-  Hyp32 hy = hyp_f32<DIM>(r[0], r[1], DIM == 3 ? r[2] : r[0], seed64, refine, wmax, 0.0f, 0.0f, tau);
+  Hyp32 hy = hyp_f32<DIM>(r[0], r[1], DIM == 3 ? r[2] : r[0], seed64, refine_band, wmax, 0.0f, 0.0f, tau);
   if (hy.kind != kHypNormal) return;
   if (hy.refined) atomicAdd(&g_viol[3], 1ull);
   const double wd[3] = {w[0], w[1], DIM == 3 ? (double)w[2] : 0.0};
