@@ -838,10 +838,12 @@ __device__ void process_cluster(const FrameDesc& a, const Smem& S, ClusterShared
     // Trials with a wide band refine their velocity.  3D minimal sets are
     // often ill-conditioned and refine on the spot above kRefineBand.  2D ones
     // have |det| = |sin(t1 - t0)| and mostly narrow bands, whose few band
-    // points cost less than refining; those above tau / 32 (the seeds of a
-    // cluster of narrow azimuth extent, such as a far object) are queued and
-    // refined in a second pass, one per lane, so that a refining lane does not
-    // hold up a warp of trials that need none.
+    // points cost less than refining; those above tau / 32 are queued, and
+    // when they are at least an eighth of the chunk (a cluster of narrow
+    // azimuth extent, such as a far object, where nearly every seed pair is
+    // ill-conditioned) a second pass refines them, one per lane.  Elsewhere
+    // the pass's latency would cost more than the band points it saves;
+    // either way the decisions are exact.
     const float refine_band = DIM == 3 ? kRefineBand : a.tau32.hi * 0x1p-5f;
     auto cosine_trials = [&]() {
       for (int hl = tid; hl < nh; hl += kThreads) {
@@ -881,7 +883,7 @@ __device__ void process_cluster(const FrameDesc& a, const Smem& S, ClusterShared
       }
       if constexpr (DIM == 2) {
         __syncthreads();
-        const int nr = cs.nref;
+        const int nr = 8 * cs.nref >= nh ? cs.nref : 0;
         for (int i = tid; i < nr; i += kThreads) {
           const int hl = S.U[i];
           int q[3];
