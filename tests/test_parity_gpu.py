@@ -163,3 +163,39 @@ def test_seeds_change_draws(ctx):
         _check(G.compare(g, o, f.offsets))
         bests.append(g["best_hypothesis"])
     assert not np.array_equal(bests[0], bests[1])
+
+
+def _far_objects(n_clusters, gen_seed):
+    """Clusters of far objects: a few metres across at hundreds of metres span
+    0.1-0.6 deg of azimuth, so every minimal set is ill-conditioned
+    (|det| = |sin(t1 - t0)| < 0.01) and most trials take the 2D refinement
+    pass.  Doppler follows the velocity profile with N(0, 0.05) noise; 20%
+    are outliers."""
+    rng = np.random.default_rng(gen_seed)
+    az, dop, off = [], [], [0]
+    for c in range(n_clusters):
+        n = int(rng.integers(16, 400))
+        t0 = rng.uniform(-1.0, 1.0)
+        half = [0.001, 0.0025, 0.005][c % 3]
+        t = t0 + rng.uniform(-half, half, n)
+        vx, vy = rng.uniform(-30.0, 30.0, 2)
+        d = vx * np.cos(t) + vy * np.sin(t) + rng.normal(0.0, 0.05, n)
+        out = rng.random(n) < 0.2
+        d[out] = rng.uniform(-40.0, 40.0, out.sum())
+        az.append(t)
+        dop.append(d)
+        off.append(off[-1] + n)
+    return (np.concatenate(az).astype(np.float32), np.concatenate(dop).astype(np.float32),
+            np.asarray(off, np.int32))
+
+
+def test_narrow_azimuth_far_objects(ctx):
+    from paper_2012_12618_gb300 import rvh
+    import ctypes
+    az, dop, off = _far_objects(60, 41)
+    g = G.run_rvh(ctx, az, dop, off, H=1024, tau=0.1, seed=5)
+    st = rvh.rvh_stats()
+    assert rvh.load().rvh_get_stats(ctx.handle, ctypes.byref(st)) == rvh.RVH_OK
+    assert st.refined_hypotheses > 0  # the queued 2D refinement ran
+    o = G.run_oracle(az, dop, off, H=1024, tau=0.1, seed=5)
+    _check(G.compare(g, o, off))
