@@ -6,8 +6,10 @@ device memory); rvh_estimate_noalloc serves them from fixed file-scope device
 arrays.  This file is named to be collected last.  The test runs the new entry
 point twice in a row through the C ABI on the same frame and checks each
 result against the context-based rvh_estimate: masks, counts, winners and
-status bit-exact, velocities and heading within 1e-6.  It passes on its own in
-a fresh process and after the other tests.
+status bit-exact, velocities and heading within 1e-6; once with the plain
+method and once with each extension (local-optimisation rounds, the adaptive
+trial count, Alg. 1's line model).  It passes on its own in a fresh process
+and after the other tests.
 """
 import ctypes
 
@@ -25,7 +27,16 @@ def _to_np(outs, n_points):
     return out
 
 
-def test_noalloc_matches_estimate_twice():
+EXTENSIONS = {
+    "plain": {},
+    "local_opt": {"refine_iterations": 2},
+    "adaptive": {"confidence": 0.99, "trial_block": 128},
+    "paper_line": {"hypothesis_model": rvh.RVH_MODEL_PAPER_LINE},
+}
+
+
+@pytest.mark.parametrize("ext", list(EXTENSIONS))
+def test_noalloc_matches_estimate_twice(ext):
     torch = pytest.importorskip("torch")
     if not torch.cuda.is_available():
         pytest.skip("no CUDA device")
@@ -36,7 +47,7 @@ def test_noalloc_matches_estimate_twice():
     dop = torch.from_numpy(f.doppler).to(dev)
     off = torch.from_numpy(f.offsets).to(dev)
     frame = rvh.make_frame(az, dop, off)
-    params = rvh.make_params(2, w.num_hypotheses, w.tau, 7)
+    params = rvh.make_params(2, w.num_hypotheses, w.tau, 7, **EXTENSIONS[ext])
 
     ctx = rvh.Context(0)
     try:
