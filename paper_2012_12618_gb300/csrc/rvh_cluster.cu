@@ -19,14 +19,17 @@
 // around any cell land in 3^g distinct buckets and x - 1, x, x + 1 in
 // consecutive ones.  A counting sort lays the points out bucket by bucket
 // (features as float4 next to their original index): a point's candidates
-// are then a few contiguous spans.  One thread per sorted point; lanes of a
-// warp in one bucket walk their common spans together (coalesced tiles,
-// shuffles), other lanes walk alone with batched loads.  Neighbour counts;
-// then a lock-free union-find over core-core neighbour pairs on sorted
-// positions (a near-neighbour linking pass and a compression first, so the
-// full pass mostly meets pairs that already share a root) that links the
-// larger root under the smaller; an atomic minimum per component gives its
-// smallest core index; a device-wide scan numbers the clusters.  The CSR:
+// are then a few contiguous spans.  One thread per sorted point.  Neighbour
+// counts look in the point's own bucket first; the points still short of
+// min_pts, and the non-core points looking for their lowest-index core
+// neighbour, walk alone (batched loads) when their neighbourhood is small
+// and with the whole warp (coalesced tiles, ballots) when it is large.  Then
+// a lock-free union-find over core-core neighbour pairs on sorted positions:
+// a near-neighbour linking pass and a compression first, a root recorded
+// per bucket, and a full per-thread pass that skips buckets already in the
+// point's set; it links the larger root under the smaller.  An atomic
+// minimum per component gives its smallest core index; a device-wide scan
+// numbers the clusters.  The CSR:
 // per-cluster counts, offsets by a scan, placement, and a shared-memory sort
 // of each cluster's indices (a global bitonic sort of (cluster, index) keys
 // when a cluster exceeds one block's capacity).
@@ -159,7 +162,7 @@ __device__ __forceinline__ bool for_spans(const ClusterArgs& a, const Cell& c, i
 // positions t0 .. min(t0 + kChunk, end) - 1, issuing their loads together.
 constexpr int kChunk = 8;
 constexpr int kNoCore = (int)0xfefefefe;  // bucket root before any core point (memset pattern 0xfe)
-constexpr int kOwnCap = 64;  // own-bucket candidates a thread counts before the shared walk
+constexpr int kOwnCap = 64;  // own-bucket candidates a thread counts before the full walk
 template <int DIM, typename Chunk>
 __device__ __forceinline__ bool for_chunks(const ClusterArgs& a, const Cell& c, int limit, Chunk chunk) {
   return for_spans<DIM>(a, c, limit, [&](int b, int e) {
