@@ -165,6 +165,12 @@ typedef struct {
   int32_t* best_hypothesis;  /* winning trial index h, -1 if none */
   int32_t* status;           /* RVH_STATUS_* bits */
   uint8_t* inlier_mask;      /* 1 = inlier of its cluster's winning trial */
+  double* threshold;         /* optional, NULL: not written.  The inlier threshold
+                                each cluster used: tau, or with
+                                RVH_MODEL_PAPER_LINE the cluster's MAD threshold
+                                in the normalised plane (Eq. eq:MAD as
+                                med |y - med y|; NaN for a cluster with fewer
+                                than 2 points) */
 } rvh_result;
 
 /* Creates a context on CUDA device `device` with its own stream.

@@ -118,6 +118,7 @@ def estimate(azimuth, doppler, offsets, *, elevation=None, num_hypotheses: int, 
         "heading": np.full(n_out, np.nan),
         "inlier_count": np.zeros(n_out, np.int32), "best_hypothesis": np.zeros(n_out, np.int32),
         "status": np.zeros(n_out, np.int32), "inlier_mask": np.zeros(dp.shape[0], np.uint8),
+        "threshold": np.full(n_out, np.nan),
     }
     counts = np.zeros(n_out * H, np.int32) if want_counts else None
     fragile = np.zeros(n_out, np.uint8) if want_fragile else None
@@ -126,7 +127,7 @@ def estimate(azimuth, doppler, offsets, *, elevation=None, num_hypotheses: int, 
         _p(az), _p(el), _p(dp), _p(off), ctypes.c_int32(nc), _p(sub), ctypes.c_int32(n_out),
         ctypes.byref(p), _p(out["vx"]), _p(out["vy"]), _p(out["vz"]), _p(out["heading"]),
         _p(out["inlier_count"]), _p(out["best_hypothesis"]), _p(out["status"]),
-        _p(out["inlier_mask"]), _p(counts), _p(fragile), _p(trials))
+        _p(out["inlier_mask"]), _p(counts), _p(fragile), _p(trials), _p(out["threshold"]))
     if rc != 0:
         raise ValueError("oracle_estimate rejected its arguments")
     if want_counts:

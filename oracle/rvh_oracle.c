@@ -206,7 +206,8 @@ int oracle_estimate(const double* azimuth, const double* elevation, const double
                     const int32_t* subset, int32_t n_subset, const orc_params* p,
                     double* vx, double* vy, double* vz, double* heading,
                     int32_t* inlier_count, int32_t* best_hypothesis, int32_t* status,
-                    uint8_t* mask, int32_t* hyp_counts, uint8_t* fragile, int32_t* trials_used) {
+                    uint8_t* mask, int32_t* hyp_counts, uint8_t* fragile, int32_t* trials_used,
+                    double* threshold) {
   if (!p || !offsets || !azimuth || !doppler || n_clusters < 0) return -1;
   const int k = p->model_dim;
   if (k != 2 && k != 3) return -1;
@@ -226,6 +227,7 @@ int oracle_estimate(const double* azimuth, const double* elevation, const double
     const int32_t n = (int32_t)(offsets[ci + 1] - offsets[ci]);
     if (fragile) fragile[oi] = 0;
     if (trials_used) trials_used[oi] = 0;
+    if (threshold) threshold[oi] = p->line_model ? NAN : tau;
     for (int32_t q = 0; q < n; ++q) mask[o + q] = 0;
     if (hyp_counts)
       for (int32_t h = 0; h < H; ++h) hyp_counts[(int64_t)oi * H + h] = -1;
@@ -288,6 +290,7 @@ int oracle_estimate(const double* azimuth, const double* elevation, const double
       for (int32_t q = 0; q < n; ++q) tmp[q] = fabs(yn[q] - med);
       thresh = median(tmp, n);
       free(tmp);
+      if (threshold) threshold[oi] = thresh;
     }
 
     /* Alg. 1 for every trial h: draw the minimal set, solve it, count the

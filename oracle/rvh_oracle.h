@@ -101,13 +101,17 @@ int oracle_draw(uint64_t seed, int32_t cluster, int32_t h, int32_t n, int32_t k,
  * fragile (optional) receives 1 for a cluster where some decision that can
  * change the outputs lies within rounding distance of its threshold.
  * trials_used (optional) receives the number of trials run per cluster.
+ * threshold (optional) receives the inlier threshold each cluster used: tau,
+ * or with line_model the cluster's MAD threshold (NaN for a cluster with
+ * fewer than k points, which has none).
  * Returns 0, or -1 on invalid arguments. */
 int oracle_estimate(const double* azimuth, const double* elevation, const double* doppler,
                     const int32_t* offsets, int32_t n_clusters,
                     const int32_t* subset, int32_t n_subset, const orc_params* p,
                     double* vx, double* vy, double* vz, double* heading,
                     int32_t* inlier_count, int32_t* best_hypothesis, int32_t* status,
-                    uint8_t* mask, int32_t* hyp_counts, uint8_t* fragile, int32_t* trials_used);
+                    uint8_t* mask, int32_t* hyp_counts, uint8_t* fragile, int32_t* trials_used,
+                    double* threshold);
 
 /* DBSCAN over n feature vectors of `dim` (1..4) FP64 components (row-major):
  * the clustering stage of Fig. 1 that forms the clusters the estimator takes.

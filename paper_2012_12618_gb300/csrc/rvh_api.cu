@@ -20,7 +20,25 @@
 #include "rvh.h"
 #include "rvh_kernels.h"
 #include "rvh_cluster.h"
+#include "rvh_outputs.h"
 #include "rvh_runtime.h"
+
+namespace rvh {
+
+__global__ void k_fill_f64(double* p, int32_t n, double v) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i < n) p[i] = v;
+}
+
+cudaError_t launch_threshold_fill(double* threshold, int32_t n_clusters, bool line_model, double tau,
+                                  cudaStream_t s) {
+  if (!threshold || n_clusters <= 0) return cudaSuccess;
+  const double v = line_model ? __builtin_nan("") : tau;
+  k_fill_f64<<<(unsigned)((n_clusters + 255) / 256), 256, 0, s>>>(threshold, n_clusters, v);
+  return cudaGetLastError();
+}
+
+}  // namespace rvh
 
 namespace {
 
@@ -243,6 +261,7 @@ void fill_desc(rvh_ctx* ctx, FrameDesc& d, const rvh_frame& f, const rvh_params&
   d.best = out.best_hypothesis;
   d.status = out.status;
   d.mask = out.inlier_mask;
+  d.threshold = out.threshold;
 }
 
 int configure_dim(rvh_ctx* ctx, int dim) {
@@ -547,7 +566,7 @@ struct Staged {
   const float *az, *el, *dop;
   const int32_t* off;
   rvh_result dev_out;       // device pointers the kernel writes
-  bool host_out[8];
+  bool host_out[rvh::kOutputs];
   bool staged_any;          // some input or output went through host memory
   char* base;
   int2* worklist;
@@ -569,11 +588,11 @@ static int stage(rvh_ctx* ctx, const rvh_frame* f, const rvh_params* p, rvh_resu
     int rc = check_host_offsets(f->cluster_offsets, nc, np);
     if (rc) return rc;
   }
-  void* outs[8] = {r->vx, r->vy, r->vz, r->heading, r->inlier_count, r->best_hypothesis, r->status, r->inlier_mask};
-  const size_t osz[8] = {8, 8, 8, 8, 4, 4, 4, 1};
-  for (int i = 0; i < 8; ++i) st.host_out[i] = outs[i] && !is_device_ptr(outs[i]);
+  void* outs[rvh::kOutputs];
+  rvh::result_ptrs(*r, outs);
+  for (int i = 0; i < rvh::kOutputs; ++i) st.host_out[i] = outs[i] && !is_device_ptr(outs[i]);
   st.staged_any = !(d_az && d_dop && d_el && d_off);
-  for (int i = 0; i < 8; ++i) st.staged_any = st.staged_any || st.host_out[i];
+  for (int i = 0; i < rvh::kOutputs; ++i) st.staged_any = st.staged_any || st.host_out[i];
   // layout
   size_t off = 0;
   auto take = [&](size_t bytes) {
@@ -590,10 +609,10 @@ static int stage(rvh_ctx* ctx, const rvh_frame* f, const rvh_params* p, rvh_resu
   const size_t o_el = d_el ? 0 : take(4 * (size_t)np);
   const size_t o_dop = d_dop ? 0 : take(4 * (size_t)np);
   const size_t o_off = d_off ? 0 : take(4 * (size_t)(nc + 1));
-  size_t o_out[8];
-  for (int i = 0; i < 8; ++i) {
-    const size_t n = (i == 7) ? (size_t)np : (size_t)nc;
-    o_out[i] = st.host_out[i] ? take(osz[i] * std::max<size_t>(n, 1)) : 0;
+  size_t o_out[rvh::kOutputs];
+  for (int i = 0; i < rvh::kOutputs; ++i) {
+    const size_t n = (i == rvh::kMaskOutput) ? (size_t)np : (size_t)nc;
+    o_out[i] = st.host_out[i] ? take(rvh::kOutputSize[i] * std::max<size_t>(n, 1)) : 0;
   }
   if (off > ctx->scratch_bytes) {
     // wait for earlier work that may still use the old scratch
@@ -623,29 +642,24 @@ static int stage(rvh_ctx* ctx, const rvh_frame* f, const rvh_params* p, rvh_resu
     if (!d_dop) RVH_CUDA(cudaMemcpyAsync((void*)st.dop, f->doppler, 4 * np, cudaMemcpyHostToDevice, s));
   }
   if (!d_off) RVH_CUDA(cudaMemcpyAsync((void*)st.off, f->cluster_offsets, 4 * (size_t)(nc + 1), cudaMemcpyHostToDevice, s));
-  void* dev[8];
-  for (int i = 0; i < 8; ++i) dev[i] = st.host_out[i] ? (void*)(b + o_out[i]) : outs[i];
-  st.dev_out.vx = (double*)dev[0];
-  st.dev_out.vy = (double*)dev[1];
-  st.dev_out.vz = (double*)dev[2];
-  st.dev_out.heading = (double*)dev[3];
-  st.dev_out.inlier_count = (int32_t*)dev[4];
-  st.dev_out.best_hypothesis = (int32_t*)dev[5];
-  st.dev_out.status = (int32_t*)dev[6];
-  st.dev_out.inlier_mask = (uint8_t*)dev[7];
+  void* dev[rvh::kOutputs];
+  for (int i = 0; i < rvh::kOutputs; ++i) dev[i] = st.host_out[i] ? (void*)(b + o_out[i]) : outs[i];
+  st.dev_out = rvh::result_from(dev);
+  RVH_CUDA(rvh::launch_threshold_fill(st.dev_out.threshold, nc, p->hypothesis_model == RVH_MODEL_PAPER_LINE,
+                                      p->inlier_threshold, s));
   return RVH_OK;
 }
 
 static int unstage(const rvh_frame* f, rvh_result* r, const Staged& st, cudaStream_t s) {
-  void* outs[8] = {r->vx, r->vy, r->vz, r->heading, r->inlier_count, r->best_hypothesis, r->status, r->inlier_mask};
-  void* dev[8] = {st.dev_out.vx, st.dev_out.vy, st.dev_out.vz, st.dev_out.heading, st.dev_out.inlier_count,
-                  st.dev_out.best_hypothesis, st.dev_out.status, st.dev_out.inlier_mask};
-  const size_t osz[8] = {8, 8, 8, 8, 4, 4, 4, 1};
+  void* outs[rvh::kOutputs];
+  void* dev[rvh::kOutputs];
+  rvh::result_ptrs(*r, outs);
+  rvh::result_ptrs(st.dev_out, dev);
   bool any = false;
-  for (int i = 0; i < 8; ++i) {
+  for (int i = 0; i < rvh::kOutputs; ++i) {
     if (!st.host_out[i]) continue;
-    const size_t n = (i == 7) ? (size_t)f->n_points : (size_t)f->n_clusters;
-    if (n) RVH_CUDA(cudaMemcpyAsync(outs[i], dev[i], osz[i] * n, cudaMemcpyDeviceToHost, s));
+    const size_t n = (i == rvh::kMaskOutput) ? (size_t)f->n_points : (size_t)f->n_clusters;
+    if (n) RVH_CUDA(cudaMemcpyAsync(outs[i], dev[i], rvh::kOutputSize[i] * n, cudaMemcpyDeviceToHost, s));
     any = true;
   }
   if (any) RVH_CUDA(cudaStreamSynchronize(s));

@@ -806,8 +806,12 @@ __device__ void process_cluster(const FrameDesc& a, const Smem& S, ClusterShared
     }
   };
   if constexpr (EXT && DIM == 2) {
-    if (a.line_model) line_rows_and_threshold<RV>(a, rows, R.pre, o, N, S.U, cs);
-    else cosine_rows();
+    if (a.line_model) {
+      line_rows_and_threshold<RV>(a, rows, R.pre, o, N, S.U, cs);
+      if (tid == 0 && a.threshold) a.threshold[ci] = cs.ln_T;  // the API wrote NaN before
+    } else {
+      cosine_rows();
+    }
   } else {
     cosine_rows();
   }

@@ -47,6 +47,7 @@ struct FrameDesc {
   int32_t* best;
   int32_t* status;
   uint8_t* mask;
+  double* threshold;         // optional per-cluster threshold output (line model: the MAD threshold)
 };
 
 constexpr int kMaxBatchFrames = 32;

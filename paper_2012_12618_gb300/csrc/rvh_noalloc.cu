@@ -16,6 +16,7 @@
 
 #include "rvh.h"
 #include "rvh_kernels.h"
+#include "rvh_outputs.h"
 #include "rvh_runtime.h"
 
 namespace {
@@ -128,6 +129,8 @@ extern "C" int rvh_estimate_noalloc(const rvh_frame* f, const rvh_params* p, rvh
   for (const void* q : ptrs)
     if (!q || !rvh::device_ptr(q)) return rvh::set_error(RVH_EINVAL, "every input and output must be device memory");
   if (r->vz && !rvh::device_ptr(r->vz)) return rvh::set_error(RVH_EINVAL, "vz must be device memory or NULL");
+  if (r->threshold && !rvh::device_ptr(r->threshold))
+    return rvh::set_error(RVH_EINVAL, "threshold must be device memory or NULL");
 
   int dev = 0;
   cudaError_t e = cudaGetDevice(&dev);
@@ -172,6 +175,7 @@ extern "C" int rvh_estimate_noalloc(const rvh_frame* f, const rvh_params* p, rvh
   fd.best = r->best_hypothesis;
   fd.status = r->status;
   fd.mask = r->inlier_mask;
+  fd.threshold = r->threshold;
   a.n_frames = 1;
   a.n_items = f->n_clusters;
   a.worklist = (int2*)d->scratch;
@@ -190,7 +194,8 @@ extern "C" int rvh_estimate_noalloc(const rvh_frame* f, const rvh_params* p, rvh
   cudaStream_t s = (cudaStream_t)stream;
   const int resident = d->sms * d->occ[dim];
   a.direct = a.n_items <= resident ? 1 : 0;
-  e = a.direct ? cudaSuccess : rvh::launch_worklist(a, s);
+  e = rvh::launch_threshold_fill(r->threshold, f->n_clusters, fd.line_model != 0, p->inlier_threshold, s);
+  if (e == cudaSuccess && !a.direct) e = rvh::launch_worklist(a, s);
   if (e == cudaSuccess) {
     const int grid = std::max(1, std::min(resident, a.n_items));
     e = rvh::launch_fused(dim, a, grid, rvh::fused_smem_bytes(kNmaxSmem, kHchunk), s);

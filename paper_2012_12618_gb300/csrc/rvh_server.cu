@@ -19,6 +19,7 @@
 
 #include "rvh.h"
 #include "rvh_kernels.h"
+#include "rvh_outputs.h"
 #include "rvh_runtime.h"
 
 namespace rvh {
@@ -83,10 +84,10 @@ struct Req {
   rvh_params params{};
   rvh_result user{};        // caller's outputs
   rvh_result dev{};         // where the kernel writes
-  bool host_out[8] = {};
+  bool host_out[kOutputs] = {};
   size_t dev_off = 0, dev_bytes = 0;
   size_t pin_off = 0, pin_bytes = 0;
-  size_t pin_out[8] = {};
+  size_t pin_out[kOutputs] = {};
   size_t rows64_off = 0;
   cudaEvent_t copied = nullptr;  // host inputs are on the device
   int step = -1;
@@ -129,18 +130,6 @@ struct Server {
   void loop();
 };
 
-static const size_t kOutSz[8] = {8, 8, 8, 8, 4, 4, 4, 1};
-
-static void out_ptrs(const rvh_result& r, void* p[8]) {
-  p[0] = r.vx;
-  p[1] = r.vy;
-  p[2] = r.vz;
-  p[3] = r.heading;
-  p[4] = r.inlier_count;
-  p[5] = r.best_hypothesis;
-  p[6] = r.status;
-  p[7] = r.inlier_mask;
-}
 
 int server_create(rvh_ctx* ctx, Server** out) {
   Server* s = new Server();
@@ -222,9 +211,9 @@ int server_submit(Server* s, const rvh_frame* f, const rvh_params* p, rvh_result
   auto q = std::make_unique<Req>();
   q->params = *p;
   q->user = *r;
-  void* uo[8];
-  out_ptrs(*r, uo);
-  for (int i = 0; i < 8; ++i) q->host_out[i] = uo[i] && !device_ptr(uo[i]);
+  void* uo[kOutputs];
+  result_ptrs(*r, uo);
+  for (int i = 0; i < kOutputs; ++i) q->host_out[i] = uo[i] && !device_ptr(uo[i]);
   const bool d_az = device_ptr(f->azimuth), d_dop = device_ptr(f->doppler);
   const bool d_el = !dim3 || device_ptr(f->elevation);
   const bool d_off = nc == 0 || device_ptr(f->cluster_offsets);
@@ -242,14 +231,14 @@ int server_submit(Server* s, const rvh_frame* f, const rvh_params* p, rvh_result
   const size_t o_el = d_el ? 0 : take(4 * (size_t)np);
   const size_t o_dop = d_dop ? 0 : take(4 * (size_t)np);
   const size_t o_off = d_off ? 0 : take(4 * (size_t)(nc + 1));
-  size_t o_out[8];
+  size_t o_out[kOutputs];
   size_t pin = 0;
-  for (int i = 0; i < 8; ++i) {
-    const size_t n = (i == 7) ? (size_t)np : (size_t)nc;
-    o_out[i] = q->host_out[i] ? take(kOutSz[i] * std::max<size_t>(n, 1)) : 0;
+  for (int i = 0; i < kOutputs; ++i) {
+    const size_t n = (i == kMaskOutput) ? (size_t)np : (size_t)nc;
+    o_out[i] = q->host_out[i] ? take(kOutputSize[i] * std::max<size_t>(n, 1)) : 0;
     if (q->host_out[i]) {
       q->pin_out[i] = pin;
-      pin += gran(kOutSz[i] * std::max<size_t>(n, 1));
+      pin += gran(kOutputSize[i] * std::max<size_t>(n, 1));
     }
   }
   {
@@ -287,16 +276,9 @@ int server_submit(Server* s, const rvh_frame* f, const rvh_params* p, rvh_result
   if (e == cudaSuccess) e = cudaEventRecord(q->copied, s->copy_stream);
   // the caller may reuse its host input buffers once this returns
   if (e == cudaSuccess) e = cudaStreamSynchronize(s->copy_stream);
-  void* dv[8];
-  for (int i = 0; i < 8; ++i) dv[i] = q->host_out[i] ? (void*)(b + o_out[i]) : uo[i];
-  q->dev.vx = (double*)dv[0];
-  q->dev.vy = (double*)dv[1];
-  q->dev.vz = (double*)dv[2];
-  q->dev.heading = (double*)dv[3];
-  q->dev.inlier_count = (int32_t*)dv[4];
-  q->dev.best_hypothesis = (int32_t*)dv[5];
-  q->dev.status = (int32_t*)dv[6];
-  q->dev.inlier_mask = (uint8_t*)dv[7];
+  void* dv[kOutputs];
+  for (int i = 0; i < kOutputs; ++i) dv[i] = q->host_out[i] ? (void*)(b + o_out[i]) : uo[i];
+  q->dev = result_from(dv);
   std::lock_guard<std::mutex> lk(s->mu);
   if (e != cudaSuccess) {
     cudaGetLastError();
@@ -319,12 +301,12 @@ int Server::finalize_step(Step& st) {
     auto it = reqs.find(id);
     if (it == reqs.end()) continue;
     Req& q = *it->second;
-    void* uo[8];
-    out_ptrs(q.user, uo);
-    for (int i = 0; i < 8; ++i) {
+    void* uo[kOutputs];
+    result_ptrs(q.user, uo);
+    for (int i = 0; i < kOutputs; ++i) {
       if (!q.host_out[i]) continue;
-      const size_t n = (i == 7) ? (size_t)q.frame.n_points : (size_t)q.frame.n_clusters;
-      if (n) memcpy(uo[i], pinned + q.pin_off + q.pin_out[i], kOutSz[i] * n);
+      const size_t n = (i == kMaskOutput) ? (size_t)q.frame.n_points : (size_t)q.frame.n_clusters;
+      if (n) memcpy(uo[i], pinned + q.pin_off + q.pin_out[i], kOutputSize[i] * n);
     }
     dev_arena.release(q.dev_off, q.dev_bytes);
     if (q.pin_bytes) pin_arena.release(q.pin_off, q.pin_bytes);
@@ -412,6 +394,10 @@ void Server::loop() {
       fill_desc(ctx, a.f[nf], q.frame, q.params, q.frame.azimuth, q.frame.elevation, q.frame.doppler,
                 q.frame.cluster_offsets, (float4*)b, (double4_32a*)(b + q.rows64_off), q.dev);
       cudaStreamWaitEvent(slot->stream, q.copied, 0);
+      if (launch_threshold_fill(q.dev.threshold, q.frame.n_clusters,
+                                q.params.hypothesis_model == RVH_MODEL_PAPER_LINE, q.params.inlier_threshold,
+                                slot->stream) != cudaSuccess)
+        thread_error = "threshold fill failed";
       ++nf;
     }
     a.n_frames = nf;
@@ -429,13 +415,13 @@ void Server::loop() {
     // outputs that go to host memory: device -> pinned staging
     for (uint64_t id : take) {
       Req& q = *reqs[id];
-      void* dv[8];
-      out_ptrs(q.dev, dv);
-      for (int i = 0; i < 8; ++i) {
+      void* dv[kOutputs];
+      result_ptrs(q.dev, dv);
+      for (int i = 0; i < kOutputs; ++i) {
         if (!q.host_out[i]) continue;
-        const size_t n = (i == 7) ? (size_t)q.frame.n_points : (size_t)q.frame.n_clusters;
-        if (n) cudaMemcpyAsync(pinned + q.pin_off + q.pin_out[i], dv[i], kOutSz[i] * n, cudaMemcpyDeviceToHost,
-                               slot->stream);
+        const size_t n = (i == kMaskOutput) ? (size_t)q.frame.n_points : (size_t)q.frame.n_clusters;
+        if (n) cudaMemcpyAsync(pinned + q.pin_off + q.pin_out[i], dv[i], kOutputSize[i] * n,
+                               cudaMemcpyDeviceToHost, slot->stream);
       }
       q.state = 1;
     }

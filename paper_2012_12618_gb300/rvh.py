@@ -50,7 +50,7 @@ class rvh_result(ctypes.Structure):
     _fields_ = [("vx", ctypes.c_void_p), ("vy", ctypes.c_void_p), ("vz", ctypes.c_void_p),
                 ("heading", ctypes.c_void_p), ("inlier_count", ctypes.c_void_p),
                 ("best_hypothesis", ctypes.c_void_p), ("status", ctypes.c_void_p),
-                ("inlier_mask", ctypes.c_void_p)]
+                ("inlier_mask", ctypes.c_void_p), ("threshold", ctypes.c_void_p)]
 
 
 class rvh_schedule(ctypes.Structure):
@@ -204,14 +204,15 @@ def make_params(model_dim: int, num_hypotheses: int, inlier_threshold: float, se
 def make_result(out: dict) -> rvh_result:
     return rvh_result(ptr(out["vx"]), ptr(out["vy"]), ptr(out.get("vz")), ptr(out["heading"]),
                       ptr(out["inlier_count"]), ptr(out["best_hypothesis"]), ptr(out["status"]),
-                      ptr(out["inlier_mask"]))
+                      ptr(out["inlier_mask"]), ptr(out.get("threshold")))
 
 
-def alloc_outputs(n_clusters: int, n_points: int, device="cuda") -> dict:
-    """Result buffers as torch tensors on `device` ("cpu" gives host memory)."""
+def alloc_outputs(n_clusters: int, n_points: int, device="cuda", threshold: bool = False) -> dict:
+    """Result buffers as torch tensors on `device` ("cpu" gives host memory);
+    threshold=True adds the optional per-cluster threshold output."""
     import torch
     kw = dict(device=device)
-    return {
+    out = {
         "vx": torch.empty(n_clusters, dtype=torch.float64, **kw),
         "vy": torch.empty(n_clusters, dtype=torch.float64, **kw),
         "vz": torch.empty(n_clusters, dtype=torch.float64, **kw),
@@ -221,6 +222,9 @@ def alloc_outputs(n_clusters: int, n_points: int, device="cuda") -> dict:
         "status": torch.empty(n_clusters, dtype=torch.int32, **kw),
         "inlier_mask": torch.empty(max(n_points, 1), dtype=torch.uint8, **kw),
     }
+    if threshold:
+        out["threshold"] = torch.empty(n_clusters, dtype=torch.float64, **kw)
+    return out
 
 
 class Context:

@@ -418,12 +418,20 @@ def check_adaptive(L):
     assert o["trials_used"][0] == 32 and o["inlier_count"][0] == 50
 
 
+def _mad_threshold(th, dop):
+    """Alg. 1's threshold with numpy: min-max normalised Doppler, then the
+    median of its absolute deviations from its median."""
+    dop = np.asarray(dop, np.float64)
+    y = (dop - dop.min()) * (1.0 / (dop.max() - dop.min())) if dop.max() > dop.min() else np.zeros_like(dop)
+    return np.median(np.abs(y - np.median(y)))
+
+
 def _line_brute(th, dop):
     """Alg. 1 by exhaustion with numpy: counts of every seed pair (lexicographic),
     the MAD threshold, and the smallest decision margin."""
     x = (th - th.min()) * (1.0 / (th.max() - th.min())) if th.max() > th.min() else np.zeros_like(th)
     y = (dop - dop.min()) * (1.0 / (dop.max() - dop.min())) if dop.max() > dop.min() else np.zeros_like(dop)
-    T = np.median(np.abs(y - np.median(y)))
+    T = _mad_threshold(th, dop)
     counts, margin = [], np.inf
     for a, b in itertools.combinations(range(th.shape[0]), 2):
         dx, dy = x[b] - x[a], y[b] - y[a]
@@ -455,6 +463,7 @@ def check_paper_line(L):
                  want_counts=True, line_model=True)
         assert np.array_equal(o["hyp_counts"][0], counts), (o["hyp_counts"][0], counts)
         assert o["best_hypothesis"][0] == int(np.argmax(counts))
+        assert o["threshold"][0] == T  # the MAD threshold, numpy's median of |y - median y|
         done += 1
     # frames: refine = lstsq of the inliers; Doppler x 2^m exact; shapes of the outputs
     w, f = _frame("stress2d", 64)
@@ -472,6 +481,12 @@ def check_paper_line(L):
             assert np.allclose([o["vx"][c], o["vy"][c]], ref, rtol=1e-9, atol=1e-9), c
             checked += 1
     assert checked >= 60
+    for c in range(64):  # each cluster's MAD threshold, as numpy forms it
+        s_, e_ = f.offsets[c], f.offsets[c + 1]
+        assert o["threshold"][c] == _mad_threshold(f.azimuth[s_:e_], dop[s_:e_]), c
+    # the cosine model reports tau for every cluster
+    cos_o = _est(L, f.azimuth, f.doppler, f.offsets, num_hypotheses=8, tau=w.tau, seed=5)
+    assert np.all(cos_o["threshold"] == w.tau)
     sc = _est(L, f.azimuth, dop * 4.0, f.offsets, want_counts=True, **kw)
     assert np.array_equal(o["hyp_counts"], sc["hyp_counts"]) and np.array_equal(o["inlier_mask"], sc["inlier_mask"])
     assert np.array_equal(o["vx"] * 4.0, sc["vx"]) and np.array_equal(o["vy"] * 4.0, sc["vy"])

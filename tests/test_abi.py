@@ -74,3 +74,25 @@ def test_params_layout_and_refine_range():
         assert rvh.rvh_estimate_noalloc(f, p, r, None) == rvh.RVH_EINVAL
         msg = rvh.rvh_last_error(None)
         assert "hypothesis_model" in msg or "model_dim" in msg, msg
+
+
+def test_result_layout_matches_the_header(tmp_path):
+    """rvh_result as the C compiler lays it out (offsetof through gcc) equals
+    the binding's ctypes structure, the optional threshold output included."""
+    import shutil
+    import subprocess
+    cc = shutil.which("gcc") or shutil.which("cc")
+    if cc is None:
+        pytest.skip("no C compiler")
+    src = tmp_path / "layout.c"
+    src.write_text(
+        '#include <stddef.h>\n#include <stdio.h>\n#include "rvh.h"\n'
+        'int main(void) { printf("%zu %zu %zu\\n", sizeof(rvh_result), offsetof(rvh_result, inlier_mask),'
+        ' offsetof(rvh_result, threshold)); return 0; }\n')
+    exe = tmp_path / "layout"
+    inc = os.path.join(os.path.dirname(os.path.dirname(os.path.abspath(__file__))), "include")
+    subprocess.run([cc, "-I", inc, str(src), "-o", str(exe)], check=True)
+    size, mask_off, thr_off = map(int, subprocess.run([str(exe)], check=True, capture_output=True,
+                                                      text=True).stdout.split())
+    assert size == ctypes.sizeof(rvh.rvh_result)
+    assert mask_off == rvh.rvh_result.inlier_mask.offset and thr_off == rvh.rvh_result.threshold.offset

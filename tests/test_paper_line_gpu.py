@@ -98,3 +98,52 @@ def test_baseline_rejects_line_model(ctx):
     f = synth.make_frame(w, n_clusters=4, gen_seed=74)
     with pytest.raises(RuntimeError, match="-1"):
         G.run_rvh(ctx, f.azimuth, f.doppler, f.offsets, H=16, tau=0.1, seed=1, baseline=True, line_model=True)
+
+
+def test_threshold_output_on_every_entry_point(ctx):
+    """The optional per-cluster threshold output: each cluster's MAD threshold
+    under Alg. 1 (bit-exact against the oracle's, NaN for clusters of one
+    point) and tau under the cosine model, through rvh_estimate with device
+    and host buffers, the serving path and the allocation-free call."""
+    import ctypes
+    import torch
+    from paper_2012_12618_gb300 import rvh
+    w = synth.WORKLOADS["stress2d"]
+    f = synth.make_frame(w, n_clusters=96, gen_seed=w.gen_seed + 900)
+    # a cluster of one point at the end: it has no threshold
+    az = np.concatenate([f.azimuth, np.float32([0.3])])
+    dop = np.concatenate([f.doppler, np.float32([1.5])])
+    off = np.concatenate([f.offsets, np.int32([f.offsets[-1] + 1])]).astype(np.int32)
+    nc, npts = off.shape[0] - 1, az.shape[0]
+    want = G.run_oracle(az, dop, off, H=64, tau=0.1, seed=3, line_model=True)["threshold"]
+    assert np.isnan(want[-1]) and np.isfinite(want[:-1]).all()
+    dev = torch.device("cuda", 0)
+    t = {k: torch.from_numpy(v).to(dev) for k, v in (("az", az), ("dop", dop), ("off", off))}
+    frame = rvh.make_frame(t["az"], t["dop"], t["off"])
+    line = rvh.make_params(2, 64, 0.1, 3, hypothesis_model=rvh.RVH_MODEL_PAPER_LINE)
+    cosine = rvh.make_params(2, 64, 0.1, 3)
+
+    def same(got, ref):
+        got = np.asarray(got)
+        assert np.array_equal(np.isnan(got), np.isnan(ref)) and np.array_equal(got[~np.isnan(ref)],
+                                                                              ref[~np.isnan(ref)])
+
+    for device in ("cuda", "cpu"):  # device buffers, then host buffers (staged)
+        outs = rvh.alloc_outputs(nc, npts, device, threshold=True)
+        ctx.check(rvh.rvh_estimate(ctx.handle, frame, line, rvh.make_result(outs), None), "estimate")
+        torch.cuda.synchronize()
+        same(outs["threshold"].cpu().numpy(), want)
+        ctx.check(rvh.rvh_estimate(ctx.handle, frame, cosine, rvh.make_result(outs), None), "estimate")
+        torch.cuda.synchronize()
+        assert (outs["threshold"].cpu().numpy() == 0.1).all()
+    # serving path, host outputs
+    outs = rvh.alloc_outputs(nc, npts, "cpu", threshold=True)
+    tk = ctypes.c_uint64(0)
+    ctx.check(rvh.rvh_submit(ctx.handle, frame, line, rvh.make_result(outs), tk), "submit")
+    assert rvh.rvh_wait(ctx.handle, tk, 30_000_000) == rvh.RVH_OK, rvh.rvh_last_error(None)
+    same(outs["threshold"].numpy(), want)
+    # allocation-free call, device outputs
+    outs = rvh.alloc_outputs(nc, npts, dev, threshold=True)
+    assert rvh.rvh_estimate_noalloc(frame, line, rvh.make_result(outs), None) == rvh.RVH_OK
+    torch.cuda.synchronize()
+    same(outs["threshold"].cpu().numpy(), want)
