@@ -14,7 +14,7 @@
  * may load or call this library.  The CUDA product path shares no code with
  * it and never calls it.
  *
- * Readings of the paper used here (each one is also listed in the design doc):
+ * Readings of the paper used here:
  *   - hypotheses are exact minimal-set solves of the cosine model (2 points in
  *     2D, 3 points in 3D), not the line fit in a normalised plane of Alg. 1;
  *   - the residual is the Doppler residual |v_d - a.v| with the test

@@ -205,7 +205,7 @@ constexpr unsigned kFull = 0xffffffffu;
 
 // The whole warp walks the candidates of one point (cell cl, warp-uniform)
 // kCoopW * 32 at a time: tile(base, end) runs on every lane, lane l taking
-// positions base + 32 w + l below end, and returns a warp-uniform verdict
+// positions base + 32 w + l below end, and returns a warp-uniform decision
 // (false ends the walk).  For the few points that need a long walk alone.
 constexpr int kCoopW = 4;
 template <int DIM, typename Tile>
