@@ -493,7 +493,7 @@ def main():
         t0 = time.perf_counter()
         ctx.check(rvh.rvh_estimate(ctx.handle, h_frame, params, h_res, sptr), "rvh_estimate(host)")
         e2e_t.append(time.perf_counter() - t0)
-    h2d = npts * 4 * (dim + 1) + (nc + 1) * 4
+    h2d = npts * 4 * dim + (nc + 1) * 4  # azimuth, Doppler (and elevation in 3D), offsets
     d2h = nc * (4 * 8 + 3 * 4) + npts
     e2e = {"value": nc / float(np.mean(e2e_t)), "unit": "clusters/s", "h2d_bytes_per_step": h2d,
            "d2h_bytes_per_step": d2h, "ms_per_step": 1e3 * float(np.mean(e2e_t))}
