@@ -199,3 +199,33 @@ def test_narrow_azimuth_far_objects(ctx):
     assert st.refined_hypotheses > 0  # the queued 2D refinement ran
     o = G.run_oracle(az, dop, off, H=1024, tau=0.1, seed=5)
     _check(G.compare(g, o, off))
+
+
+@pytest.mark.parametrize("name,nc,kw", [("dense2d", 400, {}), ("dense3d", 160, {}),
+                                        ("stress2d", 300, {"hypothesis_model": 1}),
+                                        ("dense2d", 256, {"first_cluster": 77, "refine_iterations": 1})])
+def test_host_frames_equal_device_frames(ctx, name, nc, kw):
+    """A frame and its results in host memory (staged through the context's
+    scratch) give every output, the threshold array included, exactly as
+    the same frame in device memory; with extensions and a first_cluster
+    offset too."""
+    import torch
+    from paper_2012_12618_gb300 import rvh
+    w = synth.WORKLOADS[name]
+    f = synth.make_frame(w, n_clusters=nc, gen_seed=w.gen_seed + 1300)
+    dim = 3 if f.elevation is not None else 2
+    params = rvh.make_params(dim, 256, w.tau, 9, **kw)
+    dev = torch.device("cuda", 0)
+    results = []
+    for where in (dev, "cpu"):
+        # the frame holds raw pointers: keep its tensors alive until the call is done
+        ins = [None if a is None else torch.from_numpy(a).to(where)
+               for a in (f.azimuth, f.doppler, f.offsets, f.elevation)]
+        frame = rvh.make_frame(*ins)
+        outs = rvh.alloc_outputs(f.n_clusters, f.n_points, where, threshold=True)
+        ctx.check(rvh.rvh_estimate(ctx.handle, frame, params, rvh.make_result(outs), None), "estimate")
+        torch.cuda.synchronize()
+        results.append({k: v.cpu().numpy() for k, v in outs.items()})
+    for k in results[0]:
+        assert np.array_equal(results[0][k][:f.n_points if k == "inlier_mask" else None],
+                              results[1][k][:f.n_points if k == "inlier_mask" else None], equal_nan=True), k
