@@ -34,6 +34,8 @@ MUTANTS = {
                       "      } while (0);",
                       "        if (count >= best_count) {\n          best_count = count;\n          best = h;\n        }\n"
                       "      } while (0);"),
+    "line_threshold_reports_median": ("      if (threshold) threshold[oi] = thresh;",
+                                      "      if (threshold) threshold[oi] = med;"),
     "line_tiebreak_last": ("          if (count > best_count) {\n            best_count = count;",
                            "          if (count >= best_count) {\n            best_count = count;"),
     "refine_wrong_product": ("G[r][c] = fma(aq[r], aq[c], G[r][c]);",
