@@ -33,6 +33,13 @@ violation.  What pins what:
               cluster ids follow the smallest core index; min_pts = 1 gives
               the connected components of the eps-graph (scipy); permuting
               the input permutes the result
+  fragile     the oracle's log of decisions within rounding distance of a
+              threshold (the only place a last-ulp difference of cos/sin
+              could flip a decision): an extra point planted within a few
+              ulps of tau, or a minimal set whose |det| is within a few ulps
+              of cond_eps, is flagged; the same planted 1e-9 m/s (or a
+              relative 1e-6) away is not; no cluster of the full frame64 and
+              dense2d frames is flagged
   local_opt   the re-threshold + re-fit rounds: one round's inlier set is
               numpy's re-threshold of the refined velocity, every result is
               numpy.linalg.lstsq of its own inlier set, a converged result is
@@ -560,6 +567,49 @@ def check_dbscan(L):
     assert o["n_clusters"] == 5 and o["core"].all()
 
 
+def check_fragile(L):
+    v = np.array([12.5, -3.25])
+    th = np.linspace(-1.0, 1.0, 30)               # minimal sets far from singular
+    dop = v[0] * np.cos(th) + v[1] * np.sin(th)  # noise-free inliers
+    t_x = 0.3125
+    base = v[0] * math.cos(t_x) + v[1] * math.sin(t_x)
+    tau = 0.1
+
+    def flagged(w_extra, t_extra=t_x):
+        az = np.append(th, t_extra)
+        dp = np.append(dop, w_extra)
+        o = _est(L, az, dp, [0, az.shape[0]], num_hypotheses=64, tau=tau, seed=3, want_fragile=True)
+        assert o["inlier_count"][0] in (30, 31) and o["status"][0] == 0
+        return bool(o["fragile"][0])
+
+    # at the threshold to within a few ulps, on either side: flagged
+    for sign in (1.0, -1.0):
+        w0 = base + sign * tau
+        for k in range(-2, 3):
+            w = w0
+            for _ in range(abs(k)):
+                w = np.nextafter(w, math.inf if k > 0 else -math.inf)
+            assert flagged(w), (sign, k)
+    # clear of it by 1e-9 m/s: not flagged
+    for w in (base + tau + 1e-9, base + tau - 1e-9, base - tau + 1e-9, base - tau - 1e-9, base, base + 1.0):
+        assert not flagged(w), w
+    # a minimal set whose determinant sits on cond_eps (two points, one trial)
+    a0, a1 = 0.2, 0.9
+    det = math.cos(a0) * math.sin(a1) - math.sin(a0) * math.cos(a1)  # = sin(a1 - a0) to ~1e-16
+    for eps, want in ((abs(det), True), (abs(det) * (1 + 1e-6), False), (abs(det) * (1 - 1e-6), False)):
+        o = _est(L, np.array([a0, a1]), np.array([1.0, 2.0]), [0, 2], num_hypotheses=1, tau=tau, seed=1,
+                 cond_eps=eps, want_fragile=True)
+        assert bool(o["fragile"][0]) == want, (eps, det)
+    # realistic frames: nothing within rounding distance of a decision
+    for name in ("frame64", "dense2d"):
+        w = synth.WORKLOADS[name]
+        f = synth.make_frame(w)
+        sub = None if name == "frame64" else np.sort(np.random.default_rng(2).choice(f.n_clusters, 384, replace=False))
+        o = _est(L, f.azimuth, f.doppler, f.offsets, num_hypotheses=w.num_hypotheses, tau=w.tau, seed=w.seed,
+                 subset=sub, want_fragile=True)
+        assert not o["fragile"].any(), (name, np.flatnonzero(o["fragile"]))
+
+
 ALL_CHECKS = [check_philox, check_draws, check_recovery, check_brute, check_symmetry,
               check_rotation, check_lstsq, check_status, check_planted, check_local_opt, check_adaptive,
-              check_paper_line, check_dbscan]
+              check_paper_line, check_dbscan, check_fragile]

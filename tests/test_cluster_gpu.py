@@ -173,8 +173,7 @@ def test_pipeline_cluster_gather_estimate(torch, ctx):
     o_lab = oracle.dbscan(s.features().astype(np.float64), 1.0, 4)["labels"]
     p_o, off_o = _csr(o_lab, nc)
     o = G.run_oracle(s.azimuth[p_o], s.doppler[p_o], off_o.astype(np.int32), H=256, tau=0.1, seed=3)
-    rep = G.compare(g, o, off_o)
-    assert not rep["mismatch"], rep["mismatch"][:10]
+    G.check_parity(G.compare(g, o, off_o), tau=0.1)
     # sanity against the scene's truth: the velocity along the line of sight
     # (a distant object spans a degree of azimuth, so its lateral component
     # is barely observable from one radar; its radial one is)

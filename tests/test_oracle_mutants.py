@@ -15,6 +15,10 @@ import oracle
 from tests import oracle_pins
 
 MUTANTS = {
+    "fragile_margin_dropped": ("double amp = 1e-14 * (1.0 + 1.0 / fabs(hyp_det[h]));", "double amp = 0.0;"),
+    "fragile_margin_too_wide": ("double amp = 1e-14 * (1.0 + 1.0 / fabs(hyp_det[h]));",
+                                "double amp = 1e-8 * (1.0 + 1.0 / fabs(hyp_det[h]));"),
+    "fragile_det_margin_dropped": ("int frag = min_det_margin < 1e-13;", "int frag = 0;"),
     "det2_sign": ("return fma(x, w, -(y * z));", "return fma(x, w, (y * z));"),
     "det3_cofactor_sign": ("fma(-m0[1], k1, m0[0] * k0)", "fma(m0[1], k1, m0[0] * k0)"),
     "det3_minor_index": ("double k1 = det2(m1[0], m1[2], m2[0], m2[2]);",

@@ -10,6 +10,7 @@ import numpy as np
 import pytest
 
 from paper_2012_12618_gb300 import rvh, serving, synth
+from tests import gpu_util as G
 
 pytestmark = pytest.mark.gpu
 
@@ -76,6 +77,42 @@ def test_results_same_alone_and_in_the_mix(torch):
                 assert rvh.rvh_wait(ctx.handle, tk, 30_000_000) == rvh.RVH_OK, rvh.rvh_last_error(None)
                 torch.cuda.synchronize()
                 _same(_np(outs, frames[i][0].n_points), alone[i])
+    finally:
+        ctx.close()
+
+
+def test_serving_frames_equal_the_oracle(torch):
+    """Frames of the 64-radar serving load at its full sizes (50..2000
+    clusters of 8..2048 points; 2D radars with 256 trials, 3D radars with
+    2048), submitted together through rvh_submit so that they share
+    batches, each compared on every cluster with the oracle."""
+    dev = torch.device("cuda", 0)
+    spec = synth.ServingSpec()
+    picks = [(0, 0), (32, 0), (5, 2), (40, 1), (17, 3), (63, 4)]
+    ctx = rvh.Context(0)
+    try:
+        held, tickets = [], []
+        for radar, k in picks:
+            f, w = synth.serving_frame(spec, radar, k)
+            t = [None if x is None else torch.from_numpy(x).to(dev) for x in (f.azimuth, f.doppler, f.offsets,
+                                                                               f.elevation)]
+            frame = rvh.make_frame(*t)
+            params = rvh.make_params(w.model_dim, w.num_hypotheses, w.tau, synth.radar_frame_seed(radar, k))
+            outs = rvh.alloc_outputs(f.n_clusters, f.n_points, dev)
+            tk = ctypes.c_uint64(0)
+            ctx.check(rvh.rvh_submit(ctx.handle, frame, params, rvh.make_result(outs), tk), "submit")
+            held.append(t)
+            tickets.append((radar, k, f, w, tk.value, outs))
+        assert sum(1 for r, *_ in tickets if r >= 32) >= 2 and sum(1 for r, *_ in tickets if r < 32) >= 2
+        for radar, k, f, w, tk, outs in tickets:
+            assert rvh.rvh_wait(ctx.handle, tk, 60_000_000) == rvh.RVH_OK, rvh.rvh_last_error(None)
+        torch.cuda.synchronize()
+        for radar, k, f, w, tk, outs in tickets:
+            g = _np(outs, f.n_points)
+            o = G.run_oracle_parallel(f.azimuth, f.doppler, f.offsets, el=f.elevation, H=w.num_hypotheses,
+                                      tau=w.tau, seed=synth.radar_frame_seed(radar, k))
+            G.check_parity(G.compare(g, o, f.offsets), tau=w.tau,
+                           label=f"serving radar {radar} frame {k} ({w.model_dim}D, {f.n_clusters} clusters)")
     finally:
         ctx.close()
 
