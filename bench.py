@@ -54,17 +54,40 @@ def recorded_traffic():
 
 
 class ClockSampler:
-    """nvidia-smi sampling of SM clocks and throttle reasons during the timed region."""
+    """SM clocks and throttle reasons during the timed region.
+
+    NVML (libnvidia-ml, read-only queries) is polled every millisecond from a
+    thread, so even a timed region of a few milliseconds gets samples; a
+    streaming nvidia-smi process (100 ms) runs beside it, and one nvidia-smi
+    query is taken right before and right after the region.  Nothing here
+    changes a GPU setting."""
 
     FIELDS = ("clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
               "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
               "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+    # nvmlClocksEventReasons bits
+    NVML_REASONS = {0x4: "sw_power_cap", 0x8: "hw_slowdown", 0x20: "sw_thermal_slowdown", 0x40: "hw_thermal_slowdown"}
 
     def __init__(self, index: int):
         self.index = index
-        self.samples = []
+        self.samples = []        # nvidia-smi rows
+        self.nvml = []           # (sm MHz, reason bits)
+        self.edges = []          # nvidia-smi rows at entry and exit
+        self.nvml_max = None
         self._stop = threading.Event()
         self._t = None
+        self._tn = None
+        self._p = None
+
+    def _query_once(self):
+        try:
+            out = subprocess.run(["nvidia-smi", "-i", str(self.index), f"--query-gpu={self.FIELDS}",
+                                  "--format=csv,noheader,nounits"], capture_output=True, text=True, timeout=10)
+            line = out.stdout.strip().splitlines()[0] if out.stdout.strip() else ""
+            if line:
+                self.edges.append([x.strip() for x in line.split(",")])
+        except (OSError, subprocess.SubprocessError, IndexError):
+            pass
 
     def _run(self):
         for line in self._p.stdout:
@@ -74,41 +97,85 @@ class ClockSampler:
             if line:
                 self.samples.append([x.strip() for x in line.split(",")])
 
+    def _nvml_open(self):
+        try:
+            lib = ctypes.CDLL("libnvidia-ml.so.1")
+            if lib.nvmlInit_v2() != 0:
+                return None
+            h = ctypes.c_void_p()
+            if lib.nvmlDeviceGetHandleByIndex_v2(ctypes.c_uint(self.index), ctypes.byref(h)) != 0:
+                return None
+            mx = ctypes.c_uint(0)
+            if lib.nvmlDeviceGetMaxClockInfo(h, ctypes.c_int(1), ctypes.byref(mx)) == 0:  # NVML_CLOCK_SM
+                self.nvml_max = float(mx.value)
+            return lib, h
+        except (OSError, AttributeError):
+            return None
+
+    def _run_nvml(self, lib, h):
+        clk, rs = ctypes.c_uint(0), ctypes.c_ulonglong(0)
+        get_reasons = getattr(lib, "nvmlDeviceGetCurrentClocksEventReasons", None) or \
+            getattr(lib, "nvmlDeviceGetCurrentClocksThrottleReasons")
+        while not self._stop.is_set():
+            if lib.nvmlDeviceGetClockInfo(h, ctypes.c_int(1), ctypes.byref(clk)) == 0 and \
+                    get_reasons(h, ctypes.byref(rs)) == 0:
+                self.nvml.append((float(clk.value), int(rs.value)))
+            time.sleep(0.001)
+
     def __enter__(self):
-        # one streaming nvidia-smi process, a sample every 100 ms
-        self._p = None
+        self._query_once()
         try:
             self._p = subprocess.Popen(["nvidia-smi", "-i", str(self.index), f"--query-gpu={self.FIELDS}",
                                         "--format=csv,noheader,nounits", "-lms", "100"],
                                        stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self._t = threading.Thread(target=self._run, daemon=True)
+            self._t.start()
         except OSError:
-            return self
-        self._t = threading.Thread(target=self._run, daemon=True)
-        self._t.start()
+            self._p = None
+        nv = self._nvml_open()
+        if nv:
+            self._tn = threading.Thread(target=self._run_nvml, args=nv, daemon=True)
+            self._tn.start()
         return self
 
     def __exit__(self, *exc):
         self._stop.set()
-        if self._p is None:
-            return
-        self._p.terminate()
-        try:
-            self._p.wait(timeout=5)
-        except subprocess.TimeoutExpired:
-            self._p.kill()
-            self._p.wait(timeout=5)
-        self._t.join(timeout=10)
+        if self._tn is not None:
+            self._tn.join(timeout=5)
+        if self._p is not None:
+            self._p.terminate()
+            try:
+                self._p.wait(timeout=5)
+            except subprocess.TimeoutExpired:
+                self._p.kill()
+                self._p.wait(timeout=5)
+            self._t.join(timeout=10)
+        self._query_once()
 
     def summary(self):
-        if not self.samples:
-            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["unsampled"]}
-        sm = [float(s[0]) for s in self.samples if s[0].replace(".", "").isdigit()]
-        mx = [float(s[1]) for s in self.samples if s[1].replace(".", "").isdigit()]
         names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
-        reasons = sorted({names[i] for s in self.samples for i in range(4)
-                          if len(s) > 4 + i and s[4 + i].lower().startswith("active")})
+
+        def smi(rows):
+            sm = [float(r[0]) for r in rows if r and r[0].replace(".", "").isdigit()]
+            mx = [float(r[1]) for r in rows if len(r) > 1 and r[1].replace(".", "").isdigit()]
+            rs = {names[i] for r in rows for i in range(4) if len(r) > 4 + i and r[4 + i].lower().startswith("active")}
+            return sm, mx, rs
+
+        sm_s, mx_s, rs_s = smi(self.samples)
+        sm_e, mx_e, rs_e = smi(self.edges)
+        sm_n = [c for c, _ in self.nvml]
+        rs_n = {name for _, bits in self.nvml for bit, name in self.NVML_REASONS.items() if bits & bit}
+        during = sm_n or sm_s
+        sm = during or sm_e
+        mx = ([self.nvml_max] if self.nvml_max else []) + mx_s + mx_e
+        reasons = sorted(rs_n | rs_s | (rs_e if not during else set()))
+        if not sm:
+            reasons = ["unsampled"]
         return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": max(mx) if mx else None,
-                "reasons": reasons, "samples": len(self.samples)}
+                "reasons": reasons, "samples": len(self.nvml) + len(self.samples),
+                "nvml_samples": len(self.nvml), "smi_samples": len(self.samples),
+                "sm_mhz_min": min(sm) if sm else None,
+                "edge_samples_mhz": sm_e, "source": "nvml 1 ms" if sm_n else ("nvidia-smi 100 ms" if sm_s else "entry/exit")}
 
 
 # ---- the oracle over all host cores: one spawned process per core, each
@@ -145,6 +212,123 @@ def oracle_all_cores(f, w, wname):
     return {"value": done / dt, "unit": "clusters/s", "cores": cores, "kind": "oracle",
             "sample": f"the whole {wname} frame ({done} clusters), one process per core over "
                       f"{len(ranges)} cost-balanced contiguous cluster ranges", "seconds": dt}
+
+
+def measure_workload(ctx, name, dev, stream, sptr, flush, steps, sms, max_mhz):
+    """One single-frame workload timed like the headline one: autotuned
+    schedule, device-resident inputs, L2 flushed between steps (outside the
+    events), CUDA events around each estimate and the library's own events
+    around the fused kernel."""
+    import torch
+    from paper_2012_12618_gb300 import rvh, synth
+    w = synth.WORKLOADS[name]
+    f = synth.make_frame(w)
+    nc, npts, dim = f.n_clusters, f.n_points, w.model_dim
+    pairs = int(np.diff(f.offsets).astype(np.int64).sum()) * w.num_hypotheses
+    ins = [None if a is None else torch.from_numpy(a).to(dev) for a in (f.azimuth, f.doppler, f.offsets, f.elevation)]
+    frame = rvh.make_frame(*ins)
+    params = rvh.make_params(dim, w.num_hypotheses, w.tau, w.seed)
+    outs = rvh.alloc_outputs(nc, npts, dev)
+    res = rvh.make_result(outs)
+    tuned = rvh.rvh_schedule()
+    ctx.check(rvh.rvh_autotune(ctx.handle, frame, params, res, 5, tuned), "rvh_autotune")
+    stats = rvh.rvh_stats()
+    for _ in range(3):
+        flush.fill_(2)
+        ctx.check(rvh.rvh_estimate(ctx.handle, frame, params, res, sptr), "rvh_estimate")
+    torch.cuda.synchronize()
+    step_ms, kern_ms, phase, band = [], [], np.zeros(6), 0
+    with ClockSampler(dev.index or 0) as clk:
+        for i in range(steps):
+            flush.fill_(np.uint8(i & 0xFF))
+            e0 = torch.cuda.Event(enable_timing=True)
+            e1 = torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            ctx.check(rvh.rvh_estimate(ctx.handle, frame, params, res, sptr), "rvh_estimate")
+            e1.record(stream)
+            e1.synchronize()
+            step_ms.append(e0.elapsed_time(e1))
+            ctx.check(rvh.rvh_get_stats(ctx.handle, stats), "rvh_get_stats")
+            kern_ms.append(stats.kernel_ms)
+            phase += np.array(list(stats.phase_cycles), dtype=np.float64)
+            band += stats.band_points
+    ck = clk.summary()
+    k_s = float(np.mean(kern_ms)) * 1e-3
+    t_s = float(np.mean(step_ms)) * 1e-3
+    flops = 2.0 * dim * pairs
+    peak = sms * FP32_LANES_PER_SM * 2 * max_mhz * 1e6 / 1e12
+    ach = flops / k_s / 1e12
+    share = float(phase[2] / max(phase.sum(), 1.0))
+    at_clk = (sms * FP32_LANES_PER_SM * 2 * ck["sm_mhz"] * 1e6 / 1e12) if ck.get("sm_mhz") else None
+    out = {"workload": f"{name}: {nc} clusters, sizes {w.size_law} {w.size_lo}..{w.size_hi}, {npts} points, "
+                       f"{dim}D, H={w.num_hypotheses}, tau={w.tau} m/s, outliers {w.outlier_frac:g}, "
+                       f"noise {w.noise_sigma:g} m/s",
+           "steps": steps, "ms_per_step": t_s * 1e3, "kernel_ms": k_s * 1e3, "clusters_per_s": nc / t_s,
+           "pair_evals_per_s": pairs / t_s, "roofline_achieved_tflops": ach, "roofline_frac": ach / peak,
+           "roofline_frac_at_measured_clock": ach / at_clk if at_clk else None,
+           "scoring_loop_frac": (flops / (share * k_s) / 1e12) / peak if share > 0 else None,
+           "scoring_stage_share": share, "fp64_band_decisions_per_step": band / max(steps, 1),
+           "schedule": [tuned.points_per_warp, tuned.hyps_per_lane], "grid": stats.grid, "clocks": ck,
+           "stage_share": dict(zip(["rows", "hypotheses", "scoring", "exact_rescoring", "mask_refine", "other"],
+                                   [round(float(x), 4) for x in phase / max(phase.sum(), 1.0)]))}
+    if nc <= 256:
+        out["us_per_frame"] = t_s * 1e6
+    return out
+
+
+def measure_clustering(ctx, dev, stream, sptr, flush, steps):
+    """DBSCAN of the unclustered traffic scene, then the pipeline cluster ->
+    gather -> estimate (2D, H = 1024, tau = 0.1 m/s), timed with CUDA events
+    on the stream: 3 warm-up calls, then `steps` timed ones."""
+    import torch
+    from paper_2012_12618_gb300 import rvh, synth
+    w = synth.WORKLOADS["dense2d"]
+    sc = synth.SCENES["scene"]
+    scene = synth.make_scene(sc)
+    n_s = scene.n_points
+    d_feat = torch.from_numpy(scene.features().reshape(-1).copy()).to(dev)
+    s_az, s_dop = torch.from_numpy(scene.azimuth).to(dev), torch.from_numpy(scene.doppler).to(dev)
+    c_lab = torch.empty(n_s, dtype=torch.int32, device=dev)
+    c_perm = torch.empty(n_s, dtype=torch.int32, device=dev)
+    c_off = torch.empty(n_s + 1, dtype=torch.int32, device=dev)
+    g_az = torch.empty(n_s, dtype=torch.float32, device=dev)
+    g_dop = torch.empty(n_s, dtype=torch.float32, device=dev)
+    ncl = ctypes.c_int32(0)
+    # one call sizes the result buffers, reused by every step (stable addresses)
+    ctx.check(rvh.rvh_cluster(ctx.handle, d_feat, n_s, 2, sc.eps, sc.min_pts, c_lab, c_perm, c_off, n_s, ncl,
+                              sptr), "rvh_cluster")
+    m_s = int(c_off[ncl.value].item())  # clustered points: the same every step (deterministic)
+    cl_outs = rvh.alloc_outputs(ncl.value, m_s, dev)
+    cl_frame = rvh.make_frame(g_az[:m_s], g_dop[:m_s], c_off[:ncl.value + 1])
+    cl_params = rvh.make_params(2, w.num_hypotheses, w.tau, w.seed)
+    cl_res = rvh.make_result(cl_outs)
+    cl_ms, ga_ms, es_ms, pipe_ms = [], [], [], []
+    for i in range(3 + steps):
+        flush.fill_(8)
+        ev = [torch.cuda.Event(enable_timing=True) for _ in range(4)]
+        ev[0].record(stream)
+        ctx.check(rvh.rvh_cluster(ctx.handle, d_feat, n_s, 2, sc.eps, sc.min_pts, c_lab, c_perm, c_off, n_s, ncl,
+                                  sptr), "rvh_cluster")
+        ev[1].record(stream)
+        ctx.check(rvh.rvh_gather(ctx.handle, c_perm, m_s, s_az, g_az, s_dop, g_dop, stream=sptr), "rvh_gather")
+        ev[2].record(stream)
+        ctx.check(rvh.rvh_estimate(ctx.handle, cl_frame, cl_params, cl_res, sptr), "rvh_estimate(scene)")
+        ev[3].record(stream)
+        ev[3].synchronize()
+        if i >= 3:
+            cl_ms.append(ev[0].elapsed_time(ev[1]))
+            ga_ms.append(ev[1].elapsed_time(ev[2]))
+            es_ms.append(ev[2].elapsed_time(ev[3]))
+            pipe_ms.append(ev[0].elapsed_time(ev[3]))
+    ck, pk = float(np.mean(cl_ms)), float(np.mean(pipe_ms))
+    return {"workload": f"scene: {sc.n_objects} objects, {n_s} points (x, y features), eps {sc.eps} m, "
+                        f"min_pts {sc.min_pts}; estimate H={w.num_hypotheses}, tau={w.tau}",
+            "n_clusters": int(ncl.value), "clustered_points": m_s,
+            "dbscan_ms": ck, "dbscan_points_per_s": n_s / (ck * 1e-3),
+            "gather_ms": float(np.mean(ga_ms)), "estimate_ms": float(np.mean(es_ms)),
+            "pipeline_ms": pk, "pipeline_clusters_per_s": ncl.value / (pk * 1e-3),
+            "note": "CUDA events on the stream; rvh_cluster reads its cluster count back (one sync)",
+            "steps": steps}
 
 
 def dist_env():
@@ -200,12 +384,18 @@ def main():
     ap.add_argument("--impl", default="rvh", choices=["rvh", "reference"])
     ap.add_argument("--workload", default=WORKLOAD, choices=["frame64", "dense2d", "stress2d", "dense3d"],
                     help="dense2d is the headline workload; the others are the precision, 3D and small-frame cases")
+    ap.add_argument("--clustering-only", type=int, default=0, metavar="STEPS",
+                    help="time only the clustering stage and pipeline on the traffic scene (3 warm-up calls, then "
+                         "STEPS timed ones) and print that object")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-gpu-baseline", action="store_true")
     ap.add_argument("--schedule", default="",
                     help="points_per_warp,hyps_per_lane for the scoring pass (default: the library's choice)")
-    ap.add_argument("--serving-seconds", type=float, default=3.0,
-                    help="measured seconds of the 64-radar serving load (0 skips it)")
+    ap.add_argument("--serving-seconds", type=float, default=10.0,
+                    help="measured seconds of the 64-radar serving load, after 1 s of warm-up (0 skips it)")
+    ap.add_argument("--workload-steps", type=int, default=100,
+                    help="timed steps of each of the other single-frame workloads (frame64, stress2d, dense3d "
+                         "beside the headline one; 0 skips them)")
     ap.add_argument("--refine-iterations", type=int, default=0,
                     help="local-optimisation rounds in the timed steps (default 0: the single-pass method)")
     ap.add_argument("--local-opt-steps", type=int, default=50,
@@ -225,6 +415,15 @@ def main():
     dev = torch.device("cuda", local)
 
     from paper_2012_12618_gb300 import rvh, synth
+    if args.clustering_only > 0:
+        ctx = rvh.Context(local)
+        stream = torch.cuda.Stream(dev)
+        torch.cuda.set_stream(stream)
+        flush = torch.empty(256 << 20, dtype=torch.uint8, device=dev)
+        out = measure_clustering(ctx, dev, stream, ctypes.c_void_p(stream.cuda_stream), flush, args.clustering_only)
+        print(json.dumps({"clustering": out}), flush=True)
+        ctx.close()
+        return 0
     wname = args.workload
     w = synth.WORKLOADS[wname]
     dim = w.model_dim
@@ -331,20 +530,32 @@ def main():
     share = float(phase[2] / max(phase.sum(), 1.0))
     if share > 0:
         sc = flops / (share * kern_s) / 1e12
-        roofline["scoring_loop"] = {
-            "achieved": sc, "frac": sc / peak, "stage_share": share,
-            "frac_at_measured_clock": (sc / (sms * FP32_LANES_PER_SM * 2 * clocks["sm_mhz"] * 1e6 / 1e12)
-                                       if clocks.get("sm_mhz") else None),
-            "basis": "scoring-pass share of the per-CTA stage clocks x kernel time"}
+        roofline["scoring_loop_achieved"] = sc
+        roofline["scoring_loop_frac"] = sc / peak
+        roofline["scoring_loop_stage_share"] = share
+        roofline["scoring_loop_frac_at_measured_clock"] = (
+            sc / (sms * FP32_LANES_PER_SM * 2 * clocks["sm_mhz"] * 1e6 / 1e12) if clocks.get("sm_mhz") else None)
+        roofline["scoring_loop_basis"] = "scoring-pass share of the per-CTA stage clocks x kernel time"
+
+    # ---- the other single-frame workloads, each timed like the headline one
+    workloads = {}
+    if args.workload_steps > 0 and rank == 0:
+        for other in ("frame64", "dense2d", "stress2d", "dense3d"):
+            if other != wname:
+                workloads[other] = measure_workload(ctx, other, dev, stream, sptr, flush, args.workload_steps,
+                                                    sms, max_mhz)
 
     # ---- serving: 64 radars x 20 frames/s (Poisson), mixed 2D/3D, continuous batching
     # (right after the timed steps, before the other measurements churn the GPU)
     serve = None
     if args.serving_seconds > 0 and rank == 0:
         from paper_2012_12618_gb300 import serving
-        spec = synth.ServingSpec(duration_s=args.serving_seconds, warmup_s=0.5)
+        spec = synth.ServingSpec(duration_s=args.serving_seconds, warmup_s=1.0)
         sres = serving.run_load(ctx, spec, dev)
         serve = sres.summary()
+        ctx.check(rvh.rvh_get_stats(ctx.handle, stats), "rvh_get_stats")
+        serve["steps"] = stats.serving_steps
+        serve["graph_replays"] = stats.serving_graph_replays
         serve["config"] = (f"{spec.n_radars} radars x {spec.fps:g} frames/s Poisson, clusters "
                            f"{spec.clusters_lo}..{spec.clusters_hi} per frame, sizes log-uniform "
                            f"{spec.size_lo}..{spec.size_hi}; radars 0-31 2D H=256, 32-63 3D H=2048; "
@@ -429,52 +640,7 @@ def main():
     # then the whole pipeline cluster -> gather -> estimate (H = 1024, 2D)
     clustering = None
     if args.local_opt_steps > 0 and args.refine_iterations == 0 and dim == 2:
-        sc = synth.SCENES["scene"]
-        scene = synth.make_scene(sc)
-        n_s = scene.n_points
-        d_feat = torch.from_numpy(scene.features().reshape(-1).copy()).to(dev)
-        s_az, s_dop = torch.from_numpy(scene.azimuth).to(dev), torch.from_numpy(scene.doppler).to(dev)
-        c_lab = torch.empty(n_s, dtype=torch.int32, device=dev)
-        c_perm = torch.empty(n_s, dtype=torch.int32, device=dev)
-        c_off = torch.empty(n_s + 1, dtype=torch.int32, device=dev)
-        g_az = torch.empty(n_s, dtype=torch.float32, device=dev)
-        g_dop = torch.empty(n_s, dtype=torch.float32, device=dev)
-        ncl = ctypes.c_int32(0)
-        # one call sizes the result buffers, reused by every step (stable addresses)
-        ctx.check(rvh.rvh_cluster(ctx.handle, d_feat, n_s, 2, sc.eps, sc.min_pts, c_lab, c_perm, c_off, n_s, ncl,
-                                  sptr), "rvh_cluster")
-        m_s = int(c_off[ncl.value].item())  # clustered points: the same every step (deterministic)
-        cl_outs = rvh.alloc_outputs(ncl.value, m_s, dev)
-        cl_frame = rvh.make_frame(g_az[:m_s], g_dop[:m_s], c_off[:ncl.value + 1])
-        cl_params = rvh.make_params(2, w.num_hypotheses, w.tau, w.seed)
-        cl_res = rvh.make_result(cl_outs)
-        cl_ms, ga_ms, es_ms, pipe_ms = [], [], [], []
-        for i in range(3 + args.local_opt_steps):
-            flush.fill_(8)
-            ev = [torch.cuda.Event(enable_timing=True) for _ in range(4)]
-            ev[0].record(stream)
-            ctx.check(rvh.rvh_cluster(ctx.handle, d_feat, n_s, 2, sc.eps, sc.min_pts, c_lab, c_perm, c_off, n_s, ncl,
-                                      sptr), "rvh_cluster")
-            ev[1].record(stream)
-            ctx.check(rvh.rvh_gather(ctx.handle, c_perm, m_s, s_az, g_az, s_dop, g_dop, stream=sptr), "rvh_gather")
-            ev[2].record(stream)
-            ctx.check(rvh.rvh_estimate(ctx.handle, cl_frame, cl_params, cl_res, sptr), "rvh_estimate(scene)")
-            ev[3].record(stream)
-            ev[3].synchronize()
-            if i >= 3:
-                cl_ms.append(ev[0].elapsed_time(ev[1]))
-                ga_ms.append(ev[1].elapsed_time(ev[2]))
-                es_ms.append(ev[2].elapsed_time(ev[3]))
-                pipe_ms.append(ev[0].elapsed_time(ev[3]))
-        ck, pk = float(np.mean(cl_ms)), float(np.mean(pipe_ms))
-        clustering = {"workload": f"scene: {sc.n_objects} objects, {n_s} points (x, y features), eps {sc.eps} m, "
-                                  f"min_pts {sc.min_pts}; estimate H={w.num_hypotheses}, tau={w.tau}",
-                      "n_clusters": int(ncl.value), "clustered_points": m_s,
-                      "dbscan_ms": ck, "dbscan_points_per_s": n_s / (ck * 1e-3),
-                      "gather_ms": float(np.mean(ga_ms)), "estimate_ms": float(np.mean(es_ms)),
-                      "pipeline_ms": pk, "pipeline_clusters_per_s": ncl.value / (pk * 1e-3),
-                      "note": "CUDA events on the stream; rvh_cluster reads its cluster count back (one sync)",
-                      "steps": args.local_opt_steps}
+        clustering = measure_clustering(ctx, dev, stream, sptr, flush, args.local_opt_steps)
 
     # ---- end to end through the C ABI with pinned host buffers (copies inside the timed region)
     h_az = torch.from_numpy(f.azimuth).pin_memory()
@@ -545,6 +711,7 @@ def main():
                        "per_rank": "one independent frame per rank"},
             "pair_evals_per_s": pairs * ws / t_max,
             "roofline": roofline,
+            "workloads": workloads,
             "cpu_baseline": cpu,
             "cpu_baseline_all_cores": cpu_all,
             "gpu_baseline": gpu_base,
@@ -562,7 +729,7 @@ def main():
                      "band_rate_per_pair": band / args.steps / pairs},
             "schedule": {"grid": grid, "points_per_warp": stats.points_per_warp,
                          "hyps_per_lane": stats.hyps_per_lane, "autotuned": not args.schedule,
-                         "cuda_graph_replays": stats.graph_replays},
+                         "cuda_graph_replays": stats.graph_replays, "cuda_graph_builds": stats.graph_builds},
             "stage_share": dict(zip(["rows", "hypotheses", "scoring", "exact_rescoring", "mask_refine", "other"],
                                     [round(float(x), 4) for x in phase / max(phase.sum(), 1.0)])),
             "wall_s": wall,

@@ -218,13 +218,18 @@ int rvh_estimate_baseline(rvh_ctx* ctx, const rvh_frame* frame, const rvh_params
  *
  * The first call on a device sets that device up (device addresses of the
  * arrays, the row table upload, the kernels' shared-memory opt-in), with the
- * device current; make this first call before any stream capture.
+ * device current.  Under CUDA's lazy module loading (the default) that first
+ * call is also when the driver commits the arrays' device memory, so make it
+ * during start-up, before the caller's no-allocation phase begins and before
+ * any stream capture; later calls leave the device's free memory unchanged.
  * All inputs and outputs must be device memory; the call is stream-ordered on
  * `stream` (a cudaStream_t, NULL = the legacy default stream) and returns once
  * the work is enqueued.  Every call shares the arrays, which keep the last
  * call's contents (each call resets the work counter it needs zeroed), so
  * calls that overlap on the GPU race: order them on one stream or with events.
- * Results equal rvh_estimate's. */
+ * Argument checks are rvh_estimate's (plus the limits above and device
+ * memory for every array the launch touches), and results equal
+ * rvh_estimate's: the same kernels with the same per-frame settings. */
 #define RVH_NOALLOC_MAX_POINTS 1048576
 #define RVH_NOALLOC_MAX_CLUSTERS 65536
 int rvh_estimate_noalloc(const rvh_frame* frame, const rvh_params* params, rvh_result* result, void* stream);
@@ -310,8 +315,15 @@ typedef struct {
    * winner mask + refine, scheduling/other. */
   int64_t phase_cycles[6];
   int64_t refined_hypotheses;  /* trials whose FP32 solve took one refinement step */
-  int64_t graph_replays;       /* rvh_estimate calls served by replaying a captured CUDA graph */
+  int64_t graph_replays;       /* rvh_estimate calls that replayed an instantiated CUDA graph of the fused
+                                  launch, its kernel node given the call's arguments (new frame addresses,
+                                  sizes and schedules replay the same graph) */
   int32_t kernel_launches;     /* the library's kernels launched by the last call (work list + fused) */
+  int64_t graph_builds;        /* graphs of the fused launch built by rvh_estimate calls (one per kernel
+                                  instantiation: model dimension, with or without the extensions) */
+  int64_t serving_steps;       /* serving steps launched by the context's request loop (rvh_submit) */
+  int64_t serving_graph_replays; /* serving steps that replayed an instantiated graph (work list + fused
+                                    kernel) with that step's batch of frames */
 } rvh_stats;
 
 /* Counters of the last rvh_estimate on this context (synchronises its stream). */

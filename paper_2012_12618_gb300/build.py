@@ -18,7 +18,8 @@ CSRC = os.path.join(HERE, "csrc")
 INCLUDE = os.path.join(ROOT, "include")
 LIB = os.path.join(HERE, "librvh.so")
 BUILD_DIR = os.path.join(HERE, "_build")
-SOURCES = ["rvh_fused.cu", "rvh_baseline.cu", "rvh_api.cu", "rvh_server.cu", "rvh_noalloc.cu", "rvh_cluster.cu"]
+SOURCES = ["rvh_fused.cu", "rvh_baseline.cu", "rvh_api.cu", "rvh_graph.cu", "rvh_server.cu", "rvh_noalloc.cu",
+           "rvh_cluster.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-O3", "-std=c++17", "-lineinfo", "-fmad=false", "-Xcompiler", "-fPIC,-O2",
          "--expt-relaxed-constexpr", "-I" + INCLUDE, "-I" + CSRC]

@@ -69,7 +69,7 @@ bool is_device_ptr(const void* p) {
 }
 
 // Host-side argument checks shared by every entry point.
-int check_args(const rvh_frame* f, const rvh_params* p, const rvh_result* r) {
+int check_args_impl(const rvh_frame* f, const rvh_params* p, const rvh_result* r) {
   if (!f || !p || !r) return fail(RVH_EINVAL, "frame, params and result must be non-NULL");
   if (f->n_clusters < 0) return fail(RVH_EINVAL, "n_clusters < 0");
   if (f->n_points < 0 || f->n_points > 0x7fffffffLL) return fail(RVH_EINVAL, "n_points out of range [0, 2^31)");
@@ -164,12 +164,11 @@ struct rvh_ctx {
   rvh::Server* server = nullptr;
   double2* trig = nullptr;  // device table of (cos, sin)(k/128)
   std::map<int, std::pair<int, int>> tuned;  // (dim << 8 | log2 H) -> (pw, hpl)
-  // CUDA graph of the last all-device launch sequence, replayed while its
-  // arguments stay the same
+  // CUDA graphs of the fused launch, one per kernel instantiation (model
+  // dimension x extensions), replayed with each call's arguments
   bool graphs = true;
-  cudaGraphExec_t gexec = nullptr;
-  std::vector<char> gkey;
-  int64_t graph_replays = 0;
+  rvh::LaunchGraph graph[2][2];
+  bool cta_rows = true;  // per-CTA FP64 row slots for clusters that fit shared memory
   std::string tune_prefix;                    // "<gpu name>|<sms>|"
   bool last_counts_trials = false;  // the last launch counted its trials on the device (extensions)
 };
@@ -196,6 +195,8 @@ void ctx_free(rvh_ctx* ctx, void* p, size_t bytes) {
 }
 
 int ctx_device(rvh_ctx* ctx) { return ctx->device; }
+bool ctx_graphs(rvh_ctx* ctx) { return ctx->graphs; }
+const double2* ctx_trig(rvh_ctx* ctx) { return ctx->trig; }
 int ctx_sms(rvh_ctx* ctx) { return ctx->sms; }
 
 int tune_key(int dim, int H) {
@@ -226,10 +227,10 @@ void choose_schedule(rvh_ctx* ctx, int dim, int H, int* pw, int* hpl) {
 }
 
 // Fills the per-frame descriptor; the pointers must already be device pointers.
-void fill_desc(rvh_ctx* ctx, FrameDesc& d, const rvh_frame& f, const rvh_params& p, const float* az,
+void fill_desc(const double2* trig, FrameDesc& d, const rvh_frame& f, const rvh_params& p, const float* az,
                const float* el, const float* dop, const int32_t* off, float4* rows_g, double4_32a* rows64_g,
                const rvh_result& out) {
-  d.trig = ctx->trig;
+  d.trig = trig;
   d.rows64_g = rows64_g;
   const int dim = p.model_dim;
   const double eps = p.cond_eps > 0 ? p.cond_eps : default_eps(dim);
@@ -267,7 +268,7 @@ void fill_desc(rvh_ctx* ctx, FrameDesc& d, const rvh_frame& f, const rvh_params&
 int configure_dim(rvh_ctx* ctx, int dim) {
   const size_t smem = fused_smem_bytes(ctx->nmax_smem, ctx->hchunk);
   if (ctx->occ[dim] == 0) {
-    RVH_CUDA(fused_configure(dim, smem));
+    RVH_CUDA(fused_configure_max(dim, ctx->device));
     int b = 0;
     RVH_CUDA(fused_occupancy(dim, smem, &b));
     ctx->occ[dim] = std::max(1, b);
@@ -305,10 +306,10 @@ int launch_batch(rvh_ctx* ctx, FusedArgs& a, int dim, cudaStream_t s, cudaEvent_
   return RVH_OK;
 }
 
-// Launches the fused kernel through a CUDA graph: the kernel (with its
-// ~6 KB argument block) is captured once and replayed while the arguments
-// equal those of the capture.  The stats reset, the work-list kernel and the
-// timing events stay outside the graph, so the events time the fused kernel.
+// Launches the fused kernel through the context's CUDA graph of its kernel
+// instantiation, the call's arguments written into the graph's kernel node
+// (rvh_graph.cu).  The stats reset, the work-list kernel and the timing
+// events stay outside the graph, so the events time the fused kernel.
 int launch_graph(rvh_ctx* ctx, FusedArgs& a, int dim, cudaStream_t s) {
   int grid = 1;
   size_t smem = 0;
@@ -316,31 +317,12 @@ int launch_graph(rvh_ctx* ctx, FusedArgs& a, int dim, cudaStream_t s) {
   if (rc) return rc;
   RVH_CUDA(cudaMemsetAsync(a.stats, 0, 96, s));
   if (!a.direct) RVH_CUDA(launch_worklist(a, s));
-  std::vector<char> key(sizeof(FusedArgs) + 3 * sizeof(int64_t));
-  memcpy(key.data(), &a, sizeof(FusedArgs));
-  const int64_t extra[3] = {dim, grid, (int64_t)smem};
-  memcpy(key.data() + sizeof(FusedArgs), extra, sizeof(extra));
-  if (!(ctx->gexec && key == ctx->gkey)) {
-    RVH_CUDA(cudaStreamBeginCapture(s, cudaStreamCaptureModeThreadLocal));
-    cudaError_t e = launch_fused(dim, a, grid, smem, s);
-    cudaGraph_t g = nullptr;
-    const cudaError_t ee = cudaStreamEndCapture(s, &g);
-    if (e == cudaSuccess) e = ee;
-    cudaGraphExec_t exec = nullptr;
-    if (e == cudaSuccess) e = cudaGraphInstantiate(&exec, g, 0);
-    if (g) cudaGraphDestroy(g);
-    if (e != cudaSuccess) {
-      cudaGetLastError();
-      return fail(RVH_ECUDA, std::string("graph capture: ") + cudaGetErrorString(e));
-    }
-    if (ctx->gexec) cudaGraphExecDestroy(ctx->gexec);
-    ctx->gexec = exec;
-    ctx->gkey.swap(key);
-  } else {
-    ++ctx->graph_replays;
-  }
   RVH_CUDA(cudaEventRecord(ctx->ev0, s));
-  RVH_CUDA(cudaGraphLaunch(ctx->gexec, s));
+  const cudaError_t e = ctx->graph[dim == 3][fused_ext(a) ? 1 : 0].launch(a, dim, grid, smem, false, s);
+  if (e != cudaSuccess) {
+    cudaGetLastError();
+    return fail(RVH_ECUDA, std::string("graph launch: ") + cudaGetErrorString(e));
+  }
   RVH_CUDA(cudaEventRecord(ctx->ev1, s));
   ctx->last.grid = grid;
   ctx->last.kernel_launches = a.direct ? 1 : 2;
@@ -411,6 +393,7 @@ int rvh_create(rvh_ctx** out, int device, size_t mem_budget_bytes) {
   if (const char* e = getenv("RVH_NMAX_SMEM")) c->nmax_smem = std::max(64, atoi(e));
   if (const char* e = getenv("RVH_HCHUNK")) c->hchunk = std::max(64, atoi(e));
   if (const char* e = getenv("RVH_GRAPHS")) c->graphs = atoi(e) != 0;
+  if (const char* e = getenv("RVH_CTA_ROWS")) c->cta_rows = atoi(e) != 0;
   if (cudaStreamCreateWithFlags(&c->stream, cudaStreamNonBlocking) != cudaSuccess ||
       cudaEventCreateWithFlags(&c->last_done, cudaEventDisableTiming) != cudaSuccess ||
       cudaEventCreate(&c->ev0) != cudaSuccess || cudaEventCreate(&c->ev1) != cudaSuccess) {
@@ -453,7 +436,8 @@ void rvh_destroy(rvh_ctx* ctx) {
   cudaSetDevice(ctx->device);
   if (ctx->server) server_destroy(ctx->server);
   cudaStreamSynchronize(ctx->stream);
-  if (ctx->gexec) cudaGraphExecDestroy(ctx->gexec);
+  for (auto& row : ctx->graph)
+    for (auto& g : row) g.reset();
   if (ctx->scratch) ctx_free(ctx, ctx->scratch, ctx->scratch_bytes);
   if (ctx->cl_scratch) ctx_free(ctx, ctx->cl_scratch, ctx->cl_scratch_bytes);
   if (ctx->trig) ctx_free(ctx, ctx->trig, sizeof(double2) * kTrigSize);
@@ -547,7 +531,6 @@ int rvh_get_stats(rvh_ctx* ctx, rvh_stats* out) {
     }
     for (int k = 0; k < 6; ++k) ctx->last.phase_cycles[k] = (int64_t)h[4 + k];
     ctx->last.refined_hypotheses = (int64_t)h[3];
-    ctx->last.graph_replays = ctx->graph_replays;
     ctx->last.candidates = (int64_t)h[0];
     ctx->last.band_points = (int64_t)h[1];
     ctx->last.fp64_hypotheses = (int64_t)h[2];
@@ -555,6 +538,13 @@ int rvh_get_stats(rvh_ctx* ctx, rvh_stats* out) {
     if (cudaEventElapsedTime(&ms, ctx->ev0, ctx->ev1) == cudaSuccess) ctx->last.kernel_ms = ms;
     else cudaGetLastError();
   }
+  ctx->last.graph_replays = ctx->last.graph_builds = 0;
+  for (auto& row : ctx->graph)
+    for (auto& g : row) {
+      ctx->last.graph_replays += g.replays;
+      ctx->last.graph_builds += g.builds;
+    }
+  if (ctx->server) server_counts(ctx->server, &ctx->last.serving_steps, &ctx->last.serving_graph_replays);
   *out = ctx->last;
   return RVH_OK;
 }
@@ -567,13 +557,13 @@ struct Staged {
   const int32_t* off;
   rvh_result dev_out;       // device pointers the kernel writes
   bool host_out[rvh::kOutputs];
-  bool staged_any;          // some input or output went through host memory
   char* base;
   int2* worklist;
   int* counter;
   unsigned long long* stats;
   void* rows;               // float4[n_points] (fused) or double[4 n_points] (baseline)
-  double4_32a* rows64;          // double4_32a[n_points] (fused)
+  double4_32a* rows64;      // double4_32a[n_points] (fused)
+  double4_32a* cta_rows64;  // double4_32a[resident CTAs * nmax_smem] (fused)
 };
 
 static int stage(rvh_ctx* ctx, const rvh_frame* f, const rvh_params* p, rvh_result* r, cudaStream_t s,
@@ -591,8 +581,6 @@ static int stage(rvh_ctx* ctx, const rvh_frame* f, const rvh_params* p, rvh_resu
   void* outs[rvh::kOutputs];
   rvh::result_ptrs(*r, outs);
   for (int i = 0; i < rvh::kOutputs; ++i) st.host_out[i] = outs[i] && !is_device_ptr(outs[i]);
-  st.staged_any = !(d_az && d_dop && d_el && d_off);
-  for (int i = 0; i < rvh::kOutputs; ++i) st.staged_any = st.staged_any || st.host_out[i];
   // layout
   size_t off = 0;
   auto take = [&](size_t bytes) {
@@ -605,6 +593,12 @@ static int stage(rvh_ctx* ctx, const rvh_frame* f, const rvh_params* p, rvh_resu
   const size_t o_stats = take(128);
   const size_t o_rows = take((fused ? sizeof(float4) : 4 * sizeof(double)) * (size_t)std::max<int64_t>(np, 1));
   const size_t o_rows64 = fused ? take(sizeof(double4_32a) * (size_t)std::max<int64_t>(np, 1)) : 0;
+  size_t o_cta64 = 0;
+  if (fused) {
+    const int rc = configure_dim(ctx, p->model_dim);
+    if (rc) return rc;
+    o_cta64 = take(sizeof(double4_32a) * (size_t)ctx->nmax_smem * (size_t)(ctx->sms * ctx->occ[p->model_dim]));
+  }
   const size_t o_az = d_az ? 0 : take(4 * (size_t)np);
   const size_t o_el = d_el ? 0 : take(4 * (size_t)np);
   const size_t o_dop = d_dop ? 0 : take(4 * (size_t)np);
@@ -632,6 +626,7 @@ static int stage(rvh_ctx* ctx, const rvh_frame* f, const rvh_params* p, rvh_resu
   st.stats = (unsigned long long*)(b + o_stats);
   st.rows = b + o_rows;
   st.rows64 = fused ? (double4_32a*)(b + o_rows64) : nullptr;
+  st.cta_rows64 = fused ? (double4_32a*)(b + o_cta64) : nullptr;
   st.az = d_az ? f->azimuth : (const float*)(b + o_az);
   st.el = dim3 ? (d_el ? f->elevation : (const float*)(b + o_el)) : nullptr;
   st.dop = d_dop ? f->doppler : (const float*)(b + o_dop);
@@ -669,7 +664,7 @@ static int unstage(const rvh_frame* f, rvh_result* r, const Staged& st, cudaStre
 int rvh_estimate(rvh_ctx* ctx, const rvh_frame* frame, const rvh_params* params, rvh_result* result,
                  void* stream) {
   if (!ctx) return fail(RVH_EINVAL, "ctx is NULL");
-  int rc = check_args(frame, params, result);
+  int rc = check_args_impl(frame, params, result);
   if (rc) return rc;
   if (frame->n_clusters == 0) return RVH_OK;
   std::lock_guard<std::mutex> lk(ctx->mu);
@@ -682,16 +677,18 @@ int rvh_estimate(rvh_ctx* ctx, const rvh_frame* frame, const rvh_params* params,
   ctx->stats_d = st.stats;
   FusedArgs a;
   memset(&a, 0, sizeof(a));
-  fill_desc(ctx, a.f[0], *frame, *params, st.az, st.el, st.dop, st.off, (float4*)st.rows, st.rows64, st.dev_out);
+  fill_desc(ctx->trig, a.f[0], *frame, *params, st.az, st.el, st.dop, st.off, (float4*)st.rows, st.rows64,
+            st.dev_out);
   a.n_frames = 1;
   a.n_items = frame->n_clusters;
   a.worklist = st.worklist;
   a.work_counter = st.counter;
   a.stats = st.stats;
+  a.cta_rows64 = ctx->cta_rows ? st.cta_rows64 : nullptr;
   choose_schedule(ctx, params->model_dim, trials_per_chunk(*params), &a.pw, &a.hpl);
   cudaStreamCaptureStatus cap = cudaStreamCaptureStatusNone;
   RVH_CUDA(cudaStreamIsCapturing(s, &cap));
-  if (ctx->graphs && !st.staged_any && s != nullptr && cap == cudaStreamCaptureStatusNone) {
+  if (ctx->graphs && s != nullptr && cap == cudaStreamCaptureStatusNone) {
     rc = launch_graph(ctx, a, params->model_dim, s);
   } else {
     RVH_CUDA(cudaMemsetAsync(st.stats, 0, 96, s));
@@ -714,7 +711,7 @@ int rvh_estimate(rvh_ctx* ctx, const rvh_frame* frame, const rvh_params* params,
 int rvh_estimate_baseline(rvh_ctx* ctx, const rvh_frame* frame, const rvh_params* params, rvh_result* result,
                           void* stream) {
   if (!ctx) return fail(RVH_EINVAL, "ctx is NULL");
-  int rc = check_args(frame, params, result);
+  int rc = check_args_impl(frame, params, result);
   if (rc) return rc;
   if (params->refine_iterations != 0 || params->confidence != 0.0 || params->hypothesis_model != 0)
     return fail(RVH_EINVAL,
@@ -734,7 +731,7 @@ int rvh_estimate_baseline(rvh_ctx* ctx, const rvh_frame* frame, const rvh_params
   BaselineArgs b;
   memset(&b, 0, sizeof(b));
   FrameDesc d;
-  fill_desc(ctx, d, *frame, *params, st.az, st.el, st.dop, st.off, nullptr, nullptr, st.dev_out);
+  fill_desc(ctx->trig, d, *frame, *params, st.az, st.el, st.dop, st.off, nullptr, nullptr, st.dev_out);
   b.az = d.az;
   b.el = d.el;
   b.dop = d.dop;
@@ -769,7 +766,7 @@ int rvh_autotune(rvh_ctx* ctx, const rvh_frame* frame, const rvh_params* params,
                  int32_t reps, rvh_schedule* best) {
   if (!ctx) return fail(RVH_EINVAL, "ctx is NULL");
   if (reps < 1) return fail(RVH_EINVAL, "reps must be >= 1");
-  int rc = check_args(frame, params, result);
+  int rc = check_args_impl(frame, params, result);
   if (rc) return rc;
   if (frame->n_clusters == 0) return fail(RVH_EINVAL, "empty frame");
   static const int kCand[6][2] = {{1, 4}, {1, 8}, {8, 4}, {8, 8}, {32, 4}, {32, 8}};
@@ -818,7 +815,7 @@ int rvh_autotune(rvh_ctx* ctx, const rvh_frame* frame, const rvh_params* params,
 int rvh_submit(rvh_ctx* ctx, const rvh_frame* frame, const rvh_params* params, rvh_result* result,
                uint64_t* ticket) {
   if (!ctx || !ticket) return fail(RVH_EINVAL, "NULL argument");
-  int rc = check_args(frame, params, result);
+  int rc = check_args_impl(frame, params, result);
   if (rc) return rc;
   {
     std::lock_guard<std::mutex> lk(ctx->mu);
@@ -843,6 +840,7 @@ int rvh_wait(rvh_ctx* ctx, uint64_t ticket, int64_t timeout_us) {
 }  // extern "C"
 
 namespace rvh {
+int check_args(const rvh_frame* f, const rvh_params* p, const rvh_result* r) { return check_args_impl(f, p, r); }
 int set_error(int code, const std::string& msg) { return fail(code, msg); }
 bool device_ptr(const void* p) { return is_device_ptr(p); }
 int validate_host_offsets(const int32_t* off, int32_t n, int64_t np) { return check_host_offsets(off, n, np); }

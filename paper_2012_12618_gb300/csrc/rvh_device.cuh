@@ -169,12 +169,7 @@ constexpr float kDetErr3 = 3.65e-6f;
 // vertical direction, so most 3D trials do.
 constexpr float kRefineBand = 1e-4f;
 
-// Scale of the 2D scoring pass: it evaluates residuals 2^20 times larger
-// (exact: scaling by a power of two commutes with rounding) so that its
-// saturated square test resolves the threshold to within 2^-40 m^2/s^2.
-constexpr float kScoreScale = 0x1p20f;
-
-// FP32 row of a point plus its Doppler: (c, s, w, 2^20 w) or (a0, a1, a2, w).
+// FP32 row of a point plus its Doppler: (c, s, w, 0) or (a0, a1, a2, w).
 template <int DIM>
 __device__ __forceinline__ float4 row_f32(float az, float el, float w) {
   float s, c;
@@ -186,7 +181,7 @@ __device__ __forceinline__ float4 row_f32(float az, float el, float w) {
     s = __double2float_rn(sd);
     c = __double2float_rn(cd);
   }
-  if (DIM == 2) return make_float4(c, s, w, w * kScoreScale);
+  if (DIM == 2) return make_float4(c, s, w, 0.0f);
   float se, ce;
   if (fabsf(el) <= 3.1415925f) {
     sincosf(el, &se, &ce);

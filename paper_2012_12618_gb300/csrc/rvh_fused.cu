@@ -187,10 +187,24 @@ struct Rows64 {
   }
 };
 
+// FP64 rows computed from the frame's inputs in both models: the source of
+// the finishing pass, which runs after the CTA's row slot has moved on to
+// later clusters.
+template <int DIM>
+struct Rows64Inputs {
+  const FrameDesc* a;
+  int64_t o;
+  __device__ __forceinline__ double4_32a at(int j) const {
+    double t[3];
+    row_f64<DIM>(a->trig, a->az[o + j], DIM == 3 ? a->el[o + j] : 0.0f, t);
+    return make_double4_32a(t[0], t[1], t[2], (double)a->dop[o + j]);
+  }
+};
+
 // FP64 velocity of trial h in the oracle's exact rounding sequence.  Returns
 // false if rejected.
-template <int DIM>
-__device__ bool hyp_f64(const FrameDesc& a, const Rows64<DIM>& R, int ci, int h, int N, double v[3]) {
+template <int DIM, typename RS>
+__device__ bool hyp_f64(const FrameDesc& a, const RS& R, int ci, int h, int N, double v[3]) {
   int q[3];
   draw_minimal_set<DIM>(a.key, a.cluster_base + ci, h, N, q);
   const double4_32a s0 = R.at(q[0]), s1 = R.at(q[1]), s2 = R.at(DIM == 3 ? q[2] : q[0]);
@@ -422,7 +436,7 @@ __device__ __noinline__ void line_rows_and_threshold(const FrameDesc& a, const R
     const double y = ((double)a.dop[o + j] - vmin) * rv;
     pre[j] = make_double4_32a(x, y, 0.0, 0.0);
     const float y32 = __double2float_rn(y);
-    rows.put(j, make_float4(__double2float_rn(x), 1.0f, y32, y32 * kScoreScale));
+    rows.put(j, make_float4(__double2float_rn(x), 1.0f, y32, 0.0f));
   }
   __syncthreads();
   // Eq. eq:MAD read as the median absolute deviation of the normalised Doppler
@@ -547,7 +561,7 @@ __device__ __forceinline__ bool solve_normal(const double* t, int n_in, double v
 // fallback to the winning minimal-set velocity, heading atan2(vy, vx).
 // One thread.
 template <int DIM, bool EXT>
-__device__ __noinline__ void finish_cluster(const FrameDesc& a, const Rows64<DIM>& R, int ci, int N, int hstar, int n_in,
+__device__ __noinline__ void finish_cluster(const FrameDesc& a, const Rows64Inputs<DIM>& R, int ci, int N, int hstar, int n_in,
                                const double* t, const double* v64, bool has_v64) {
   double vout[3] = {v64[0], v64[1], v64[2]};
   int st = 0;
@@ -756,7 +770,7 @@ __device__ __noinline__ int local_opt_rounds(const FrameDesc& a, const RV rows, 
 
 template <int DIM, bool SMEM_ROWS, bool EXT>
 __device__ void process_cluster(const FrameDesc& a, const Smem& S, ClusterShared& cs, int ci, int hchunk,
-                                int pw, int hpl, int frame, FinishRec* fq, int* fq_n) {
+                                int pw, int hpl, int frame, FinishRec* fq, int* fq_n, double4_32a* cta_pre) {
   const int tid = threadIdx.x;
   const int64_t o = a.offsets[ci];
   const int64_t e = a.offsets[ci + 1];
@@ -777,7 +791,10 @@ __device__ void process_cluster(const FrameDesc& a, const Smem& S, ClusterShared
   } else {
     rows.p = a.rows_g + o;
   }
-  const Rows64<DIM> R = {&a, o, a.rows64_g + o};
+  // FP64 rows: the CTA's own slot when the cluster fits it (the slot is
+  // reused cluster after cluster and stays in L2), else the frame's
+  // per-point scratch
+  const Rows64<DIM> R = {&a, o, (SMEM_ROWS && cta_pre) ? cta_pre : a.rows64_g + o};
   long long t_stage = clock64();
   auto stage_done = [&](int k) {
     if (tid == 0) {
@@ -1088,7 +1105,9 @@ __global__ void __launch_bounds__(kThreads, RVH_MIN_BLOCKS) fused_kernel(const _
     if (threadIdx.x < n) {
       const FinishRec& q = fq[threadIdx.x];
       const FrameDesc& F = a.f[q.frame];
-      const Rows64<DIM> R = {&F, q.o, F.rows64_g + q.o};
+      // the CTA's row slot has moved on to later clusters: rows are
+      // recomputed for the (rare) fallback solve
+      const Rows64Inputs<DIM> R = {&F, q.o};
       finish_cluster<DIM, EXT>(F, R, q.ci, q.N, q.hstar, q.n_in, q.t, q.v64, q.has_v64 != 0);
     }
     __syncthreads();
@@ -1115,10 +1134,11 @@ __global__ void __launch_bounds__(kThreads, RVH_MIN_BLOCKS) fused_kernel(const _
     const FrameDesc& F = a.f[fc.x];
     const int ci = fc.y;
     const int64_t o = F.offsets[ci], e = F.offsets[ci + 1];
+    double4_32a* cta_pre = a.cta_rows64 ? a.cta_rows64 + (size_t)blockIdx.x * a.nmax_smem : nullptr;
     if (e - o <= (int64_t)a.nmax_smem || e < o) {
-      process_cluster<DIM, true, EXT>(F, S, cs, ci, a.hchunk, a.pw, a.hpl, fc.x, fq, &fq_n);
+      process_cluster<DIM, true, EXT>(F, S, cs, ci, a.hchunk, a.pw, a.hpl, fc.x, fq, &fq_n, cta_pre);
     } else {
-      process_cluster<DIM, false, EXT>(F, S, cs, ci, a.hchunk, a.pw, a.hpl, fc.x, fq, &fq_n);
+      process_cluster<DIM, false, EXT>(F, S, cs, ci, a.hchunk, a.pw, a.hpl, fc.x, fq, &fq_n, cta_pre);
     }
     __syncthreads();
     if (fq_n == kFinishBatch) flush();
@@ -1185,17 +1205,37 @@ size_t fused_smem_bytes(int nmax_smem, int hchunk) {
 }
 
 cudaError_t launch_worklist(const FusedArgs& a, cudaStream_t s) {
-  worklist_kernel<<<1, 1024, 0, s>>>(a);
+  worklist_kernel<<<1, kWorklistThreads, 0, s>>>(a);
   return cudaGetLastError();
 }
 
-cudaError_t fused_configure(int dim, size_t smem) {
-  const cudaFuncAttribute at = cudaFuncAttributeMaxDynamicSharedMemorySize;
-  cudaError_t e = dim == 2 ? cudaFuncSetAttribute(fused_kernel<2, false>, at, (int)smem)
-                           : cudaFuncSetAttribute(fused_kernel<3, false>, at, (int)smem);
-  if (e != cudaSuccess) return e;
-  return dim == 2 ? cudaFuncSetAttribute(fused_kernel<2, true>, at, (int)smem)
-                  : cudaFuncSetAttribute(fused_kernel<3, true>, at, (int)smem);
+bool fused_ext(const FusedArgs& a) {
+  bool ext = false;
+  for (int f = 0; f < a.n_frames; ++f)
+    ext = ext || a.f[f].lo_iters > 0 || a.f[f].confidence > 0.0 || a.f[f].line_model != 0;
+  return ext;
+}
+
+const void* fused_kernel_fn(int dim, bool ext) {
+  if (dim == 2) return ext ? (const void*)fused_kernel<2, true> : (const void*)fused_kernel<2, false>;
+  return ext ? (const void*)fused_kernel<3, true> : (const void*)fused_kernel<3, false>;
+}
+
+const void* worklist_kernel_fn() { return (const void*)worklist_kernel; }
+
+int fused_threads() { return kThreads; }
+
+cudaError_t fused_configure_max(int dim, int device) {
+  int optin = 0;
+  cudaError_t e = cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, device);
+  for (int ext = 0; ext < 2 && e == cudaSuccess; ++ext) {
+    const void* fn = fused_kernel_fn(dim, ext != 0);
+    cudaFuncAttributes fa;
+    e = cudaFuncGetAttributes(&fa, fn);
+    if (e == cudaSuccess)
+      e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, optin - (int)fa.sharedSizeBytes);
+  }
+  return e;
 }
 
 cudaError_t fused_occupancy(int dim, size_t smem, int* blocks_per_sm) {
@@ -1205,9 +1245,7 @@ cudaError_t fused_occupancy(int dim, size_t smem, int* blocks_per_sm) {
 }
 
 cudaError_t launch_fused(int dim, const FusedArgs& a, int grid, size_t smem, cudaStream_t s) {
-  bool ext = false;
-  for (int f = 0; f < a.n_frames; ++f)
-    ext = ext || a.f[f].lo_iters > 0 || a.f[f].confidence > 0.0 || a.f[f].line_model != 0;
+  const bool ext = fused_ext(a);
   if (dim == 2) {
     if (ext) fused_kernel<2, true><<<grid, kThreads, smem, s>>>(a);
     else fused_kernel<2, false><<<grid, kThreads, smem, s>>>(a);

@@ -65,13 +65,31 @@ struct FusedArgs {
   int hchunk;
   int pw, hpl;
   int direct;                // 1: one item per CTA, item = blockIdx.x (no work list)
+  // [grid * nmax_smem] FP64 rows, one slot per CTA, used for clusters of at
+  // most nmax_smem points (a working set that stays in L2); NULL: every
+  // cluster uses its frame's per-point rows64_g
+  double4_32a* cta_rows64;
 };
 
 size_t fused_smem_bytes(int nmax_smem, int hchunk);
-cudaError_t fused_configure(int dim, size_t smem);
+// Opts both instantiations of the fused kernel of this model dimension in to
+// the largest dynamic shared memory a block can have on `device` (the
+// opt-in maximum less the kernel's static shared memory).  Every caller
+// uses this one setting, so no caller lowers a limit another relies on.
+cudaError_t fused_configure_max(int dim, int device);
 cudaError_t fused_occupancy(int dim, size_t smem, int* blocks_per_sm);
 cudaError_t launch_worklist(const FusedArgs& a, cudaStream_t s);
 cudaError_t launch_fused(int dim, const FusedArgs& a, int grid, size_t smem, cudaStream_t s);
+// The instantiation a batch needs: with the extensions (local optimisation,
+// adaptive trial count, line model) when any frame uses one.
+bool fused_ext(const FusedArgs& a);
+// Kernel entry points and launch shapes, for graph nodes built by the host
+// (rvh_graph.cu): the fused kernel takes kThreads threads per CTA, the
+// work-list kernel one CTA of kWorklistThreads.
+const void* fused_kernel_fn(int dim, bool ext);
+const void* worklist_kernel_fn();
+int fused_threads();
+constexpr int kWorklistThreads = 1024;
 
 struct BaselineArgs {
   const float* az;

@@ -70,14 +70,9 @@ int setup_device(int dev, DeviceSetup** out) {
     e = cudaDeviceGetAttribute(&d.sms, cudaDevAttrMultiProcessorCount, dev);
     if (e != cudaSuccess) return rvh::set_error(RVH_ECUDA, cudaGetErrorString(e));
     const size_t smem = rvh::fused_smem_bytes(kNmaxSmem, kHchunk);
-    // opt the kernels in to (nearly) the device's per-block maximum, so this
-    // never lowers a limit that context-based launches rely on
-    int optin = 0;
-    e = cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
-    if (e != cudaSuccess) return rvh::set_error(RVH_ECUDA, cudaGetErrorString(e));
-    const size_t allow = std::max(smem, (size_t)optin > 8192 ? (size_t)optin - 8192 : smem);
     for (int dim = 2; dim <= 3; ++dim) {
-      e = rvh::fused_configure(dim, allow);
+      // the same opt-in as context launches use: neither lowers the other's limit
+      e = rvh::fused_configure_max(dim, dev);
       if (e == cudaSuccess) e = rvh::fused_occupancy(dim, smem, &d.occ[dim]);
       if (e != cudaSuccess) return rvh::set_error(RVH_ECUDA, std::string("kernel set-up: ") + cudaGetErrorString(e));
       if (d.occ[dim] < 1) d.occ[dim] = 1;
@@ -88,46 +83,26 @@ int setup_device(int dev, DeviceSetup** out) {
   return RVH_OK;
 }
 
-float round_up_f(double x) {
-  float f = (float)x;
-  return ((double)f < x) ? std::nextafter(f, INFINITY) : f;
-}
-float round_down_f(double x) {
-  float f = (float)x;
-  return ((double)f > x) ? std::nextafter(f, -INFINITY) : f;
-}
-
 }  // namespace
 
 extern "C" int rvh_estimate_noalloc(const rvh_frame* f, const rvh_params* p, rvh_result* r, void* stream) {
-  if (!f || !p || !r) return rvh::set_error(RVH_EINVAL, "frame, params and result must be non-NULL");
-  if (f->n_clusters < 0 || f->n_points < 0) return rvh::set_error(RVH_EINVAL, "negative size");
-  if (f->n_clusters > kMaxClusters || f->n_points > kMaxPoints)
+  if (f && (f->n_clusters > kMaxClusters || f->n_points > kMaxPoints))
     return rvh::set_error(RVH_EINVAL, "frame exceeds the no-allocation limits (" + std::to_string(kMaxClusters) +
                                           " clusters, " + std::to_string(kMaxPoints) + " points)");
-  if (p->model_dim != 2 && p->model_dim != 3) return rvh::set_error(RVH_EINVAL, "model_dim must be 2 or 3");
-  if ((p->model_dim == 3) != (f->elevation != nullptr))
-    return rvh::set_error(RVH_EINVAL, "model_dim 3 needs elevation, model_dim 2 needs elevation == NULL");
-  if (p->num_hypotheses < 1) return rvh::set_error(RVH_EINVAL, "num_hypotheses must be >= 1");
-  if (std::isnan(p->inlier_threshold) || p->inlier_threshold < 0 || std::isnan(p->cond_eps))
-    return rvh::set_error(RVH_EINVAL, "inlier_threshold must be >= 0 and cond_eps not NaN");
-  if (p->first_cluster < 0 || (int64_t)p->first_cluster + f->n_clusters > 0x7fffffffLL)
-    return rvh::set_error(RVH_EINVAL, "first_cluster out of range");
-  if (p->refine_iterations < 0 || p->refine_iterations > RVH_MAX_REFINE_ITERATIONS)
-    return rvh::set_error(RVH_EINVAL, "refine_iterations out of range [0, RVH_MAX_REFINE_ITERATIONS]");
-  if (!(p->confidence >= 0.0 && p->confidence < 1.0)) return rvh::set_error(RVH_EINVAL, "confidence must be in [0, 1)");
-  if (p->confidence > 0.0 && p->trial_block != 0 &&
-      (p->trial_block < 32 || p->trial_block > 1024 || p->trial_block % 32 != 0))
-    return rvh::set_error(RVH_EINVAL, "trial_block must be 0 or a multiple of 32 in [32, 1024]");
-  if (p->hypothesis_model != RVH_MODEL_VELOCITY_PROFILE && p->hypothesis_model != RVH_MODEL_PAPER_LINE)
-    return rvh::set_error(RVH_EINVAL, "hypothesis_model must be RVH_MODEL_VELOCITY_PROFILE or RVH_MODEL_PAPER_LINE");
-  if (p->hypothesis_model == RVH_MODEL_PAPER_LINE && (p->model_dim != 2 || p->refine_iterations != 0))
-    return rvh::set_error(RVH_EINVAL, "hypothesis_model RVH_MODEL_PAPER_LINE needs model_dim 2 and refine_iterations 0");
-  if (f->n_clusters == 0) return f->n_points == 0 ? RVH_OK : rvh::set_error(RVH_EINVAL, "points without clusters");
-  const void* ptrs[11] = {f->azimuth, f->doppler, f->cluster_offsets, r->vx, r->vy, r->heading, r->inlier_count,
-                          r->best_hypothesis, r->status, r->inlier_mask, p->model_dim == 3 ? f->elevation : f->azimuth};
-  for (const void* q : ptrs)
-    if (!q || !rvh::device_ptr(q)) return rvh::set_error(RVH_EINVAL, "every input and output must be device memory");
+  int rc = rvh::check_args(f, p, r);  // the checks of rvh_estimate
+  if (rc) return rc;
+  if (f->n_clusters == 0) return RVH_OK;
+  // what the launch reads or writes must be device memory: per-point arrays
+  // when there are points, per-cluster arrays always
+  const bool pts = f->n_points > 0;
+  const void* offs = f->cluster_offsets;
+  const void* need[10] = {offs, r->vx, r->vy, r->heading, r->inlier_count, r->best_hypothesis, r->status,
+                          pts ? (const void*)f->azimuth : offs, pts ? (const void*)f->doppler : offs,
+                          pts ? (const void*)r->inlier_mask : offs};
+  for (const void* q : need)
+    if (!rvh::device_ptr(q)) return rvh::set_error(RVH_EINVAL, "every input and output must be device memory");
+  if (pts && p->model_dim == 3 && !rvh::device_ptr(f->elevation))
+    return rvh::set_error(RVH_EINVAL, "every input and output must be device memory");
   if (r->vz && !rvh::device_ptr(r->vz)) return rvh::set_error(RVH_EINVAL, "vz must be device memory or NULL");
   if (r->threshold && !rvh::device_ptr(r->threshold))
     return rvh::set_error(RVH_EINVAL, "threshold must be device memory or NULL");
@@ -136,46 +111,16 @@ extern "C" int rvh_estimate_noalloc(const rvh_frame* f, const rvh_params* p, rvh
   cudaError_t e = cudaGetDevice(&dev);
   if (e != cudaSuccess || dev < 0 || dev >= kMaxDevices) return rvh::set_error(RVH_ECUDA, "no current device");
   DeviceSetup* d = nullptr;
-  int rc = setup_device(dev, &d);
+  rc = setup_device(dev, &d);
   if (rc) return rc;
 
   const int dim = p->model_dim;
   rvh::FusedArgs a;
-  memset(&a, 0, sizeof(a));
+  memset(&a, 0, sizeof(a));  // cta_rows64 = NULL: FP64 rows in the per-point array below
   rvh::FrameDesc& fd = a.f[0];
-  const double eps = p->cond_eps > 0 ? p->cond_eps : (dim == 2 ? 1e-4 : 1e-6);
-  const double eD = (dim == 2 ? 5.98e-7 : 3.65e-6) + 0x1p-50;
-  fd.az = f->azimuth;
-  fd.el = f->elevation;
-  fd.dop = f->doppler;
-  fd.offsets = f->cluster_offsets;
-  fd.n_clusters = f->n_clusters;
-  fd.H = p->num_hypotheses;
-  fd.n_points = f->n_points;
-  fd.rows_g = (float4*)(d->scratch + kWorklistBytes + kCounterBytes);
-  fd.rows64_g = (double4_32a*)(d->scratch + kWorklistBytes + kCounterBytes + kRowsBytes);
-  fd.trig = d->trig;
-  fd.tau = p->inlier_threshold;
-  fd.eps = eps;
-  fd.tau32.lo = round_down_f(p->inlier_threshold);
-  fd.tau32.hi = round_up_f(p->inlier_threshold);
-  fd.acc = round_up_f(eps + eD);
-  fd.rej = (eps - eD > 0) ? round_down_f(eps - eD) : -1.0f;
-  fd.key = make_uint2((uint32_t)(p->seed & 0xFFFFFFFFu), (uint32_t)(p->seed >> 32));
-  fd.cluster_base = p->first_cluster;
-  fd.lo_iters = p->refine_iterations;
-  fd.confidence = p->confidence;
-  fd.trial_block = p->confidence > 0.0 ? (p->trial_block ? p->trial_block : RVH_DEFAULT_TRIAL_BLOCK) : 0;
-  fd.line_model = p->hypothesis_model == RVH_MODEL_PAPER_LINE ? 1 : 0;
-  fd.vx = r->vx;
-  fd.vy = r->vy;
-  fd.vz = r->vz;
-  fd.heading = r->heading;
-  fd.inlier_count = r->inlier_count;
-  fd.best = r->best_hypothesis;
-  fd.status = r->status;
-  fd.mask = r->inlier_mask;
-  fd.threshold = r->threshold;
+  rvh::fill_desc(d->trig, fd, *f, *p, f->azimuth, f->elevation, f->doppler, f->cluster_offsets,
+                 (float4*)(d->scratch + kWorklistBytes + kCounterBytes),
+                 (double4_32a*)(d->scratch + kWorklistBytes + kCounterBytes + kRowsBytes), *r);
   a.n_frames = 1;
   a.n_items = f->n_clusters;
   a.worklist = (int2*)d->scratch;

@@ -60,8 +60,8 @@ struct AosRows {
   __device__ __forceinline__ void put(int j, float4 v) const { p[j] = v; }
 };
 
-// Packed FP32 pairs (fma.rn.f32x2 / add.rn.f32x2 round each half like the
-// scalar instruction, so results are those of fmaf / FP32 add per element).
+// Packed FP32 pairs (fma.rn.f32x2 rounds each half like the scalar
+// instruction, so results are those of fmaf per element).
 __device__ __forceinline__ unsigned long long pack2(float lo, float hi) {
   unsigned long long r;
   asm("mov.b64 %0, {%1, %2};" : "=l"(r) : "f"(lo), "f"(hi));
@@ -76,78 +76,73 @@ __device__ __forceinline__ unsigned long long fma2(unsigned long long a, unsigne
   asm("fma.rn.f32x2 %0, %1, %2, %3;" : "=l"(d) : "l"(a), "l"(b), "l"(c));
   return d;
 }
-__device__ __forceinline__ unsigned long long add2(unsigned long long a, unsigned long long b) {
-  unsigned long long d;
-  asm("add.rn.f32x2 %0, %1, %2;" : "=l"(d) : "l"(a), "l"(b));
+// Appends the sign bit of e to a 32-bit history of sign bits: the high word
+// of (acc:e) << 1, i.e. (acc << 1) | (e >> 31), one funnel shift on the
+// integer pipe.
+__device__ __forceinline__ uint32_t push_sign(uint32_t acc, float e) {
+  uint32_t d;
+  asm("shf.l.clamp.b32 %0, %1, %2, 1;" : "=r"(d) : "r"(__float_as_uint(e)), "r"(acc));
   return d;
 }
-// min(1, max(0, C - r^2)) in one saturated FMA (NaN gives 0).  With
-// C >= t^2 + 1 it is 1 whenever |r| <= t, and 0 once r^2 >= C; in between a
-// fraction, so sums of it bound the count of |r| <= t from above.
-__device__ __forceinline__ float sat_square(float r, float C) {
-  float e;
-  asm("{.reg .f32 n; neg.f32 n, %1; fma.rn.sat.f32 %0, n, %1, %2;}" : "=f"(e) : "f"(r), "f"(C));
-  return e;
-}
-// 1.0f if |r| <= t else 0.0f (false for NaN)
-__device__ __forceinline__ float in_band(float r, float t) {
-  float e;
-  asm("{.reg .f32 a; abs.f32 a, %1; set.le.f32.f32 %0, a, %2;}" : "=f"(e) : "f"(r), "f"(t));
-  return e;
+
+// -C with C the smallest float above thi^2 rounded up: C > thi^2, so
+// r^2 < C for every |r| <= thi, and r^2 < C holds beyond thi only for r^2
+// within two ulps of thi^2.
+__device__ __forceinline__ float neg_count_bound(float thi) {
+  return -__uint_as_float(__float_as_uint(__fmul_ru(thi, thi)) + 1u);
 }
 
 // a4 over tiled rows: the residuals of two points per instruction.  Lane l
 // handles trial sub-group l / PW and point quads l % PW, l % PW + PW, ...;
 // the rows stage pads the last quad with NaN Dopplers, which never count.
 // Per element the arithmetic is resid_f32's: w + nz z + ny y + nx x by fmaf.
-// 2D evaluates it 2^20 times larger (the rows' fourth slot holds 2^20 w, the
-// velocity is scaled likewise, both exactly) and counts with the saturated
-// square test against C = 2^40 thi^2 + 1 rounded up, which keeps the count
-// on the FP32 pipe: U_h >= #{|r32| <= thi}, exceeding it only by points
-// whose squared residual lies within 2^-40 of thi^2.  3D counts with FSET.
+// The test is e = r r - C (one packed FMA for two points, exact until its
+// final rounding, which keeps the sign): e < 0 exactly when r^2 < C, and C
+// exceeds thi^2 (neg_count_bound), so the count U_h is an upper bound of
+// #{|r32| <= thi} that exceeds it only by points within two ulps of thi^2.
+// NaN residuals (NaN Dopplers, the padding) give the canonical NaN, whose
+// sign bit is clear, so they do not count (a NaN that did would only loosen
+// the bound).  The
+// count leaves the FP32 pipe: sign bits are shifted into a 32-bit history
+// (push_sign, integer pipe) and popcounted every block of quads (8 quads = 32
+// points fill the history exactly; 2D uses blocks of 4 with a reset, which
+// measured faster for its shorter loop body).
 template <int DIM, int PW, int HPL>
 __device__ __forceinline__ void phase_a_tiles(const TileRows rows, int N, const Smem& S, int nh) {
   constexpr int NHL = 32 / PW;
   constexpr int G = NHL * HPL;
+  constexpr int BLOCK = DIM == 2 ? 4 : 8;  // quads per popcount
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const int hl = lane / PW, pl = lane % PW;
   const int ngroups = (nh + G - 1) / G;
   const int nq = (N + 3) >> 2;
   for (int g = warp; g < ngroups; g += kWarps) {
     const int base = g * G + hl * HPL;
-    unsigned long long nx[HPL], ny[HPL], nz[HPL], acc[HPL];
-    float th[HPL];
+    unsigned long long nx[HPL], ny[HPL], nz[HPL], nc[HPL];
+    uint32_t bits[HPL];
+    int cnt[HPL];
 #pragma unroll
     for (int m = 0; m < HPL; ++m) {
       const int h = base + m;
       const float4 v = (h < nh) ? S.hyp[h] : make_float4(0.f, 0.f, 0.f, __int_as_float(0x7fc00000));
-      if (DIM == 2) {
-        const float sx = v.x * kScoreScale, sy = v.y * kScoreScale, st = v.w * kScoreScale;
-        nx[m] = pack2(sx, sx);
-        ny[m] = pack2(sy, sy);
-        th[m] = __fadd_ru(__fmul_ru(st, st), 1.0f);  // C = (2^20 thi)^2 + 1, rounded up
-      } else {
-        nx[m] = pack2(v.x, v.x);
-        ny[m] = pack2(v.y, v.y);
-        th[m] = v.w;
-      }
+      nx[m] = pack2(v.x, v.x);
+      ny[m] = pack2(v.y, v.y);
       nz[m] = pack2(v.z, v.z);
-      acc[m] = 0ull;
+      const float c = neg_count_bound(v.w);
+      nc[m] = pack2(c, c);
+      bits[m] = 0u;
+      cnt[m] = 0;
     }
-    for (int q = pl; q < nq; q += PW) {
-      const float4 c = rows.quad(q, 0), sn = rows.quad(q, 1), z = rows.quad(q, DIM == 2 ? 3 : 2);
+    auto quad = [&](int q) {
+      const float4 c = rows.quad(q, 0), sn = rows.quad(q, 1), w = rows.quad(q, DIM == 2 ? 2 : 3);
       const unsigned long long c01 = pack2(c.x, c.y), c23 = pack2(c.z, c.w);
       const unsigned long long s01 = pack2(sn.x, sn.y), s23 = pack2(sn.z, sn.w);
-      unsigned long long w01, w23, z01 = 0ull, z23 = 0ull;
-      if (DIM == 2) {  // 2^20 w
-        w01 = pack2(z.x, z.y);
-        w23 = pack2(z.z, z.w);
-      } else {
-        const float4 w = rows.quad(q, 3);
+      const unsigned long long w01 = pack2(w.x, w.y), w23 = pack2(w.z, w.w);
+      unsigned long long z01 = 0ull, z23 = 0ull;
+      if (DIM == 3) {
+        const float4 z = rows.quad(q, 2);
         z01 = pack2(z.x, z.y);
         z23 = pack2(z.z, z.w);
-        w01 = pack2(w.x, w.y);
-        w23 = pack2(w.z, w.w);
       }
 #pragma unroll
       for (int m = 0; m < HPL; ++m) {
@@ -159,24 +154,28 @@ __device__ __forceinline__ void phase_a_tiles(const TileRows rows, int N, const 
           r01 = fma2(nx[m], c01, fma2(ny[m], s01, fma2(nz[m], z01, w01)));
           r23 = fma2(nx[m], c23, fma2(ny[m], s23, fma2(nz[m], z23, w23)));
         }
-        float a0, a1, a2, a3;
-        unpack2(r01, a0, a1);
-        unpack2(r23, a2, a3);
-        if (DIM == 2) {
-          acc[m] = add2(acc[m], pack2(sat_square(a0, th[m]), sat_square(a1, th[m])));
-          acc[m] = add2(acc[m], pack2(sat_square(a2, th[m]), sat_square(a3, th[m])));
-        } else {
-          acc[m] = add2(acc[m], pack2(in_band(a0, th[m]), in_band(a1, th[m])));
-          acc[m] = add2(acc[m], pack2(in_band(a2, th[m]), in_band(a3, th[m])));
-        }
+        float e0, e1, e2, e3;
+        unpack2(fma2(r01, r01, nc[m]), e0, e1);
+        unpack2(fma2(r23, r23, nc[m]), e2, e3);
+        bits[m] = push_sign(push_sign(push_sign(push_sign(bits[m], e0), e1), e2), e3);
+      }
+    };
+    int q = pl;
+    for (; q + (BLOCK - 1) * PW < nq; q += BLOCK * PW) {
+#pragma unroll
+      for (int u = 0; u < BLOCK; ++u) quad(q + u * PW);
+#pragma unroll
+      for (int m = 0; m < HPL; ++m) {
+        cnt[m] += __popc(bits[m]);
+        if (BLOCK < 8) bits[m] = 0u;  // a block of 8 quads shifts all 32 bits out
       }
     }
-    float cnt[HPL];
+#pragma unroll
+    for (int m = 0; m < HPL; ++m) bits[m] = 0u;
+    for (; q < nq; q += PW) quad(q);  // fewer than BLOCK quads
 #pragma unroll
     for (int m = 0; m < HPL; ++m) {
-      float lo, hi;
-      unpack2(acc[m], lo, hi);
-      cnt[m] = lo + hi;  // integers below 2^24 (3D); 2D: at least the count (rounding is monotone)
+      cnt[m] += __popc(bits[m]);
 #pragma unroll
       for (int o = PW / 2; o > 0; o >>= 1) cnt[m] += __shfl_xor_sync(0xffffffffu, cnt[m], o);
     }
@@ -184,7 +183,7 @@ __device__ __forceinline__ void phase_a_tiles(const TileRows rows, int N, const 
 #pragma unroll
       for (int m = 0; m < HPL; ++m) {
         const int h = base + m;
-        if (h < nh && S.kind[h] == kHypNormal) S.U[h] = (int)cnt[m];  // floor
+        if (h < nh && S.kind[h] == kHypNormal) S.U[h] = cnt[m];
       }
     }
   }

@@ -125,6 +125,10 @@ struct Server {
   bool stop = false;
   std::thread thread;
   std::string thread_error;
+  // graphs of the step launch, per step slot (each slot has its own stream)
+  // x model dimension x extensions x work list
+  std::vector<std::unique_ptr<LaunchGraph>> graphs;
+  int64_t n_steps = 0, n_graph_replays = 0;
 
   int finalize_step(Step& st);   // requires mu held
   void loop();
@@ -171,6 +175,7 @@ int server_create(rvh_ctx* ctx, Server** out) {
       return set_error(RVH_ENOMEM, "serving pool too small for the step scratch");
     }
   }
+  for (size_t k = 0; k < s->steps.size() * 8; ++k) s->graphs.emplace_back(new LaunchGraph());
   s->thread = std::thread([s] { s->loop(); });
   *out = s;
   return RVH_OK;
@@ -191,6 +196,7 @@ void server_destroy(Server* s) {
   }
   cudaStreamSynchronize(s->copy_stream);
   cudaStreamDestroy(s->copy_stream);
+  s->graphs.clear();
   for (auto& kv : s->reqs)
     if (kv.second->copied) cudaEventDestroy(kv.second->copied);
   cudaFreeHost(s->pinned);
@@ -391,7 +397,7 @@ void Server::loop() {
     for (uint64_t id : take) {
       Req& q = *reqs[id];
       char* b = (char*)pool + q.dev_off;
-      fill_desc(ctx, a.f[nf], q.frame, q.params, q.frame.azimuth, q.frame.elevation, q.frame.doppler,
+      fill_desc(ctx_trig(ctx), a.f[nf], q.frame, q.params, q.frame.azimuth, q.frame.elevation, q.frame.doppler,
                 q.frame.cluster_offsets, (float4*)b, (double4_32a*)(b + q.rows64_off), q.dev);
       cudaStreamWaitEvent(slot->stream, q.copied, 0);
       if (launch_threshold_fill(q.dev.threshold, q.frame.n_clusters,
@@ -410,7 +416,30 @@ void Server::loop() {
       Hmax = std::max(Hmax, a.f[i].trial_block > 0 ? std::min(a.f[i].trial_block, a.f[i].H) : a.f[i].H);
     choose_schedule(ctx, dimsel ? 3 : 2, Hmax, &a.pw, &a.hpl);
     int rc = RVH_OK;
-    if (n_items > 0) rc = launch_batch(ctx, a, dimsel ? 3 : 2, slot->stream, nullptr, nullptr);
+    if (n_items > 0) {
+      const int dim = dimsel ? 3 : 2;
+      if (ctx_graphs(ctx)) {
+        // the slot's graph for this kernel instantiation and node list,
+        // replayed with this step's batch
+        int grid = 1;
+        size_t smem = 0;
+        rc = prepare_launch(ctx, a, dim, &grid, &smem);
+        if (rc == RVH_OK) {
+          const size_t k = (size_t)(slot - steps.data()) * 8 + (size_t)dimsel * 4 + (fused_ext(a) ? 2 : 0) +
+                           (a.direct ? 0 : 1);
+          LaunchGraph& g = *graphs[k];
+          const int64_t r0 = g.replays;
+          if (g.launch(a, dim, grid, smem, !a.direct, slot->stream) != cudaSuccess) {
+            cudaGetLastError();
+            rc = RVH_ECUDA;
+          }
+          n_graph_replays += g.replays - r0;
+        }
+      } else {
+        rc = launch_batch(ctx, a, dim, slot->stream, nullptr, nullptr);
+      }
+      ++n_steps;
+    }
     if (rc != RVH_OK) thread_error = "launch failed";
     // outputs that go to host memory: device -> pinned staging
     for (uint64_t id : take) {
@@ -429,6 +458,12 @@ void Server::loop() {
     slot->busy = true;
     slot->reqs = take;
   }
+}
+
+void server_counts(Server* s, int64_t* steps, int64_t* graph_replays) {
+  std::lock_guard<std::mutex> lk(s->mu);
+  *steps = s->n_steps;
+  *graph_replays = s->n_graph_replays;
 }
 
 int server_poll(Server* s, uint64_t ticket) {

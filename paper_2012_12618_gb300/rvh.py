@@ -64,7 +64,8 @@ class rvh_stats(ctypes.Structure):
                 ("kernel_ms", ctypes.c_float), ("grid", ctypes.c_int32), ("points_per_warp", ctypes.c_int32),
                 ("hyps_per_lane", ctypes.c_int32), ("phase_cycles", ctypes.c_int64 * 6),
                 ("refined_hypotheses", ctypes.c_int64), ("graph_replays", ctypes.c_int64),
-                ("kernel_launches", ctypes.c_int32)]
+                ("kernel_launches", ctypes.c_int32), ("graph_builds", ctypes.c_int64),
+                ("serving_steps", ctypes.c_int64), ("serving_graph_replays", ctypes.c_int64)]
 
 
 # exported symbols and their ctypes signatures (restype, argtypes)

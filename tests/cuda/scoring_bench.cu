@@ -7,9 +7,10 @@
 // phase_a_tiles<DIM, 1, 4> (the schedule the library picks for H >= 1024)
 // `reps` times.  The grid is 4 CTAs of 256 threads per SM, as in the fused
 // kernel.  The counts of the last pass are checked against a host
-// evaluation of the same FP32 formula (fmaf chain): 3D counts |r| <= thi
-// exactly; the 2D pass (saturated square test) must give an upper bound
-// within the points whose |r| exceeds thi by at most 1e-6.
+// evaluation of the same FP32 formula (fmaf chain): each count must be an
+// upper bound of #{|r| <= thi} that exceeds it only by points whose |r|
+// exceeds thi by at most 1e-6 (the pass counts r^2 < C with C two ulps
+// above thi^2).
 //
 //   scoring_bench <dim 2|3> <N <= 1536> <reps>
 // Output: "key=value ..." (ms, pairs, pairs_per_s, sms, ctas_per_sm, mismatches).
@@ -89,7 +90,7 @@ int run(int N, int reps) {
     const double a0 = cos(t) * cos(e), a1 = sin(t) * cos(e), a2 = sin(e);
     double w = vx * a0 + vy * a1 + vz * a2 + noise(g);
     if (j % 5 == 4) w = U01(g) * 2.0 * sqrt(sp * sp + vz * vz);
-    pts[j] = DIM == 2 ? make_float4((float)a0, (float)a1, (float)w, (float)w * kScoreScale)
+    pts[j] = DIM == 2 ? make_float4((float)a0, (float)a1, (float)w, 0.0f)
                       : make_float4((float)a0, (float)a1, (float)a2, (float)w);
   }
   // trial records (-X, -Y, -Z, thi) scattered around the true velocity
@@ -139,7 +140,7 @@ int run(int N, int reps) {
       c += (std::fabs(r) <= v.w) ? 1 : 0;
       c_wide += (std::fabs(r) <= v.w + 1e-6f) ? 1 : 0;
     }
-    mism += DIM == 2 ? (Ug[h] < c || Ug[h] > c_wide) : (c != Ug[h]);
+    mism += (Ug[h] < c || Ug[h] > c_wide);
     total_in += c;
   }
   const double pairs = (double)grid * reps * (double)kH * N;

@@ -69,6 +69,11 @@ def test_params_layout_and_refine_range():
         assert rvh.rvh_estimate_noalloc(f, p, r, None) == rvh.RVH_EINVAL
         msg = rvh.rvh_last_error(None)
         assert "confidence" in msg or "trial_block" in msg, msg
+    # the checks are rvh_estimate's: point arrays are needed once there are points
+    p = rvh.make_params(2, 8, 0.1, 1)
+    pts = rvh.rvh_frame(None, None, None, None, 1, 5)
+    assert rvh.rvh_estimate_noalloc(pts, p, r, None) == rvh.RVH_EINVAL
+    assert "azimuth" in rvh.rvh_last_error(None)
     for dim, model, iters in ((2, 2, 0), (2, -1, 0), (3, 1, 0), (2, 1, 2)):
         p = rvh.make_params(dim, 8, 0.1, 1, refine_iterations=iters, hypothesis_model=model)
         assert rvh.rvh_estimate_noalloc(f, p, r, None) == rvh.RVH_EINVAL
@@ -87,12 +92,16 @@ def test_result_layout_matches_the_header(tmp_path):
     src = tmp_path / "layout.c"
     src.write_text(
         '#include <stddef.h>\n#include <stdio.h>\n#include "rvh.h"\n'
-        'int main(void) { printf("%zu %zu %zu\\n", sizeof(rvh_result), offsetof(rvh_result, inlier_mask),'
-        ' offsetof(rvh_result, threshold)); return 0; }\n')
+        'int main(void) { printf("%zu %zu %zu %zu %zu %zu\\n", sizeof(rvh_result), offsetof(rvh_result, inlier_mask),'
+        ' offsetof(rvh_result, threshold), sizeof(rvh_stats), offsetof(rvh_stats, graph_builds),'
+        ' offsetof(rvh_stats, serving_graph_replays)); return 0; }\n')
     exe = tmp_path / "layout"
     inc = os.path.join(os.path.dirname(os.path.dirname(os.path.abspath(__file__))), "include")
     subprocess.run([cc, "-I", inc, str(src), "-o", str(exe)], check=True)
-    size, mask_off, thr_off = map(int, subprocess.run([str(exe)], check=True, capture_output=True,
-                                                      text=True).stdout.split())
+    size, mask_off, thr_off, ssize, gb_off, sgr_off = map(int, subprocess.run(
+        [str(exe)], check=True, capture_output=True, text=True).stdout.split())
     assert size == ctypes.sizeof(rvh.rvh_result)
     assert mask_off == rvh.rvh_result.inlier_mask.offset and thr_off == rvh.rvh_result.threshold.offset
+    # rvh_stats, with the graph and serving counters at its end
+    assert ssize == ctypes.sizeof(rvh.rvh_stats)
+    assert gb_off == rvh.rvh_stats.graph_builds.offset and sgr_off == rvh.rvh_stats.serving_graph_replays.offset

@@ -40,3 +40,21 @@ def test_scoring_pass_counts_and_rate(exe, dim, n):
     frac = float(d["pairs_per_s"]) * 2 * dim / (int(d["sms"]) * FP32_PEAK_FLOP_PER_CLK_SM * 2.07e9)
     print(f"scoring pass dim={dim} N={n}: {float(d['pairs_per_s']):.3e} pairs/s, FP32 fraction {frac:.3f}")
     assert frac > 0.05, d
+
+
+def test_fp64_rate(tmp_path):
+    """The FP64 FMA rate the design weighs FP64 work by (tests/cuda/fp64_rate.cu)."""
+    torch = pytest.importorskip("torch")
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    out = str(tmp_path / "fp64_rate")
+    cmd = [build.nvcc(), *build.ARCH, *build.FLAGS, os.path.join(HERE, "cuda", "fp64_rate.cu"), "-o", out]
+    subprocess.run(cmd, check=True, capture_output=True)
+    r = subprocess.run([out, "4096"], capture_output=True, text=True, timeout=300)
+    assert r.returncode == 0, r.stdout + r.stderr
+    d = dict(kv.split("=") for kv in r.stdout.split() if "=" in kv)
+    assert d["check"] == "1", d
+    print(f"FP64 FMA rate: {float(d['dfma_per_s']):.3e}/s, {float(d['dfma_per_clk_sm']):.3f} per SM per cycle "
+          f"at {d['clock_mhz']} MHz")
+    assert float(d["dfma_per_clk_sm"]) > 0.5, d
+

@@ -117,6 +117,46 @@ def test_serving_frames_equal_the_oracle(torch):
         ctx.close()
 
 
+def test_serving_steps_replay_graphs(torch):
+    """Serving steps launch through CUDA graphs: a slot's graph for a kernel
+    instantiation and node list is built once and replayed by later steps
+    with their own batches, and results stay those of the frames alone."""
+    dev = torch.device("cuda", 0)
+    frames = _frames()
+    ctx = rvh.Context(0)
+    try:
+        inputs, alone = [], []
+        for f, w, seed in frames:
+            t = [None if x is None else torch.from_numpy(x).to(dev) for x in (f.azimuth, f.doppler, f.offsets,
+                                                                               f.elevation)]
+            frame = rvh.make_frame(*t)
+            params = rvh.make_params(w.model_dim, w.num_hypotheses, w.tau, seed)
+            outs = rvh.alloc_outputs(f.n_clusters, f.n_points, dev)
+            ctx.check(rvh.rvh_estimate(ctx.handle, frame, params, rvh.make_result(outs), None), "estimate")
+            torch.cuda.synchronize()
+            alone.append(_np(outs, f.n_points))
+            inputs.append((t, frame, params))
+        for wave in range(8):
+            tickets = []
+            for i in (wave % len(frames), (wave + 3) % len(frames)):
+                f = frames[i][0]
+                outs = rvh.alloc_outputs(f.n_clusters, f.n_points, dev)
+                tk = ctypes.c_uint64(0)
+                ctx.check(rvh.rvh_submit(ctx.handle, inputs[i][1], inputs[i][2], rvh.make_result(outs), tk), "submit")
+                tickets.append((i, tk.value, outs))
+            for i, tk, outs in tickets:
+                assert rvh.rvh_wait(ctx.handle, tk, 30_000_000) == rvh.RVH_OK, rvh.rvh_last_error(None)
+                torch.cuda.synchronize()
+                _same(_np(outs, frames[i][0].n_points), alone[i])
+        st = rvh.rvh_stats()
+        ctx.check(rvh.rvh_get_stats(ctx.handle, st), "stats")
+        # at most one graph per slot (3) x dimension (2) x work list or not (2) is built
+        assert st.serving_steps >= 8 and st.serving_graph_replays >= st.serving_steps - 12, \
+            (st.serving_steps, st.serving_graph_replays)
+    finally:
+        ctx.close()
+
+
 def test_extension_frames_same_alone_and_in_the_mix(torch):
     """Frames that use the extensions (local optimisation, adaptive trial
     count, Alg. 1's line model) batched with plain frames: a batch holding
