@@ -387,6 +387,11 @@ def main():
     ap.add_argument("--clustering-only", type=int, default=0, metavar="STEPS",
                     help="time only the clustering stage and pipeline on the traffic scene (3 warm-up calls, then "
                          "STEPS timed ones) and print that object")
+    ap.add_argument("--strong", action="store_true",
+                    help="strong scaling: the ranks split one frame into contiguous cost-balanced cluster ranges "
+                         "(partition.rank_shard, first_cluster = range start) instead of one frame each; rank 0 "
+                         "checks, after the timed steps, that the merged results equal its own estimate of the "
+                         "whole frame")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-gpu-baseline", action="store_true")
     ap.add_argument("--schedule", default="",
@@ -427,8 +432,22 @@ def main():
     wname = args.workload
     w = synth.WORKLOADS[wname]
     dim = w.model_dim
-    # weak scaling: every rank estimates its own frame (independent sensors)
-    f = synth.make_frame(w, gen_seed=w.gen_seed + 1000 * rank)
+    first_cluster = 0
+    whole = None
+    if args.strong:
+        # strong scaling: every rank estimates its share of one frame
+        import dataclasses
+        from paper_2012_12618_gb300 import partition
+        whole = synth.make_frame(w)
+        sh = partition.rank_shard(whole.azimuth, whole.doppler, whole.offsets, w.num_hypotheses, rank, ws,
+                                  whole.elevation)
+        f = dataclasses.replace(whole, azimuth=sh.azimuth, doppler=sh.doppler, offsets=sh.offsets,
+                                elevation=sh.elevation, truth_v=whole.truth_v[sh.c0:sh.c1],
+                                outlier=whole.outlier[sh.p0:sh.p1], band=whole.band[sh.p0:sh.p1])
+        first_cluster = sh.c0
+    else:
+        # weak scaling: every rank estimates its own frame (independent sensors)
+        f = synth.make_frame(w, gen_seed=w.gen_seed + 1000 * rank)
     nc, npts = f.n_clusters, f.n_points
     sizes = np.diff(f.offsets).astype(np.int64)
     pairs = int(sizes.sum()) * w.num_hypotheses
@@ -443,7 +462,8 @@ def main():
     d_off = torch.from_numpy(f.offsets).to(dev)
     outs = rvh.alloc_outputs(nc, npts, dev)
     frame = rvh.make_frame(d_az, d_dop, d_off, d_el)
-    params = rvh.make_params(dim, w.num_hypotheses, w.tau, w.seed, refine_iterations=args.refine_iterations)
+    params = rvh.make_params(dim, w.num_hypotheses, w.tau, w.seed, refine_iterations=args.refine_iterations,
+                             first_cluster=first_cluster)
     res = rvh.make_result(outs)
     # a dedicated stream: the library and the timing events share it
     stream = torch.cuda.Stream(dev)
@@ -500,8 +520,33 @@ def main():
         tt = torch.tensor([t_step], device=dev, dtype=torch.float64)
         torch.distributed.all_reduce(tt, op=torch.distributed.ReduceOp.MAX)
         t_max = float(tt.item())
-    value = nc * ws / t_max
+    value = (whole.n_clusters if args.strong else nc * ws) / t_max
     grid = stats.grid
+
+    # ---- strong scaling: the ranks' shards merged equal one GPU's estimate of the frame
+    strong = None
+    if args.strong:
+        from paper_2012_12618_gb300 import partition
+        mine = {k: v.cpu().numpy() for k, v in outs.items()}
+        mine["inlier_mask"] = mine["inlier_mask"][:npts]
+        parts = [(first_cluster, first_cluster + nc, mine)]
+        if ws > 1:
+            parts = [None] * ws
+            torch.distributed.all_gather_object(parts, (first_cluster, first_cluster + nc, mine))
+        if rank == 0:
+            w_outs = rvh.alloc_outputs(whole.n_clusters, whole.n_points, dev)
+            w_ins = [None if a is None else torch.from_numpy(a).to(dev)
+                     for a in (whole.azimuth, whole.doppler, whole.offsets, whole.elevation)]
+            ctx.check(rvh.rvh_estimate(ctx.handle, rvh.make_frame(*w_ins),
+                                       rvh.make_params(dim, w.num_hypotheses, w.tau, w.seed,
+                                                       refine_iterations=args.refine_iterations),
+                                       rvh.make_result(w_outs), sptr), "rvh_estimate(whole frame)")
+            torch.cuda.synchronize()
+            one = {k: v.cpu().numpy() for k, v in w_outs.items()}
+            one["inlier_mask"] = one["inlier_mask"][:whole.n_points]
+            merged = partition.merge([p[2] for p in parts], [(p[0], p[1]) for p in parts], whole.offsets)
+            strong = {"ranks": ws, "shard_clusters": [p[1] - p[0] for p in parts],
+                      "merged_equals_one_gpu": all(np.array_equal(merged[k], one[k], equal_nan=True) for k in one)}
 
     # ---- roofline of the fused kernel (FP32 pipe; k FMA = 2k flop per trial x point pair)
     kern_s = float(np.mean(kern_ms)) * 1e-3
@@ -653,7 +698,7 @@ def main():
     for _ in range(2):
         ctx.check(rvh.rvh_estimate(ctx.handle, h_frame, params, h_res, sptr), "rvh_estimate(host)")
     e2e_t = []
-    for _ in range(max(3, args.steps // 2)):
+    for _ in range(max(50, args.steps // 2)):
         flush.fill_(3)
         torch.cuda.synchronize()
         t0 = time.perf_counter()
@@ -662,7 +707,10 @@ def main():
     h2d = npts * 4 * dim + (nc + 1) * 4  # azimuth, Doppler (and elevation in 3D), offsets
     d2h = nc * (4 * 8 + 3 * 4) + npts
     e2e = {"value": nc / float(np.mean(e2e_t)), "unit": "clusters/s", "h2d_bytes_per_step": h2d,
-           "d2h_bytes_per_step": d2h, "ms_per_step": 1e3 * float(np.mean(e2e_t))}
+           "d2h_bytes_per_step": d2h, "ms_per_step": 1e3 * float(np.mean(e2e_t)),
+           "ms_per_step_median": 1e3 * float(np.median(e2e_t)), "steps": len(e2e_t),
+           "timing": "host clock around rvh_estimate with pinned host buffers: copies in, kernels, copies out "
+                     "and the stream synchronisation, after an L2 flush outside the region"}
 
     # ---- plain all-FP64 one-launch-per-cluster GPU version (same frame)
     gpu_base = None
@@ -702,13 +750,16 @@ def main():
         line = {
             "metric": "clusters/s", "value": value, "unit": "clusters/s", "n_gpus": ws, "steps": args.steps,
             "warmup": max(args.warmup, 3), "ms_per_step": t_max * 1e3, "higher_is_better": True,
-            "scaling": "weak", "vs_baseline": None, "dtype": "f32+f64", "data": "synthetic",
+            "scaling": "strong" if args.strong else "weak", "vs_baseline": None, "dtype": "f32+f64",
+            "data": "synthetic",
             "config": {"workload": f"{wname}: {nc} clusters, sizes {w.size_law} {w.size_lo}..{w.size_hi}, "
                                    f"{npts} points, {dim}D, H={w.num_hypotheses}, tau={w.tau} m/s, "
                                    f"outliers {w.outlier_frac:g}, noise {w.noise_sigma:g} m/s, seed={w.seed}, "
                                    f"refine_iterations={args.refine_iterations}",
                        "l2": "flushed between timed steps (256 MiB write outside the step events)",
-                       "per_rank": "one independent frame per rank"},
+                       "per_rank": ("a contiguous cost-balanced cluster range of one frame (first_cluster = "
+                                    "range start)" if args.strong else "one independent frame per rank")},
+            "strong_scaling_check": strong,
             "pair_evals_per_s": pairs * ws / t_max,
             "roofline": roofline,
             "workloads": workloads,

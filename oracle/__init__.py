@@ -41,7 +41,8 @@ class _Params(ctypes.Structure):
                 ("tau", ctypes.c_double), ("seed", ctypes.c_uint64),
                 ("cond_eps", ctypes.c_double), ("enumerate", ctypes.c_int32),
                 ("refine_iterations", ctypes.c_int32), ("confidence", ctypes.c_double),
-                ("trial_block", ctypes.c_int32), ("line_model", ctypes.c_int32)]
+                ("trial_block", ctypes.c_int32), ("line_model", ctypes.c_int32),
+                ("first_cluster", ctypes.c_int32)]
 
 
 _lib = None
@@ -94,13 +95,15 @@ def estimate(azimuth, doppler, offsets, *, elevation=None, num_hypotheses: int, 
              seed: int, cond_eps: float | None = None, enumerate_subsets: bool = False,
              subset=None, want_counts: bool = False, want_fragile: bool = False,
              refine_iterations: int = 0, confidence: float = 0.0, trial_block: int = 128,
-             want_trials: bool = False, line_model: bool = False, _lib=None) -> dict:
+             want_trials: bool = False, line_model: bool = False, first_cluster: int = 0, _lib=None) -> dict:
     """Run the oracle over all clusters (or the listed subset).  Inputs are
     widened to FP64 exactly.  refine_iterations > 0 adds that many local
     optimisation rounds (re-threshold against the least-squares velocity,
     re-fit) after the refine.  confidence in (0, 1) selects the adaptive trial
     count (stopping checks every trial_block trials).  line_model selects
-    Alg. 1 as printed (normalised line fits, MAD threshold; 2D; tau unused)."""
+    Alg. 1 as printed (normalised line fits, MAD threshold; 2D; tau unused).
+    first_cluster: the frame index of cluster 0 of these arrays (a shard of
+    a frame draws the whole frame's minimal sets)."""
     az = np.ascontiguousarray(azimuth, dtype=np.float64)
     dp = np.ascontiguousarray(doppler, dtype=np.float64)
     el = None if elevation is None else np.ascontiguousarray(elevation, dtype=np.float64)
@@ -112,7 +115,8 @@ def estimate(azimuth, doppler, offsets, *, elevation=None, num_hypotheses: int, 
     H = int(num_hypotheses)
     p = _Params(k, H, float(tau), int(seed) & 0xFFFFFFFFFFFFFFFF,
                 default_cond_eps(k) if cond_eps is None else float(cond_eps), int(enumerate_subsets),
-                int(refine_iterations), float(confidence), int(trial_block), int(bool(line_model)))
+                int(refine_iterations), float(confidence), int(trial_block), int(bool(line_model)),
+                int(first_cluster))
     out = {
         "vx": np.full(n_out, np.nan), "vy": np.full(n_out, np.nan), "vz": np.full(n_out, np.nan),
         "heading": np.full(n_out, np.nan),

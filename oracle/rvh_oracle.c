@@ -216,6 +216,7 @@ int oracle_estimate(const double* azimuth, const double* elevation, const double
   if (!(p->confidence >= 0.0 && p->confidence < 1.0)) return -1;
   if (p->confidence > 0.0 && p->trial_block < 1) return -1;
   if (p->line_model && (k != 2 || p->refine_iterations != 0)) return -1;
+  if (p->first_cluster < 0 || (int64_t)p->first_cluster + n_clusters > 0x7fffffffLL) return -1;
   const int32_t H = p->num_hypotheses;
   const double tau = p->tau;
   const int32_t n_out = subset ? n_subset : n_clusters;
@@ -308,7 +309,7 @@ int oracle_estimate(const double* azimuth, const double* elevation, const double
       do {
         int32_t qs[3] = {0, 0, 0};
         int drawn = p->enumerate ? enumerate_subset(h, n, k, qs)
-                                 : oracle_draw(p->seed, ci, h, n, k, qs);
+                                 : oracle_draw(p->seed, p->first_cluster + ci, h, n, k, qs);
         if (drawn != 0) break;
         if (p->line_model) {
           /* Alg. 1: slope and intercept through the two normalised seeds */

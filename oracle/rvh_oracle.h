@@ -83,6 +83,9 @@ typedef struct {
   int32_t trial_block;    /* adaptive: trials between stopping checks (B >= 1) */
   int32_t line_model;     /* 1: Alg. 1 as printed (2D only): normalised line fits,
                              perpendicular distance, MAD threshold; tau unused */
+  int32_t first_cluster;  /* the frame index of cluster 0 of these arrays: a shard
+                             of a frame draws its minimal sets with counter
+                             (h, first_cluster + cluster, 0, 0), as the whole frame */
 } orc_params;
 
 /* Philox4x32 with 10 rounds: out = Philox(ctr; key). */

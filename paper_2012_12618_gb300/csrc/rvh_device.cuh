@@ -169,7 +169,8 @@ constexpr float kDetErr3 = 3.65e-6f;
 // vertical direction, so most 3D trials do.
 constexpr float kRefineBand = 1e-4f;
 
-// FP32 row of a point plus its Doppler: (c, s, w, 0) or (a0, a1, a2, w).
+// FP32 row of a point plus its Doppler: (c, s, w, t) or (a0, a1, a2, w); the
+// 2D row keeps the FP32 azimuth t, from which the FP64 row is computed.
 template <int DIM>
 __device__ __forceinline__ float4 row_f32(float az, float el, float w) {
   float s, c;
@@ -181,7 +182,7 @@ __device__ __forceinline__ float4 row_f32(float az, float el, float w) {
     s = __double2float_rn(sd);
     c = __double2float_rn(cd);
   }
-  if (DIM == 2) return make_float4(c, s, w, 0.0f);
+  if (DIM == 2) return make_float4(c, s, w, az);
   float se, ce;
   if (fabsf(el) <= 3.1415925f) {
     sincosf(el, &se, &ce);

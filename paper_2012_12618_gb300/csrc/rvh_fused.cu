@@ -185,6 +185,15 @@ struct Rows64 {
     row_f64<2>(a->trig, a->az[o + j], 0.0f, t);
     return make_double4_32a(t[0], t[1], 0.0, (double)a->dop[o + j]);
   }
+  // The same row when the point's FP32 cosine-model row is at hand: in 2D it
+  // carries the Doppler and the azimuth (row_f32), so nothing is read from
+  // global memory.
+  __device__ __forceinline__ double4_32a at(int j, float4 row) const {
+    if (DIM == 3) return pre[j];
+    double t[3];
+    row_f64<2>(a->trig, row.w, 0.0f, t);
+    return make_double4_32a(t[0], t[1], 0.0, (double)row.z);
+  }
 };
 
 // FP64 rows computed from the frame's inputs in both models: the source of
@@ -436,7 +445,7 @@ __device__ __noinline__ void line_rows_and_threshold(const FrameDesc& a, const R
     const double y = ((double)a.dop[o + j] - vmin) * rv;
     pre[j] = make_double4_32a(x, y, 0.0, 0.0);
     const float y32 = __double2float_rn(y);
-    rows.put(j, make_float4(__double2float_rn(x), 1.0f, y32, 0.0f));
+    rows.put(j, make_float4(__double2float_rn(x), 1.0f, y32, a.az[o + j]));
   }
   __syncthreads();
   // Eq. eq:MAD read as the median absolute deviation of the normalised Doppler
@@ -484,9 +493,10 @@ __device__ int exact_count_block(const FrameDesc& a, const RV rows, const Rows64
   unsigned long long lbin = 0;
   auto cosine_band = [&]() {
     for (int j = tid; j < N; j += kThreads) {
-      const float r = fabsf(resid_f32<DIM>(rows.at(j), hy.x, hy.y, hy.z));
+      const float4 row = rows.at(j);
+      const float r = fabsf(resid_f32<DIM>(row, hy.x, hy.y, hy.z));
       if (!(r <= tlo) && !(r > hy.w)) {
-        const double4_32a s = R.at(j);
+        const double4_32a s = R.at(j, row);
         const double a64[3] = {s.x, s.y, s.z};
         if (fabs(residual_f64<DIM>(a64, s.w, v)) <= a.tau) ++lbin;
       }
@@ -641,11 +651,12 @@ __device__ __forceinline__ int mask_and_sums(const FrameDesc& a, const RV rows, 
   int nin = 0, nch = 0;
   auto cosine_pass = [&]() {
     for (int j = tid; j < N; j += kThreads) {
-      const float r = fabsf(resid_f32<DIM>(rows.at(j), hy.x, hy.y, hy.z));
+      const float4 row = rows.at(j);
+      const float r = fabsf(resid_f32<DIM>(row, hy.x, hy.y, hy.z));
       bool in = r <= tlo;
       const bool band = !in && !(r > hy.w);
       if (in || band) {
-        const double4_32a s = R.at(j);
+        const double4_32a s = R.at(j, row);
         if (band) {
           const double a64[3] = {s.x, s.y, s.z};
           in = fabs(residual_f64<DIM>(a64, s.w, v64)) <= a.tau;
@@ -873,7 +884,7 @@ __device__ void process_cluster(const FrameDesc& a, const Smem& S, ClusterShared
         const int q2 = DIM == 3 ? q[2] : q[0];
         const float4 p0 = rows.at(q[0]), p1 = rows.at(q[1]), p2 = rows.at(q2);
         const int qs[3] = {q[0], q[1], q2};
-        auto seed64 = [&](int i) { return R.at(qs[i]); };
+        auto seed64 = [&](int i) { return R.at(qs[i], i == 0 ? p0 : (i == 1 ? p1 : p2)); };
         const float rb = DIM == 3 ? refine_band : __int_as_float(0x7f800000);
         Hyp32 hy = hyp_f32<DIM>(p0, p1, p2, seed64, rb, wmax, a.acc, a.rej, a.tau32);
         if (hy.kind == kHypUndecided) {
@@ -910,10 +921,10 @@ __device__ void process_cluster(const FrameDesc& a, const Smem& S, ClusterShared
           int q[3];
           draw_minimal_set<DIM>(a.key, a.cluster_base + ci, hc0 + hl, N, q);
           const int qs[3] = {q[0], q[1], q[0]};
-          auto seed64 = [&](int k) { return R.at(qs[k]); };
+          const float4 p0 = rows.at(q[0]), p1 = rows.at(q[1]);
+          auto seed64 = [&](int k) { return R.at(qs[k], k == 1 ? p1 : p0); };
           // the trial was accepted in the first pass: no conditioning test
-          Hyp32 hy = hyp_f32<DIM>(rows.at(q[0]), rows.at(q[1]), rows.at(q[0]), seed64, refine_band, wmax, 0.0f,
-                                  0.0f, a.tau32);
+          Hyp32 hy = hyp_f32<DIM>(p0, p1, p0, seed64, refine_band, wmax, 0.0f, 0.0f, a.tau32);
           if (hy.kind != kHypNormal) {
             hy.kind = kHypExactOnly;
             hy.thi = __int_as_float(0x7f800000);

@@ -30,7 +30,7 @@ struct Smem {
 
 // ---- FP32 rows of the cluster being processed ---------------------------------------
 // Shared memory holds them as tiles of 32 points, component-major inside a
-// tile (32 c | 32 s | 32 w | 32 unused in 2D; 32 a0 | 32 a1 | 32 a2 | 32 w in
+// tile (32 c | 32 s | 32 w | 32 t in 2D; 32 a0 | 32 a1 | 32 a2 | 32 w in
 // 3D): a warp reading consecutive points touches 32 banks per component, and
 // four consecutive points of one component are one aligned float4, which the
 // scoring pass consumes as two packed pairs.  Clusters larger than the shared

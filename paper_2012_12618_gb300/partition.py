@@ -9,6 +9,8 @@ single-device result exactly.  Results are concatenated on the host.
 """
 from __future__ import annotations
 
+import dataclasses
+
 import numpy as np
 
 # per-cluster cost in point-evaluations of fixed work (load, hypothesis
@@ -51,3 +53,36 @@ def merge(parts: list[dict], ranges: list[tuple[int, int]], offsets) -> dict:
         out[key] = np.concatenate([p[key] for p in parts])
     assert out["inlier_mask"].shape[0] == int(off[ranges[-1][1]] - off[ranges[0][0]])
     return out
+
+
+@dataclasses.dataclass
+class Shard:
+    """One rank's part of a frame: clusters [c0, c1) (points [p0, p1)) with
+    their offsets rebased to 0; estimate it with first_cluster = c0."""
+    azimuth: np.ndarray
+    doppler: np.ndarray
+    offsets: np.ndarray
+    elevation: np.ndarray | None
+    c0: int
+    c1: int
+    p0: int
+    p1: int
+
+    @property
+    def n_clusters(self) -> int:
+        return self.c1 - self.c0
+
+    @property
+    def n_points(self) -> int:
+        return self.p1 - self.p0
+
+
+def rank_shard(azimuth, doppler, offsets, num_hypotheses: int, rank: int, world: int, elevation=None) -> Shard:
+    """The shard of `rank` out of `world` ranks: its range of
+    balanced_ranges and the points of that range."""
+    if not 0 <= rank < world:
+        raise ValueError("rank out of range")
+    c0, c1 = balanced_ranges(offsets, num_hypotheses, world)[rank]
+    az, dop, off, el, (p0, p1) = shard(azimuth, doppler, offsets, c0, c1, elevation)
+    return Shard(az, dop, off, el, c0, c1, p0, p1)
+

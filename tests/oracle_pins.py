@@ -40,6 +40,10 @@ violation.  What pins what:
               of cond_eps, is flagged; the same planted 1e-9 m/s (or a
               relative 1e-6) away is not; no cluster of the full frame64 and
               dense2d frames is flagged
+  first_cluster  a shard of a frame (clusters [c0, c1), offsets rebased)
+              estimated with first_cluster = c0 gives the whole frame's
+              results for those clusters, and differs from the same
+              arrays estimated as a frame of their own
   local_opt   the re-threshold + re-fit rounds: one round's inlier set is
               numpy's re-threshold of the refined velocity, every result is
               numpy.linalg.lstsq of its own inlier set, a converged result is
@@ -610,6 +614,23 @@ def check_fragile(L):
         assert not o["fragile"].any(), (name, np.flatnonzero(o["fragile"]))
 
 
+def check_first_cluster(L):
+    w = synth.WORKLOADS["frame64"]
+    f = synth.make_frame(w, n_clusters=24, gen_seed=29)
+    c0, c1 = 9, 17
+    p0, p1 = int(f.offsets[c0]), int(f.offsets[c1])
+    off = (f.offsets[c0:c1 + 1] - p0).astype(np.int32)
+    part = _est(L, f.azimuth[p0:p1], f.doppler[p0:p1], off, num_hypotheses=64, tau=w.tau, seed=5, first_cluster=c0)
+    whole = _est(L, f.azimuth, f.doppler, f.offsets, num_hypotheses=64, tau=w.tau, seed=5,
+                 subset=np.arange(c0, c1, dtype=np.int32))
+    for k in ("best_hypothesis", "inlier_count", "status", "vx", "vy"):
+        assert np.array_equal(part[k], whole[k], equal_nan=True), k
+    assert np.array_equal(part["inlier_mask"], whole["inlier_mask"][p0:p1])
+    # and not the draws of a frame whose clusters start at 0
+    plain = _est(L, f.azimuth[p0:p1], f.doppler[p0:p1], off, num_hypotheses=64, tau=w.tau, seed=5)
+    assert not np.array_equal(plain["best_hypothesis"], part["best_hypothesis"])
+
+
 ALL_CHECKS = [check_philox, check_draws, check_recovery, check_brute, check_symmetry,
               check_rotation, check_lstsq, check_status, check_planted, check_local_opt, check_adaptive,
-              check_paper_line, check_dbscan, check_fragile]
+              check_paper_line, check_dbscan, check_fragile, check_first_cluster]

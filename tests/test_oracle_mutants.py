@@ -15,6 +15,8 @@ import oracle
 from tests import oracle_pins
 
 MUTANTS = {
+    "first_cluster_ignored": ("oracle_draw(p->seed, p->first_cluster + ci, h, n, k, qs)",
+                              "oracle_draw(p->seed, ci, h, n, k, qs)"),
     "fragile_margin_dropped": ("double amp = 1e-14 * (1.0 + 1.0 / fabs(hyp_det[h]));", "double amp = 0.0;"),
     "fragile_margin_too_wide": ("double amp = 1e-14 * (1.0 + 1.0 / fabs(hyp_det[h]));",
                                 "double amp = 1e-8 * (1.0 + 1.0 / fabs(hyp_det[h]));"),
