@@ -508,6 +508,28 @@ def check_paper_line(L):
     # one azimuth for every point: every seed pair shares x
     deg = _est(L, np.full(6, 0.3), np.arange(6.0), [0, 6], num_hypotheses=8, tau=0.1, seed=1, line_model=True)
     assert deg["status"][0] == oracle.ALL_DEGENERATE
+    # NaN Dopplers (the reading of Alg. 1's normalize() and median for them):
+    # the extremes are taken over the numbers, the medians sort NaN after
+    # every number, and a NaN point is never an inlier
+    rng2 = np.random.default_rng(37)
+    for trial in range(6):
+        n = int(rng2.integers(9, 15))
+        th = np.sort(rng2.uniform(-1.0, 1.0, n))
+        dop = 5.0 * np.cos(th) + rng2.normal(0, 0.2, n)
+        nan_at = rng2.choice(n, size=int(rng2.integers(1, 3)), replace=False)
+        dop[nan_at] = np.nan
+
+        def med_nan_last(a):
+            s_ = np.sort(a)  # numpy sorts NaN after every number
+            k = s_.shape[0]
+            return s_[k // 2] if k % 2 else 0.5 * (s_[k // 2 - 1] + s_[k // 2])
+
+        lo, hi = np.nanmin(dop), np.nanmax(dop)
+        y = (dop - lo) * (1.0 / (hi - lo))
+        T = med_nan_last(np.abs(y - med_nan_last(np.abs(y))))
+        o = _est(L, th, dop, [0, n], num_hypotheses=64, tau=0.1, seed=trial, line_model=True)
+        assert np.isfinite(T) and o["threshold"][0] == T, (o["threshold"][0], T)
+        assert not o["inlier_mask"][nan_at].any()
 
 
 def _canonical(labels):

@@ -187,3 +187,33 @@ def test_pipeline_cluster_gather_estimate(torch, ctx):
         u = np.array([np.cos(t), np.sin(t)])
         err.append(abs(np.dot([g["vx"][c], g["vy"][c]], u) - np.dot(s.truth_v[oid], u)))
     assert np.median(err) < 0.05, np.median(err)
+
+
+def test_nearest_neighbour_clustering_is_min_pts_one(torch, ctx):
+    """Threshold nearest-neighbour clustering (single linkage cut at eps, one
+    of the clustering choices Fig. 1 names) is DBSCAN with min_pts = 1: every
+    point is a core point and the clusters are the connected components of
+    the eps-graph.  rvh_cluster with min_pts = 1 equals scipy's connected
+    components on a 16,895-point scene, cluster for cluster."""
+    sparse = pytest.importorskip("scipy.sparse")
+    csgraph = pytest.importorskip("scipy.sparse.csgraph")
+    spatial = pytest.importorskip("scipy.spatial")
+    s = synth.make_scene(synth.SCENES["scene"], n_objects=96, gen_seed=24)
+    f = s.features()
+    rc, nc, lab, perm, off = _cluster(torch, ctx, f, 0.8, 1)
+    assert rc == rvh.RVH_OK and (lab >= 0).all()
+    f64 = f.astype(np.float64)
+    pairs = spatial.cKDTree(f64).query_pairs(0.8 + 1e-6, output_type="ndarray")
+    d2 = ((f64[pairs[:, 0]] - f64[pairs[:, 1]]) ** 2).sum(1)
+    pairs = pairs[d2 <= 0.8 * 0.8]  # the same test as the library: squared FP64 distance <= eps^2
+    n = f.shape[0]
+    g = sparse.coo_matrix((np.ones(len(pairs)), (pairs[:, 0], pairs[:, 1])), shape=(n, n))
+    ncc, cc = csgraph.connected_components(g, directed=False)
+    assert nc == ncc
+    # the same partition; clusters numbered by their smallest point index
+    first = np.full(ncc, n)
+    np.minimum.at(first, cc, np.arange(n))
+    rank = np.empty(ncc, np.int64)
+    rank[np.argsort(first)] = np.arange(ncc)
+    assert np.array_equal(lab, rank[cc])
+

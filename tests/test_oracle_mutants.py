@@ -15,6 +15,8 @@ import oracle
 from tests import oracle_pins
 
 MUTANTS = {
+    "line_median_nan_first": ("return isnan(x) - isnan(y);", "return isnan(y) - isnan(x);"),
+    "line_extreme_keeps_nan": ("vmin = fmin(vmin, w[q]);", "vmin = vmin < w[q] ? vmin : w[q];"),
     "first_cluster_ignored": ("oracle_draw(p->seed, p->first_cluster + ci, h, n, k, qs)",
                               "oracle_draw(p->seed, ci, h, n, k, qs)"),
     "fragile_margin_dropped": ("double amp = 1e-14 * (1.0 + 1.0 / fabs(hyp_det[h]));", "double amp = 0.0;"),
