@@ -884,7 +884,7 @@ __device__ void process_cluster(const FrameDesc& a, const Smem& S, ClusterShared
         const int q2 = DIM == 3 ? q[2] : q[0];
         const float4 p0 = rows.at(q[0]), p1 = rows.at(q[1]), p2 = rows.at(q2);
         const int qs[3] = {q[0], q[1], q2};
-        auto seed64 = [&](int i) { return R.at(qs[i], i == 0 ? p0 : (i == 1 ? p1 : p2)); };
+        auto seed64 = [&](int i) { return R.at(qs[i]); };
         const float rb = DIM == 3 ? refine_band : __int_as_float(0x7f800000);
         Hyp32 hy = hyp_f32<DIM>(p0, p1, p2, seed64, rb, wmax, a.acc, a.rej, a.tau32);
         if (hy.kind == kHypUndecided) {
@@ -921,10 +921,12 @@ __device__ void process_cluster(const FrameDesc& a, const Smem& S, ClusterShared
           int q[3];
           draw_minimal_set<DIM>(a.key, a.cluster_base + ci, hc0 + hl, N, q);
           const int qs[3] = {q[0], q[1], q[0]};
-          const float4 p0 = rows.at(q[0]), p1 = rows.at(q[1]);
-          auto seed64 = [&](int k) { return R.at(qs[k], k == 1 ? p1 : p0); };
+          // seed rows from the frame's arrays: keeping the loaded FP32 rows
+          // alive across the solve instead measured slower on trials that refine
+          auto seed64 = [&](int k) { return R.at(qs[k]); };
           // the trial was accepted in the first pass: no conditioning test
-          Hyp32 hy = hyp_f32<DIM>(p0, p1, p0, seed64, refine_band, wmax, 0.0f, 0.0f, a.tau32);
+          Hyp32 hy = hyp_f32<DIM>(rows.at(q[0]), rows.at(q[1]), rows.at(q[0]), seed64, refine_band, wmax, 0.0f,
+                                  0.0f, a.tau32);
           if (hy.kind != kHypNormal) {
             hy.kind = kHypExactOnly;
             hy.thi = __int_as_float(0x7f800000);
