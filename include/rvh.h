@@ -185,16 +185,23 @@ void rvh_destroy(rvh_ctx* ctx);
 
 /* Estimates one frame with the fused FP32/FP64-band persistent kernel.
  * stream: a cudaStream_t, or NULL for the context's stream.
- * When every input and output pointer is device memory the call is
- * stream-ordered: it returns once the work is enqueued, and the results are
- * valid after the stream reaches this point.  When any pointer is host
- * memory, inputs are copied in and outputs copied back inside the call,
- * which returns after the stream has completed.  A context's scratch is
- * reused across calls; calls on one context are serialised on the device
- * (a later call waits for the previous one).  In the all-device case on a
- * stream that is not being captured, the fused kernel launch is captured
- * once into a CUDA graph and replayed while the arguments stay the same
- * (environment RVH_GRAPHS=0 turns this off). */
+ * Each input and output may be device memory, page-locked host memory
+ * (cudaHostAlloc / cudaHostRegister, mapped for the device) or pageable
+ * host memory.  Device buffers are used where they are.  Host inputs are
+ * copied into the context's scratch, one bulk copy per array, inside the
+ * call.  Page-locked outputs are written in place by the kernels over the
+ * CPU-GPU link; pageable outputs are staged in the context's scratch and
+ * copied back inside the call.  When every output is device memory the call is stream-ordered: it
+ * returns once the work is enqueued, and the results are valid after the
+ * stream reaches this point.  When any output is host memory the call
+ * returns after the stream has completed, with the results in place.  Host
+ * inputs must stay unchanged until the call returns.  A context's scratch is
+ * reused across calls; calls on one context are serialised on the device (a
+ * later call waits for the previous one).  On a stream that is not being
+ * captured, the fused kernel runs as an instantiated CUDA graph, one per
+ * kernel instantiation, which every later call replays with its own
+ * arguments (frame addresses and sizes may change from call to call;
+ * environment RVH_GRAPHS=0 launches plainly instead). */
 int rvh_estimate(rvh_ctx* ctx, const rvh_frame* frame, const rvh_params* params,
                  rvh_result* result, void* stream);
 

@@ -68,6 +68,31 @@ bool is_device_ptr(const void* p) {
   return at.type == cudaMemoryTypeDevice || at.type == cudaMemoryTypeManaged;
 }
 
+// Where a buffer lives, for the kernels: device memory (used as is), page-
+// locked host memory the GPU maps (outputs there are written in place
+// through its device address, over the CPU-GPU link), or pageable host
+// memory (staged through the context's scratch).
+enum class Mem { kNone, kDevice, kPinned, kPageable };
+
+Mem mem_kind(const void* p, void** dev) {
+  *dev = nullptr;
+  if (!p) return Mem::kNone;
+  cudaPointerAttributes at{};
+  if (cudaPointerGetAttributes(&at, p) != cudaSuccess) {
+    cudaGetLastError();
+    return Mem::kPageable;
+  }
+  if (at.type == cudaMemoryTypeDevice || at.type == cudaMemoryTypeManaged) {
+    *dev = const_cast<void*>(p);
+    return Mem::kDevice;
+  }
+  if (at.type == cudaMemoryTypeHost && at.devicePointer) {
+    *dev = at.devicePointer;
+    return Mem::kPinned;
+  }
+  return Mem::kPageable;
+}
+
 // Host-side argument checks shared by every entry point.
 int check_args_impl(const rvh_frame* f, const rvh_params* p, const rvh_result* r) {
   if (!f || !p || !r) return fail(RVH_EINVAL, "frame, params and result must be non-NULL");
@@ -556,7 +581,8 @@ struct Staged {
   const float *az, *el, *dop;
   const int32_t* off;
   rvh_result dev_out;       // device pointers the kernel writes
-  bool host_out[rvh::kOutputs];
+  bool host_out[rvh::kOutputs];  // staged through scratch (pageable host memory)
+  bool sync_out;                 // some output is host memory: the call returns once it is written
   char* base;
   int2* worklist;
   int* counter;
@@ -571,16 +597,34 @@ static int stage(rvh_ctx* ctx, const rvh_frame* f, const rvh_params* p, rvh_resu
   const int64_t np = f->n_points;
   const int32_t nc = f->n_clusters;
   const bool dim3 = p->model_dim == 3;
-  const bool d_az = is_device_ptr(f->azimuth), d_dop = is_device_ptr(f->doppler);
-  const bool d_el = !dim3 || is_device_ptr(f->elevation);
-  const bool d_off = is_device_ptr(f->cluster_offsets);
-  if (!d_off) {
+  // inputs in device memory are read where they are; host inputs (pinned or
+  // not) are copied in with one bulk copy each: reading them across the
+  // CPU-GPU link from the kernels puts the link's latency on every
+  // cluster's load and measured slower than the copy
+  void* v_az = nullptr;
+  void* v_dop = nullptr;
+  void* v_el = nullptr;
+  void* v_off = nullptr;
+  const Mem k_az = mem_kind(f->azimuth, &v_az), k_dop = mem_kind(f->doppler, &v_dop);
+  const Mem k_el = dim3 ? mem_kind(f->elevation, &v_el) : Mem::kNone;
+  const Mem k_off = mem_kind(f->cluster_offsets, &v_off);
+  const bool d_az = k_az == Mem::kDevice;
+  const bool d_dop = k_dop == Mem::kDevice;
+  const bool d_el = !dim3 || k_el == Mem::kDevice;
+  const bool d_off = k_off == Mem::kDevice;
+  if (k_off != Mem::kDevice) {  // host offsets are checked here
     int rc = check_host_offsets(f->cluster_offsets, nc, np);
     if (rc) return rc;
   }
   void* outs[rvh::kOutputs];
+  void* v_out[rvh::kOutputs];
   rvh::result_ptrs(*r, outs);
-  for (int i = 0; i < rvh::kOutputs; ++i) st.host_out[i] = outs[i] && !is_device_ptr(outs[i]);
+  st.sync_out = false;
+  for (int i = 0; i < rvh::kOutputs; ++i) {
+    const Mem k = mem_kind(outs[i], &v_out[i]);
+    st.host_out[i] = k == Mem::kPageable;                     // staged, copied back
+    st.sync_out = st.sync_out || k == Mem::kPinned || k == Mem::kPageable;  // host results complete on return
+  }
   // layout
   size_t off = 0;
   auto take = [&](size_t bytes) {
@@ -627,10 +671,10 @@ static int stage(rvh_ctx* ctx, const rvh_frame* f, const rvh_params* p, rvh_resu
   st.rows = b + o_rows;
   st.rows64 = fused ? (double4_32a*)(b + o_rows64) : nullptr;
   st.cta_rows64 = fused ? (double4_32a*)(b + o_cta64) : nullptr;
-  st.az = d_az ? f->azimuth : (const float*)(b + o_az);
-  st.el = dim3 ? (d_el ? f->elevation : (const float*)(b + o_el)) : nullptr;
-  st.dop = d_dop ? f->doppler : (const float*)(b + o_dop);
-  st.off = d_off ? f->cluster_offsets : (const int32_t*)(b + o_off);
+  st.az = d_az ? (const float*)v_az : (const float*)(b + o_az);
+  st.el = dim3 ? (d_el ? (const float*)v_el : (const float*)(b + o_el)) : nullptr;
+  st.dop = d_dop ? (const float*)v_dop : (const float*)(b + o_dop);
+  st.off = d_off ? (const int32_t*)v_off : (const int32_t*)(b + o_off);
   if (np > 0) {
     if (!d_az) RVH_CUDA(cudaMemcpyAsync((void*)st.az, f->azimuth, 4 * np, cudaMemcpyHostToDevice, s));
     if (dim3 && !d_el) RVH_CUDA(cudaMemcpyAsync((void*)st.el, f->elevation, 4 * np, cudaMemcpyHostToDevice, s));
@@ -638,7 +682,7 @@ static int stage(rvh_ctx* ctx, const rvh_frame* f, const rvh_params* p, rvh_resu
   }
   if (!d_off) RVH_CUDA(cudaMemcpyAsync((void*)st.off, f->cluster_offsets, 4 * (size_t)(nc + 1), cudaMemcpyHostToDevice, s));
   void* dev[rvh::kOutputs];
-  for (int i = 0; i < rvh::kOutputs; ++i) dev[i] = st.host_out[i] ? (void*)(b + o_out[i]) : outs[i];
+  for (int i = 0; i < rvh::kOutputs; ++i) dev[i] = st.host_out[i] ? (void*)(b + o_out[i]) : v_out[i];
   st.dev_out = rvh::result_from(dev);
   RVH_CUDA(rvh::launch_threshold_fill(st.dev_out.threshold, nc, p->hypothesis_model == RVH_MODEL_PAPER_LINE,
                                       p->inlier_threshold, s));
@@ -650,14 +694,12 @@ static int unstage(const rvh_frame* f, rvh_result* r, const Staged& st, cudaStre
   void* dev[rvh::kOutputs];
   rvh::result_ptrs(*r, outs);
   rvh::result_ptrs(st.dev_out, dev);
-  bool any = false;
   for (int i = 0; i < rvh::kOutputs; ++i) {
     if (!st.host_out[i]) continue;
     const size_t n = (i == rvh::kMaskOutput) ? (size_t)f->n_points : (size_t)f->n_clusters;
     if (n) RVH_CUDA(cudaMemcpyAsync(outs[i], dev[i], rvh::kOutputSize[i] * n, cudaMemcpyDeviceToHost, s));
-    any = true;
   }
-  if (any) RVH_CUDA(cudaStreamSynchronize(s));
+  if (st.sync_out) RVH_CUDA(cudaStreamSynchronize(s));
   return RVH_OK;
 }
 

@@ -217,12 +217,14 @@ def test_narrow_azimuth_far_objects(ctx):
 
 @pytest.mark.parametrize("name,nc,kw", [("dense2d", 400, {}), ("dense3d", 160, {}),
                                         ("stress2d", 300, {"hypothesis_model": 1}),
-                                        ("dense2d", 256, {"first_cluster": 77, "refine_iterations": 1})])
+                                        ("dense2d", 256, {"first_cluster": 77, "refine_iterations": 1}),
+                                        ("dense2d", 700, {"confidence": 0.99, "trial_block": 64})])
 def test_host_frames_equal_device_frames(ctx, name, nc, kw):
-    """A frame and its results in host memory (staged through the context's
-    scratch) give every output, the threshold array included, exactly as
-    the same frame in device memory; with extensions and a first_cluster
-    offset too."""
+    """A frame and its results in host memory give every output, the
+    threshold array included, exactly as the same frame in device memory:
+    page-locked buffers (read and written in place by the kernels) and
+    pageable ones (staged through the context's scratch), mixed with device
+    buffers too; with extensions and a first_cluster offset."""
     import torch
     from paper_2012_12618_gb300 import rvh
     w = synth.WORKLOADS[name]
@@ -230,16 +232,25 @@ def test_host_frames_equal_device_frames(ctx, name, nc, kw):
     dim = 3 if f.elevation is not None else 2
     params = rvh.make_params(dim, 256, w.tau, 9, **kw)
     dev = torch.device("cuda", 0)
+
+    def place(t, where):
+        return t.to(dev) if where == "device" else (t.pin_memory() if where == "pinned" else t)
+
     results = []
-    for where in (dev, "cpu"):
+    for w_in, w_out in (("device", "device"), ("pinned", "pinned"), ("pageable", "pageable"),
+                        ("pinned", "device"), ("device", "pinned"), ("pinned", "pageable")):
         # the frame holds raw pointers: keep its tensors alive until the call is done
-        ins = [None if a is None else torch.from_numpy(a).to(where)
+        ins = [None if a is None else place(torch.from_numpy(a.copy()), w_in)
                for a in (f.azimuth, f.doppler, f.offsets, f.elevation)]
         frame = rvh.make_frame(*ins)
-        outs = rvh.alloc_outputs(f.n_clusters, f.n_points, where, threshold=True)
+        outs = {k: place(v, w_out) for k, v in rvh.alloc_outputs(f.n_clusters, f.n_points, "cpu",
+                                                                 threshold=True).items()}
+        for v in outs.values():
+            v.fill_(7)
         ctx.check(rvh.rvh_estimate(ctx.handle, frame, params, rvh.make_result(outs), None), "estimate")
         torch.cuda.synchronize()
         results.append({k: v.cpu().numpy() for k, v in outs.items()})
-    for k in results[0]:
-        assert np.array_equal(results[0][k][:f.n_points if k == "inlier_mask" else None],
-                              results[1][k][:f.n_points if k == "inlier_mask" else None], equal_nan=True), k
+    for r in results[1:]:
+        for k in results[0]:
+            assert np.array_equal(results[0][k][:f.n_points if k == "inlier_mask" else None],
+                                  r[k][:f.n_points if k == "inlier_mask" else None], equal_nan=True), k
