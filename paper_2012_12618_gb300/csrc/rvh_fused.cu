@@ -148,7 +148,7 @@ __device__ __forceinline__ void phase_a(const float4* __restrict__ rows, int N, 
 // trials (pairs of registers per coordinate) do not fit in the 64 registers a
 // thread has at four CTAs per SM.
 template <int DIM>
-__device__ void phase_a_dispatch(int pw, int hpl, const TileRows rows, int N, const Smem& S, int nh) {
+__device__ void phase_a_dispatch(int pw, int hpl, const TileRowsOf<DIM> rows, int N, const Smem& S, int nh) {
   (void)hpl;
   if (pw == 1) {
     phase_a_tiles<DIM, 1, 4>(rows, N, S, nh);
@@ -186,12 +186,11 @@ struct Rows64 {
     return make_double4_32a(t[0], t[1], 0.0, (double)a->dop[o + j]);
   }
   // The same row when the point's FP32 cosine-model row is at hand: in 2D it
-  // carries the Doppler and the azimuth (row_f32), so nothing is read from
-  // global memory.
+  // carries the Doppler (row_f32), so only the azimuth is read.
   __device__ __forceinline__ double4_32a at(int j, float4 row) const {
     if (DIM == 3) return pre[j];
     double t[3];
-    row_f64<2>(a->trig, row.w, 0.0f, t);
+    row_f64<2>(a->trig, a->az[o + j], 0.0f, t);
     return make_double4_32a(t[0], t[1], 0.0, (double)row.z);
   }
 };
@@ -779,6 +778,96 @@ __device__ __noinline__ int local_opt_rounds(const FrameDesc& a, const RV rows, 
   return n_in;
 }
 
+// a2 + a3 for trials hc0 .. hc0 + nh - 1 of cluster ci under the cosine
+// model: draw, FP32 solve (refined when ill-conditioned), bound, records
+// into S.  Trials with a wide band refine their velocity.  3D minimal sets
+// are often ill-conditioned and refine on the spot above kRefineBand.  2D
+// ones have |det| = |sin(t1 - t0)| and mostly narrow bands, whose few band
+// points cost less than refining; those above tau / 32 are queued, and when
+// they are at least an eighth of the chunk (a cluster of narrow azimuth
+// extent, such as a far object, where nearly every seed pair is
+// ill-conditioned) a second pass refines them, one per lane.  Elsewhere the
+// pass's latency would cost more than the band points it saves; either way
+// the decisions are exact.
+template <int DIM, typename RV>
+__device__ __forceinline__ void cosine_trial_chunk(const FrameDesc& a, const RV rows, const Rows64<DIM>& R,
+                                                     const Smem& S, ClusterShared& cs, int ci, int N, int hc0,
+                                                     int nh, float wmax, unsigned long long* fp64_count,
+                                                     unsigned long long* refined_count) {
+  const int tid = threadIdx.x;
+  const float refine_band = DIM == 3 ? kRefineBand : a.tau32.hi * 0x1p-5f;
+  unsigned long long n_fp64 = 0, n_ref = 0;
+  for (int hl = tid; hl < nh; hl += kThreads) {
+    int q[3];
+    draw_minimal_set<DIM>(a.key, a.cluster_base + ci, hc0 + hl, N, q);
+    const int q2 = DIM == 3 ? q[2] : q[0];
+    const float4 p0 = rows.at(q[0]), p1 = rows.at(q[1]), p2 = rows.at(q2);
+    const int qs[3] = {q[0], q[1], q2};
+    auto seed64 = [&](int i) { return R.at(qs[i]); };
+    const float rb = DIM == 3 ? refine_band : __int_as_float(0x7f800000);
+    Hyp32 hy = hyp_f32<DIM>(p0, p1, p2, seed64, rb, wmax, a.acc, a.rej, a.tau32);
+    if (hy.kind == kHypUndecided) {
+      ++n_fp64;
+      double v[3];
+      if (hyp_f64<DIM>(a, R, ci, hc0 + hl, N, v)) {
+        hy = hyp_f32<DIM>(p0, p1, p2, seed64, rb, wmax, 0.0f, 0.0f, a.tau32);
+        if (hy.kind != kHypNormal) {
+          hy.kind = kHypExactOnly;
+          hy.thi = __int_as_float(0x7f800000);
+          hy.tlo = -1.0f;
+        }
+      } else {
+        hy.kind = kHypRejected;
+      }
+    }
+    if (hy.kind == kHypExactOnly) ++n_fp64;
+    n_ref += hy.refined;
+    S.hyp[hl] = make_float4(hy.nx, hy.ny, hy.nz, hy.kind == kHypRejected ? __int_as_float(0x7fc00000) : hy.thi);
+    S.tlo[hl] = hy.tlo;
+    S.kind[hl] = (int8_t)hy.kind;
+    if constexpr (DIM == 2) {
+      // the queue lives in U until the second pass has read it
+      if (hy.kind == kHypNormal && hy.thi - a.tau32.hi > refine_band) S.U[atomicAdd(&cs.nref, 1)] = hl;
+    } else {
+      S.U[hl] = hy.kind == kHypRejected ? -1 : (hy.kind == kHypExactOnly ? N : 0);
+    }
+  }
+  if constexpr (DIM == 2) {
+    __syncthreads();
+    const int nr = 8 * cs.nref >= nh ? cs.nref : 0;
+    for (int i = tid; i < nr; i += kThreads) {
+      const int hl = S.U[i];
+      int q[3];
+      draw_minimal_set<DIM>(a.key, a.cluster_base + ci, hc0 + hl, N, q);
+      const int qs[3] = {q[0], q[1], q[0]};
+      // seed rows from the frame's arrays: keeping the loaded FP32 rows
+      // alive across the solve instead measured slower on trials that refine
+      auto seed64 = [&](int k) { return R.at(qs[k]); };
+      // the trial was accepted in the first pass: no conditioning test
+      Hyp32 hy = hyp_f32<DIM>(rows.at(q[0]), rows.at(q[1]), rows.at(q[0]), seed64, refine_band, wmax, 0.0f,
+                              0.0f, a.tau32);
+      if (hy.kind != kHypNormal) {
+        hy.kind = kHypExactOnly;
+        hy.thi = __int_as_float(0x7f800000);
+        hy.tlo = -1.0f;
+        ++n_fp64;
+      }
+      n_ref += hy.refined;
+      S.hyp[hl] = make_float4(hy.nx, hy.ny, hy.nz, hy.thi);
+      S.tlo[hl] = hy.tlo;
+      S.kind[hl] = (int8_t)hy.kind;
+    }
+    __syncthreads();
+    for (int hl = tid; hl < nh; hl += kThreads) {
+      const int k = S.kind[hl];
+      S.U[hl] = k == kHypRejected ? -1 : (k == kHypExactOnly ? N : 0);
+    }
+    if (tid == 0) cs.nref = 0;
+  }
+  *fp64_count += n_fp64;
+  *refined_count += n_ref;
+}
+
 template <int DIM, bool SMEM_ROWS, bool EXT>
 __device__ void process_cluster(const FrameDesc& a, const Smem& S, ClusterShared& cs, int ci, int hchunk,
                                 int pw, int hpl, int frame, FinishRec* fq, int* fq_n, double4_32a* cta_pre) {
@@ -795,7 +884,7 @@ __device__ void process_cluster(const FrameDesc& a, const Smem& S, ClusterShared
     if (tid == 0) write_invalid<DIM>(a, ci, RVH_STATUS_TOO_FEW_POINTS);
     return;
   }
-  using RV = typename std::conditional<SMEM_ROWS, TileRows, AosRows>::type;
+  using RV = typename std::conditional<SMEM_ROWS, TileRowsOf<DIM>, AosRows>::type;
   RV rows;
   if constexpr (SMEM_ROWS) {
     rows.f = S.rows;
@@ -867,84 +956,8 @@ __device__ void process_cluster(const FrameDesc& a, const Smem& S, ClusterShared
   for (int hc0 = 0; hc0 < a.H; hc0 += chunk) {
     const int nh = min(chunk, a.H - hc0);
     // a2 + a3: draw, FP32 solve (refined when ill-conditioned), bound
-    // Trials with a wide band refine their velocity.  3D minimal sets are
-    // often ill-conditioned and refine on the spot above kRefineBand.  2D ones
-    // have |det| = |sin(t1 - t0)| and mostly narrow bands, whose few band
-    // points cost less than refining; those above tau / 32 are queued, and
-    // when they are at least an eighth of the chunk (a cluster of narrow
-    // azimuth extent, such as a far object, where nearly every seed pair is
-    // ill-conditioned) a second pass refines them, one per lane.  Elsewhere
-    // the pass's latency would cost more than the band points it saves;
-    // either way the decisions are exact.
-    const float refine_band = DIM == 3 ? kRefineBand : a.tau32.hi * 0x1p-5f;
     auto cosine_trials = [&]() {
-      for (int hl = tid; hl < nh; hl += kThreads) {
-        int q[3];
-        draw_minimal_set<DIM>(a.key, a.cluster_base + ci, hc0 + hl, N, q);
-        const int q2 = DIM == 3 ? q[2] : q[0];
-        const float4 p0 = rows.at(q[0]), p1 = rows.at(q[1]), p2 = rows.at(q2);
-        const int qs[3] = {q[0], q[1], q2};
-        auto seed64 = [&](int i) { return R.at(qs[i]); };
-        const float rb = DIM == 3 ? refine_band : __int_as_float(0x7f800000);
-        Hyp32 hy = hyp_f32<DIM>(p0, p1, p2, seed64, rb, wmax, a.acc, a.rej, a.tau32);
-        if (hy.kind == kHypUndecided) {
-          ++n_fp64;
-          double v[3];
-          if (hyp_f64<DIM>(a, R, ci, hc0 + hl, N, v)) {
-            hy = hyp_f32<DIM>(p0, p1, p2, seed64, rb, wmax, 0.0f, 0.0f, a.tau32);
-            if (hy.kind != kHypNormal) {
-              hy.kind = kHypExactOnly;
-              hy.thi = __int_as_float(0x7f800000);
-              hy.tlo = -1.0f;
-            }
-          } else {
-            hy.kind = kHypRejected;
-          }
-        }
-        if (hy.kind == kHypExactOnly) ++n_fp64;
-        n_ref += hy.refined;
-        S.hyp[hl] = make_float4(hy.nx, hy.ny, hy.nz, hy.kind == kHypRejected ? __int_as_float(0x7fc00000) : hy.thi);
-        S.tlo[hl] = hy.tlo;
-        S.kind[hl] = (int8_t)hy.kind;
-        if constexpr (DIM == 2) {
-          // the queue lives in U until the second pass has read it
-          if (hy.kind == kHypNormal && hy.thi - a.tau32.hi > refine_band) S.U[atomicAdd(&cs.nref, 1)] = hl;
-        } else {
-          S.U[hl] = hy.kind == kHypRejected ? -1 : (hy.kind == kHypExactOnly ? N : 0);
-        }
-      }
-      if constexpr (DIM == 2) {
-        __syncthreads();
-        const int nr = 8 * cs.nref >= nh ? cs.nref : 0;
-        for (int i = tid; i < nr; i += kThreads) {
-          const int hl = S.U[i];
-          int q[3];
-          draw_minimal_set<DIM>(a.key, a.cluster_base + ci, hc0 + hl, N, q);
-          const int qs[3] = {q[0], q[1], q[0]};
-          // seed rows from the frame's arrays: keeping the loaded FP32 rows
-          // alive across the solve instead measured slower on trials that refine
-          auto seed64 = [&](int k) { return R.at(qs[k]); };
-          // the trial was accepted in the first pass: no conditioning test
-          Hyp32 hy = hyp_f32<DIM>(rows.at(q[0]), rows.at(q[1]), rows.at(q[0]), seed64, refine_band, wmax, 0.0f,
-                                  0.0f, a.tau32);
-          if (hy.kind != kHypNormal) {
-            hy.kind = kHypExactOnly;
-            hy.thi = __int_as_float(0x7f800000);
-            hy.tlo = -1.0f;
-            ++n_fp64;
-          }
-          n_ref += hy.refined;
-          S.hyp[hl] = make_float4(hy.nx, hy.ny, hy.nz, hy.thi);
-          S.tlo[hl] = hy.tlo;
-          S.kind[hl] = (int8_t)hy.kind;
-        }
-        __syncthreads();
-        for (int hl = tid; hl < nh; hl += kThreads) {
-          const int k = S.kind[hl];
-          S.U[hl] = k == kHypRejected ? -1 : (k == kHypExactOnly ? N : 0);
-        }
-        if (tid == 0) cs.nref = 0;
-      }
+      cosine_trial_chunk<DIM, RV>(a, rows, R, S, cs, ci, N, hc0, nh, wmax, &n_fp64, &n_ref);
     };
     if constexpr (EXT && DIM == 2) {
       if (a.line_model) {
@@ -1147,8 +1160,9 @@ __global__ void __launch_bounds__(kThreads, RVH_MIN_BLOCKS) fused_kernel(const _
     const FrameDesc& F = a.f[fc.x];
     const int ci = fc.y;
     const int64_t o = F.offsets[ci], e = F.offsets[ci + 1];
-    double4_32a* cta_pre = a.cta_rows64 ? a.cta_rows64 + (size_t)blockIdx.x * a.nmax_smem : nullptr;
-    if (e - o <= (int64_t)a.nmax_smem || e < o) {
+    double4_32a* cta_pre =
+        a.cta_rows64 ? a.cta_rows64 + (size_t)blockIdx.x * smem_row_capacity(2, a.nmax_smem) : nullptr;
+    if (e - o <= (int64_t)smem_row_capacity(DIM, a.nmax_smem) || e < o) {
       process_cluster<DIM, true, EXT>(F, S, cs, ci, a.hchunk, a.pw, a.hpl, fc.x, fq, &fq_n, cta_pre);
     } else {
       process_cluster<DIM, false, EXT>(F, S, cs, ci, a.hchunk, a.pw, a.hpl, fc.x, fq, &fq_n, cta_pre);

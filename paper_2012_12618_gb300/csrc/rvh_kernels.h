@@ -26,7 +26,7 @@ struct FrameDesc {
   int32_t n_clusters;
   int32_t H;
   int64_t n_points;
-  float4* rows_g;            // [n_points] FP32 rows of clusters larger than nmax_smem
+  float4* rows_g;            // [n_points] FP32 rows of clusters beyond the shared-memory row capacity
   double4_32a* rows64_g;         // [n_points] FP64 rows (a0, a1, a2, w) of every point
   const double2* trig;       // (cos, sin)(k/128), k = -420..420
   double tau;
@@ -65,11 +65,19 @@ struct FusedArgs {
   int hchunk;
   int pw, hpl;
   int direct;                // 1: one item per CTA, item = blockIdx.x (no work list)
-  // [grid * nmax_smem] FP64 rows, one slot per CTA, used for clusters of at
-  // most nmax_smem points (a working set that stays in L2); NULL: every
-  // cluster uses its frame's per-point rows64_g
+  // [grid * smem_row_capacity(2, nmax_smem)] FP64 rows, one slot per CTA,
+  // used for clusters whose rows fit shared memory (a working set that
+  // stays in L2); NULL: every cluster uses its frame's per-point rows64_g
   double4_32a* cta_rows64;
 };
+
+// Points of a cluster whose FP32 rows fit the shared-memory row area of a
+// fused launch, roundup32(nmax_smem) rows of 16 bytes: 3D rows (a0, a1, a2,
+// w) take 16 bytes, 2D rows (c, s, w) 12, so 2D fits four thirds as many.
+// The CTAs' FP64 row slots hold the 2D capacity, the larger one.
+__host__ __device__ inline int smem_row_capacity(int dim, int nmax_smem) {
+  return dim == 2 ? ((((nmax_smem + 31) & ~31) * 4 / 3) & ~31) : nmax_smem;
+}
 
 size_t fused_smem_bytes(int nmax_smem, int hchunk);
 // Opts both instantiations of the fused kernel of this model dimension in to

@@ -21,7 +21,7 @@ constexpr int kWarps = kThreads / 32;
 #endif
 
 struct Smem {
-  float* rows;        // [roundup32(nmax_smem) * 4] row tiles (TileRows)
+  float* rows;        // [roundup32(nmax_smem) * 4] floats of row tiles (TileRows)
   float4* hyp;        // [hchunk] (-X, -Y, -Z, thi)
   float* tlo;         // [hchunk]
   int* U;             // [hchunk] upper bounds of the exact counts (-1 = rejected)
@@ -30,29 +30,33 @@ struct Smem {
 
 // ---- FP32 rows of the cluster being processed ---------------------------------------
 // Shared memory holds them as tiles of 32 points, component-major inside a
-// tile (32 c | 32 s | 32 w | 32 t in 2D; 32 a0 | 32 a1 | 32 a2 | 32 w in
-// 3D): a warp reading consecutive points touches 32 banks per component, and
-// four consecutive points of one component are one aligned float4, which the
-// scoring pass consumes as two packed pairs.  Clusters larger than the shared
-// memory area keep plain float4 rows in global scratch.
+// tile (32 c | 32 s | 32 w in 2D; 32 a0 | 32 a1 | 32 a2 | 32 w in 3D): a
+// warp reading consecutive points touches 32 banks per component, and four
+// consecutive points of one component are one aligned float4, which the
+// scoring pass consumes as two packed pairs.  NC = 3 (2D) or 4 (3D)
+// components; at() of a 2D row leaves .w zero.  Clusters larger than the
+// shared memory area keep plain float4 rows in global scratch.
+template <int NC>
 struct TileRows {
   float* f;
   __device__ __forceinline__ float4 at(int j) const {
-    const float* b = f + ((j >> 5) << 7) + (j & 31);
-    return make_float4(b[0], b[32], b[64], b[96]);
+    const float* b = f + (j >> 5) * (32 * NC) + (j & 31);
+    return make_float4(b[0], b[32], b[64], NC == 4 ? b[96] : 0.0f);
   }
   __device__ __forceinline__ void put(int j, float4 v) const {
-    float* b = f + ((j >> 5) << 7) + (j & 31);
+    float* b = f + (j >> 5) * (32 * NC) + (j & 31);
     b[0] = v.x;
     b[32] = v.y;
     b[64] = v.z;
-    b[96] = v.w;
+    if (NC == 4) b[96] = v.w;
   }
   // component k of points 4q .. 4q + 3
   __device__ __forceinline__ float4 quad(int q, int k) const {
-    return *reinterpret_cast<const float4*>(f + ((q >> 3) << 7) + (k << 5) + ((q & 7) << 2));
+    return *reinterpret_cast<const float4*>(f + (q >> 3) * (32 * NC) + (k << 5) + ((q & 7) << 2));
   }
 };
+template <int DIM>
+using TileRowsOf = TileRows<DIM == 2 ? 3 : 4>;
 
 struct AosRows {
   float4* p;
@@ -76,13 +80,22 @@ __device__ __forceinline__ unsigned long long fma2(unsigned long long a, unsigne
   asm("fma.rn.f32x2 %0, %1, %2, %3;" : "=l"(d) : "l"(a), "l"(b), "l"(c));
   return d;
 }
-// Appends the sign bit of e to a 32-bit history of sign bits: the high word
-// of (acc:e) << 1, i.e. (acc << 1) | (e >> 31), one funnel shift on the
-// integer pipe.
-__device__ __forceinline__ uint32_t push_sign(uint32_t acc, float e) {
+// Sign masks of two floats in one word: 0x0000FFFF if lo < 0 (sign bit set),
+// plus 0xFFFF0000 if hi < 0 -- one byte permute (prmt, msb-replicating
+// selectors) on the integer pipe.  Summed as 32-bit integers over many
+// points, the words give A = 0xFFFF (S_lo + 2^16 S_hi) mod 2^32, with S_lo
+// and S_hi the numbers of negative lo and hi values; sign_count recovers
+// S_lo + S_hi while both stay below 2^16.
+__device__ __forceinline__ uint32_t sign_pair(float lo, float hi) {
   uint32_t d;
-  asm("shf.l.clamp.b32 %0, %1, %2, 1;" : "=r"(d) : "r"(__float_as_uint(e)), "r"(acc));
+  asm("prmt.b32 %0, %1, %2, 0xFFBB;" : "=r"(d) : "r"(__float_as_uint(lo)), "r"(__float_as_uint(hi)));
   return d;
+}
+// 0xFFFEFFFF is the inverse of 0xFFFF modulo 2^32: (2^16 - 1)(2^32 - 2^16 - 1)
+// = 2^48 - 2^33 + 1.
+__device__ __forceinline__ int sign_count(uint32_t acc) {
+  const uint32_t x = acc * 0xFFFEFFFFu;  // S_lo + 2^16 S_hi
+  return (int)(x & 0xFFFFu) + (int)(x >> 16);
 }
 
 // -C with C the smallest float above thi^2 rounded up: C > thi^2, so
@@ -102,16 +115,15 @@ __device__ __forceinline__ float neg_count_bound(float thi) {
 // #{|r32| <= thi} that exceeds it only by points within two ulps of thi^2.
 // NaN residuals (NaN Dopplers, the padding) give the canonical NaN, whose
 // sign bit is clear, so they do not count (a NaN that did would only loosen
-// the bound).  The
-// count leaves the FP32 pipe: sign bits are shifted into a 32-bit history
-// (push_sign, integer pipe) and popcounted every block of quads (8 quads = 32
-// points fill the history exactly; 2D uses blocks of 4 with a reset, which
-// measured faster for its shorter loop body).
+// the bound).  The count leaves the FP32 pipe: per quad and trial two byte
+// permutes turn the four sign bits into 16-bit masks and one three-input
+// integer add accumulates them (sign_pair / sign_count: even and odd points
+// of a lane stay below 2^16 each, since a cluster in shared memory has at
+// most 227 KB / 16 B points).
 template <int DIM, int PW, int HPL>
-__device__ __forceinline__ void phase_a_tiles(const TileRows rows, int N, const Smem& S, int nh) {
+__device__ __forceinline__ void phase_a_tiles(const TileRowsOf<DIM> rows, int N, const Smem& S, int nh) {
   constexpr int NHL = 32 / PW;
   constexpr int G = NHL * HPL;
-  constexpr int BLOCK = DIM == 2 ? 4 : 8;  // quads per popcount
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const int hl = lane / PW, pl = lane % PW;
   const int ngroups = (nh + G - 1) / G;
@@ -119,8 +131,7 @@ __device__ __forceinline__ void phase_a_tiles(const TileRows rows, int N, const 
   for (int g = warp; g < ngroups; g += kWarps) {
     const int base = g * G + hl * HPL;
     unsigned long long nx[HPL], ny[HPL], nz[HPL], nc[HPL];
-    uint32_t bits[HPL];
-    int cnt[HPL];
+    uint32_t acc[HPL];
 #pragma unroll
     for (int m = 0; m < HPL; ++m) {
       const int h = base + m;
@@ -130,8 +141,7 @@ __device__ __forceinline__ void phase_a_tiles(const TileRows rows, int N, const 
       nz[m] = pack2(v.z, v.z);
       const float c = neg_count_bound(v.w);
       nc[m] = pack2(c, c);
-      bits[m] = 0u;
-      cnt[m] = 0;
+      acc[m] = 0u;
     }
     auto quad = [&](int q) {
       const float4 c = rows.quad(q, 0), sn = rows.quad(q, 1), w = rows.quad(q, DIM == 2 ? 2 : 3);
@@ -157,25 +167,20 @@ __device__ __forceinline__ void phase_a_tiles(const TileRows rows, int N, const 
         float e0, e1, e2, e3;
         unpack2(fma2(r01, r01, nc[m]), e0, e1);
         unpack2(fma2(r23, r23, nc[m]), e2, e3);
-        bits[m] = push_sign(push_sign(push_sign(push_sign(bits[m], e0), e1), e2), e3);
+        acc[m] += sign_pair(e0, e1) + sign_pair(e2, e3);
       }
     };
+    constexpr int UN = DIM == 2 ? 8 : 4;  // quads per loop iteration (measured)
     int q = pl;
-    for (; q + (BLOCK - 1) * PW < nq; q += BLOCK * PW) {
+    for (; q + (UN - 1) * PW < nq; q += UN * PW) {
 #pragma unroll
-      for (int u = 0; u < BLOCK; ++u) quad(q + u * PW);
-#pragma unroll
-      for (int m = 0; m < HPL; ++m) {
-        cnt[m] += __popc(bits[m]);
-        if (BLOCK < 8) bits[m] = 0u;  // a block of 8 quads shifts all 32 bits out
-      }
+      for (int u = 0; u < UN; ++u) quad(q + u * PW);
     }
-#pragma unroll
-    for (int m = 0; m < HPL; ++m) bits[m] = 0u;
-    for (; q < nq; q += PW) quad(q);  // fewer than BLOCK quads
+    for (; q < nq; q += PW) quad(q);
+    int cnt[HPL];
 #pragma unroll
     for (int m = 0; m < HPL; ++m) {
-      cnt[m] += __popc(bits[m]);
+      cnt[m] = sign_count(acc[m]);
 #pragma unroll
       for (int o = PW / 2; o > 0; o >>= 1) cnt[m] += __shfl_xor_sync(0xffffffffu, cnt[m], o);
     }

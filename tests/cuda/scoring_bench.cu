@@ -52,7 +52,7 @@ __global__ void __launch_bounds__(kThreads, RVH_MIN_BLOCKS)
   S.U = reinterpret_cast<int*>(p);
   p += (size_t)kH * sizeof(int);
   S.kind = reinterpret_cast<int8_t*>(p);
-  const TileRows rows{S.rows};
+  const TileRowsOf<DIM> rows{S.rows};
   for (int j = threadIdx.x; j < N; j += kThreads) rows.put(j, pts[j]);
   if (threadIdx.x < ((N + 3) & ~3) - N) {
     const float nan = __int_as_float(0x7fc00000);
