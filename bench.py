@@ -237,7 +237,7 @@ def measure_workload(ctx, name, dev, stream, sptr, flush, steps, sms, max_mhz):
         flush.fill_(2)
         ctx.check(rvh.rvh_estimate(ctx.handle, frame, params, res, sptr), "rvh_estimate")
     torch.cuda.synchronize()
-    step_ms, kern_ms, phase, band = [], [], np.zeros(6), 0
+    step_ms, kern_ms, phase, band, scored = [], [], np.zeros(6), 0, 0
     with ClockSampler(dev.index or 0) as clk:
         for i in range(steps):
             flush.fill_(np.uint8(i & 0xFF))
@@ -252,10 +252,14 @@ def measure_workload(ctx, name, dev, stream, sptr, flush, steps, sms, max_mhz):
             kern_ms.append(stats.kernel_ms)
             phase += np.array(list(stats.phase_cycles), dtype=np.float64)
             band += stats.band_points
+            scored += stats.pairs_scored
     ck = clk.summary()
     k_s = float(np.mean(kern_ms)) * 1e-3
     t_s = float(np.mean(step_ms)) * 1e-3
-    flops = 2.0 * dim * pairs
+    # the roofline counts the (trial, point) pairs the scoring pass evaluated:
+    # with exact pruning, fewer than the method's N x H
+    scored_per_step = scored / max(steps, 1)
+    flops = 2.0 * dim * scored_per_step
     peak = sms * FP32_LANES_PER_SM * 2 * max_mhz * 1e6 / 1e12
     ach = flops / k_s / 1e12
     share = float(phase[2] / max(phase.sum(), 1.0))
@@ -264,7 +268,9 @@ def measure_workload(ctx, name, dev, stream, sptr, flush, steps, sms, max_mhz):
                        f"{dim}D, H={w.num_hypotheses}, tau={w.tau} m/s, outliers {w.outlier_frac:g}, "
                        f"noise {w.noise_sigma:g} m/s",
            "steps": steps, "ms_per_step": t_s * 1e3, "kernel_ms": k_s * 1e3, "clusters_per_s": nc / t_s,
-           "pair_evals_per_s": pairs / t_s, "roofline_achieved_tflops": ach, "roofline_frac": ach / peak,
+           "pair_evals_per_s": pairs / t_s, "pairs_scored_fraction": scored_per_step / pairs,
+           "roofline_achieved_tflops": ach, "roofline_frac": ach / peak,
+           "roofline_frac_full_pairs": 2.0 * dim * pairs / k_s / 1e12 / peak,
            "roofline_frac_at_measured_clock": ach / at_clk if at_clk else None,
            "scoring_loop_frac": (flops / (share * k_s) / 1e12) / peak if share > 0 else None,
            "scoring_stage_share": share, "fp64_band_decisions_per_step": band / max(steps, 1),
@@ -401,6 +407,8 @@ def main():
     ap.add_argument("--workload-steps", type=int, default=100,
                     help="timed steps of each of the other single-frame workloads (frame64, stress2d, dense3d "
                          "beside the headline one; 0 skips them)")
+    ap.add_argument("--unpruned-steps", type=int, default=200,
+                    help="steps timed again with exact pruning off (roofline.unpruned; 0 skips them)")
     ap.add_argument("--refine-iterations", type=int, default=0,
                     help="local-optimisation rounds in the timed steps (default 0: the single-pass method)")
     ap.add_argument("--local-opt-steps", type=int, default=50,
@@ -486,7 +494,7 @@ def main():
     torch.cuda.synchronize()
 
     step_ms, kern_ms = [], []
-    band = cand = fp64h = refined = launches = 0
+    band = cand = fp64h = refined = launches = scored = 0
     phase = np.zeros(6)
     if ws > 1:
         torch.distributed.barrier()
@@ -509,6 +517,7 @@ def main():
             fp64h += stats.fp64_hypotheses
             refined += stats.refined_hypotheses
             launches += stats.kernel_launches
+            scored += stats.pairs_scored
             phase += np.array(list(stats.phase_cycles), dtype=np.float64)
         torch.cuda.synchronize()
     wall = time.perf_counter() - t_wall
@@ -550,7 +559,10 @@ def main():
 
     # ---- roofline of the fused kernel (FP32 pipe; k FMA = 2k flop per trial x point pair)
     kern_s = float(np.mean(kern_ms)) * 1e-3
-    flops = 2.0 * dim * pairs
+    # the (trial, point) pairs the scoring pass evaluated: the method's N x H
+    # less those of trials dropped by exact pruning (they cannot win)
+    scored_per_step = scored / max(args.steps, 1)
+    flops = 2.0 * dim * scored_per_step
     achieved = flops / kern_s / 1e12
     props = torch.cuda.get_device_properties(dev)
     sms = props.multi_processor_count
@@ -568,7 +580,10 @@ def main():
                 "peak_basis": f"{sms} SMs x {FP32_LANES_PER_SM} FP32 FMA lanes x 2 flop x {max_mhz:.0f} MHz",
                 "frac_at_measured_clock": (achieved / (sms * FP32_LANES_PER_SM * 2 * clocks["sm_mhz"] * 1e6 / 1e12)
                                            if clocks.get("sm_mhz") else None),
-                "algorithmic_flops_per_launch": flops, "kernel_ms": kern_s * 1e3}
+                "algorithmic_flops_per_launch": flops, "kernel_ms": kern_s * 1e3,
+                "pairs_basis": "trial x point pairs the scoring pass evaluated (rvh_stats.pairs_scored)",
+                "pairs_scored_fraction": scored_per_step / pairs,
+                "frac_full_pairs": 2.0 * dim * pairs / kern_s / 1e12 / peak}
     # the scoring pass alone: its share of the per-CTA stage clocks (clock64,
     # summed over CTAs) times the kernel time; co-resident CTAs in other
     # stages share the SM meanwhile, so this is an attribution, not a solo run
@@ -581,6 +596,26 @@ def main():
         roofline["scoring_loop_frac_at_measured_clock"] = (
             sc / (sms * FP32_LANES_PER_SM * 2 * clocks["sm_mhz"] * 1e6 / 1e12) if clocks.get("sm_mhz") else None)
         roofline["scoring_loop_basis"] = "scoring-pass share of the per-CTA stage clocks x kernel time"
+    if clocks.get("sm_mhz") and grid:
+        # CTA clocks summed over the persistent grid against grid x kernel time:
+        # what is missing is the tail after each CTA's last cluster
+        roofline["cta_busy_fraction"] = float(phase.sum()) / (args.steps * grid * kern_s * clocks["sm_mhz"] * 1e6)
+
+    # the same kernel without pruning (every trial over every point), for the
+    # kernel-quality fraction on the full pair count
+    if rank == 0 and args.unpruned_steps > 0:
+        ctx.check(rvh.rvh_set_pruning(ctx.handle, 0), "rvh_set_pruning")
+        u_ms = []
+        for i in range(3 + args.unpruned_steps):
+            flush.fill_(np.uint8(i & 0xFF))
+            step()
+            ctx.check(rvh.rvh_get_stats(ctx.handle, stats), "rvh_get_stats")
+            if i >= 3:
+                u_ms.append(stats.kernel_ms)
+        ctx.check(rvh.rvh_set_pruning(ctx.handle, 1), "rvh_set_pruning")
+        u_s = float(np.mean(u_ms)) * 1e-3
+        roofline["unpruned"] = {"kernel_ms": u_s * 1e3, "frac": 2.0 * dim * pairs / u_s / 1e12 / peak,
+                                "steps": args.unpruned_steps}
 
     # ---- the other single-frame workloads, each timed like the headline one
     workloads = {}

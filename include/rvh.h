@@ -331,6 +331,8 @@ typedef struct {
   int64_t serving_steps;       /* serving steps launched by the context's request loop (rvh_submit) */
   int64_t serving_graph_replays; /* serving steps that replayed an instantiated graph (work list + fused
                                     kernel) with that step's batch of frames */
+  int64_t pairs_scored;        /* trial x point pairs the scoring pass of the last rvh_estimate evaluated:
+                                  pair_evals without pruning, fewer with it (rvh_set_pruning) */
 } rvh_stats;
 
 /* Counters of the last rvh_estimate on this context (synchronises its stream). */
@@ -340,6 +342,19 @@ int rvh_get_stats(rvh_ctx* ctx, rvh_stats* out);
  * per trial group) and hyps_per_lane in {4, 8}; 0 restores the automatic
  * choice. */
 int rvh_set_schedule(rvh_ctx* ctx, int32_t points_per_warp, int32_t hyps_per_lane);
+
+/* Staged scoring with exact pruning (default on): the scoring pass of a
+ * cluster of at least 256 points whose rows fit shared memory (the
+ * lanes-over-trials schedule, points_per_warp 1) runs in stages of 128
+ * points; after the first, the trial with the highest partial count is
+ * counted exactly and leads, and after each stage a trial whose partial
+ * count plus the points still to come cannot beat the lead's (count, lower
+ * index) key is dropped.  Counts only grow by one per point and the exact
+ * count never exceeds the upper-bound count, so no dropped trial can win:
+ * every output equals the unpruned pass's (the winner of Sec. III-A over
+ * all trials of Alg. 1), with fewer (trial, point) evaluations
+ * (rvh_stats.pairs_scored).  enabled: 1 on, 0 off. */
+int rvh_set_pruning(rvh_ctx* ctx, int32_t enabled);
 
 /* A scoring schedule and its measured fused-kernel time. */
 typedef struct {

@@ -194,6 +194,7 @@ struct rvh_ctx {
   bool graphs = true;
   rvh::LaunchGraph graph[2][2];
   bool cta_rows = true;  // per-CTA FP64 row slots for clusters that fit shared memory
+  bool prune = true;     // staged scoring pass with exact pruning (rvh_set_pruning)
   std::string tune_prefix;                    // "<gpu name>|<sms>|"
   bool last_counts_trials = false;  // the last launch counted its trials on the device (extensions)
 };
@@ -313,6 +314,7 @@ int prepare_launch(rvh_ctx* ctx, FusedArgs& a, int dim, int* grid, size_t* smem)
   // when every item gets its own resident CTA the order cannot matter: skip
   // the work-list kernel
   a.direct = a.n_items <= resident ? 1 : 0;
+  a.prune = ctx->prune ? 1 : 0;
   return RVH_OK;
 }
 
@@ -340,7 +342,7 @@ int launch_graph(rvh_ctx* ctx, FusedArgs& a, int dim, cudaStream_t s) {
   size_t smem = 0;
   int rc = prepare_launch(ctx, a, dim, &grid, &smem);
   if (rc) return rc;
-  RVH_CUDA(cudaMemsetAsync(a.stats, 0, 96, s));
+  RVH_CUDA(cudaMemsetAsync(a.stats, 0, sizeof(unsigned long long) * kStatsWords, s));
   if (!a.direct) RVH_CUDA(launch_worklist(a, s));
   RVH_CUDA(cudaEventRecord(ctx->ev0, s));
   const cudaError_t e = ctx->graph[dim == 3][fused_ext(a) ? 1 : 0].launch(a, dim, grid, smem, false, s);
@@ -542,13 +544,21 @@ int rvh_set_schedule(rvh_ctx* ctx, int32_t pw, int32_t hpl) {
   return RVH_OK;
 }
 
+int rvh_set_pruning(rvh_ctx* ctx, int32_t enabled) {
+  if (!ctx) return fail(RVH_EINVAL, "ctx is NULL");
+  if (enabled != 0 && enabled != 1) return fail(RVH_EINVAL, "enabled must be 0 or 1");
+  std::lock_guard<std::mutex> lk(ctx->mu);
+  ctx->prune = enabled != 0;
+  return RVH_OK;
+}
+
 int rvh_get_stats(rvh_ctx* ctx, rvh_stats* out) {
   if (!ctx || !out) return fail(RVH_EINVAL, "NULL argument");
   std::lock_guard<std::mutex> lk(ctx->mu);
   RVH_CUDA(cudaSetDevice(ctx->device));
   if (ctx->have_launch) {
     RVH_CUDA(cudaEventSynchronize(ctx->last_done));
-    unsigned long long h[12] = {0, 0, 0, 0, 0, 0, 0, 0, 0, 0, 0, 0};
+    unsigned long long h[kStatsWords] = {};
     RVH_CUDA(cudaMemcpy(h, ctx->stats_d, sizeof(h), cudaMemcpyDeviceToHost));
     if (ctx->last_counts_trials) {  // the kernel counted the trials it ran
       ctx->last.hypotheses = (int64_t)h[10];
@@ -559,6 +569,7 @@ int rvh_get_stats(rvh_ctx* ctx, rvh_stats* out) {
     ctx->last.candidates = (int64_t)h[0];
     ctx->last.band_points = (int64_t)h[1];
     ctx->last.fp64_hypotheses = (int64_t)h[2];
+    ctx->last.pairs_scored = (int64_t)h[12];
     float ms = 0.f;
     if (cudaEventElapsedTime(&ms, ctx->ev0, ctx->ev1) == cudaSuccess) ctx->last.kernel_ms = ms;
     else cudaGetLastError();
@@ -734,7 +745,7 @@ int rvh_estimate(rvh_ctx* ctx, const rvh_frame* frame, const rvh_params* params,
   if (ctx->graphs && s != nullptr && cap == cudaStreamCaptureStatusNone) {
     rc = launch_graph(ctx, a, params->model_dim, s);
   } else {
-    RVH_CUDA(cudaMemsetAsync(st.stats, 0, 96, s));
+    RVH_CUDA(cudaMemsetAsync(st.stats, 0, sizeof(unsigned long long) * kStatsWords, s));
     rc = launch_batch(ctx, a, params->model_dim, s, ctx->ev0, ctx->ev1);
   }
   if (rc) return rc;

@@ -245,6 +245,7 @@ struct ClusterShared {
   int sel_digit, sel_k;       // radix select: digit and rank inside it
   float red4[4][kWarps];      // line model: min / max of azimuth and Doppler
   unsigned long long runs[2];  // trials run, pairs scored
+  unsigned long long scored;   // (trial, point) pairs the scoring pass evaluated
   int nref;                   // 2D trials queued for refinement in the current chunk
 };
 
@@ -601,7 +602,7 @@ __device__ __noinline__ void finish_cluster(const FrameDesc& a, const Rows64Inpu
 // together, one lane each.  Serial FP64 on one lane costs as much pipe time
 // per instruction as a full warp, so a lone thread finishing each cluster
 // kept the other 255 threads at the next barrier for microseconds.
-constexpr int kFinishBatch = 32;
+constexpr int kFinishBatch = 16;
 struct FinishRec {
   double t[9];
   double v64[3];
@@ -778,6 +779,60 @@ __device__ __noinline__ int local_opt_rounds(const FrameDesc& a, const RV rows, 
   return n_in;
 }
 
+// Keeps, in order, the entries of S.list[0 .. n) (from_list) or the trials
+// 0 .. n - 1 for which keep(h) holds, writing them to S.list[0 ..); returns
+// how many.  Entries are read before any is written (compaction in place).
+// red: kWarps ints of shared memory.
+template <typename Keep>
+__device__ __forceinline__ int compact_list(const Smem& S, int n, bool from_list, Keep keep, int* red) {
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+  int out = 0;
+  for (int r0 = 0; r0 < n; r0 += 4 * kThreads) {
+    int hv[4], c = 0;
+#pragma unroll
+    for (int k = 0; k < 4; ++k) {
+      const int i = r0 + 4 * tid + k;
+      int h = -1;
+      if (i < n) {
+        h = from_list ? (int)S.list[i] : i;
+        if (!keep(h)) h = -1;
+      }
+      hv[k] = h;
+      c += h >= 0 ? 1 : 0;
+    }
+    int incl = c;
+#pragma unroll
+    for (int d = 1; d < 32; d <<= 1) {
+      const int t = __shfl_up_sync(0xffffffffu, incl, d);
+      if (lane >= d) incl += t;
+    }
+    if (lane == 31) red[warp] = incl;
+    __syncthreads();
+    int pos = out + incl - c, tot = 0;
+#pragma unroll
+    for (int w = 0; w < kWarps; ++w) {
+      const int v = red[w];
+      tot += v;
+      pos += w < warp ? v : 0;
+    }
+#pragma unroll
+    for (int k = 0; k < 4; ++k)
+      if (hv[k] >= 0) S.list[pos++] = (uint16_t)hv[k];
+    out += tot;
+    __syncthreads();
+  }
+  return out;
+}
+
+// Quads (4 points) per stage of the staged scoring pass.
+constexpr int kStageQuads = 32;
+#ifndef RVH_STAGE_MIN_N
+#define RVH_STAGE_MIN_N 512
+#endif
+#ifndef RVH_STAGE_GROWTH
+#define RVH_STAGE_GROWTH 1
+#endif
+
 // a2 + a3 for trials hc0 .. hc0 + nh - 1 of cluster ci under the cosine
 // model: draw, FP32 solve (refined when ill-conditioned), bound, records
 // into S.  Trials with a wide band refine their velocity.  3D minimal sets
@@ -870,7 +925,8 @@ __device__ __forceinline__ void cosine_trial_chunk(const FrameDesc& a, const RV 
 
 template <int DIM, bool SMEM_ROWS, bool EXT>
 __device__ void process_cluster(const FrameDesc& a, const Smem& S, ClusterShared& cs, int ci, int hchunk,
-                                int pw, int hpl, int frame, FinishRec* fq, int* fq_n, double4_32a* cta_pre) {
+                                int pw, int hpl, int prune, int frame, FinishRec* fq, int* fq_n,
+                                double4_32a* cta_pre) {
   const int tid = threadIdx.x;
   const int64_t o = a.offsets[ci];
   const int64_t e = a.offsets[ci + 1];
@@ -947,7 +1003,7 @@ __device__ void process_cluster(const FrameDesc& a, const Smem& S, ClusterShared
   }
   __syncthreads();
   const float wmax = cs.wmax;
-  unsigned long long n_fp64 = 0, n_cand = 0, n_ref = 0;
+  unsigned long long n_fp64 = 0, n_cand = 0, n_ref = 0, n_scored = 0;
   stage_done(0);
 
   // trials run in chunks of hchunk, or in the adaptive blocks of trial_block
@@ -988,28 +1044,10 @@ __device__ void process_cluster(const FrameDesc& a, const Smem& S, ClusterShared
     __syncthreads();
     stage_done(1);
 
-    // a4: scoring pass (the hot loop)
-    phase_a_dispatch<DIM>(pw, hpl, rows, N, S, nh);
-    __syncthreads();
-    stage_done(2);
-
-    // a5 + a6: exact counts of the trials whose upper bound can still win,
-    // best first: the trial with the highest key (U, then lowest index) is
-    // counted next, until no remaining key beats the lead.  C_h <= U_h, so a
-    // trial whose key (U_h, h) does not beat the lead cannot win with its
-    // exact count either, and the winner -- the highest exact count, the
-    // lowest index among equals -- is the one counting every trial would
-    // give.  Trials of earlier chunks have lower indices; the lead's key
-    // already ranks them.  A counted trial leaves the pool (U = -1).
-    for (;;) {
-      unsigned long long km = 0;
-      for (int hl = tid; hl < nh; hl += kThreads) {
-        const int u = S.U[hl];
-        if (u >= 0) km = max(km, best_key(u, hc0 + hl));
-      }
-      km = block_max_u64(km, cs.red_u);
-      if (km <= cs.best) break;  // also km == 0: no trial left
-      const int c = (int)(0xFFFFFFFFu - (uint32_t)(km & 0xFFFFFFFFull)) - hc0;
+    // a5 + a6 (used by the staged pass and by the best-first counts below):
+    // exact count of trial hc0 + c, which leaves the pool (U = -1) and
+    // becomes the lead if its key beats it
+    auto count_trial = [&](int c) {
       const float4 hy = S.hyp[c];
       const float htlo = S.tlo[c];
       int B = 0;
@@ -1029,6 +1067,88 @@ __device__ void process_cluster(const FrameDesc& a, const Smem& S, ClusterShared
         }
       }
       __syncthreads();
+    };
+
+    // a4: scoring pass (the hot loop)
+    bool staged = false;
+    if constexpr (SMEM_ROWS) staged = prune && pw == 1 && N >= RVH_STAGE_MIN_N;
+    if (!staged) {
+      phase_a_dispatch<DIM>(pw, hpl, rows, N, S, nh);
+      if (tid == 0) n_scored += (unsigned long long)nh * (unsigned long long)N;
+    } else if constexpr (SMEM_ROWS) {
+      // Staged, with exact pruning: the trials still in the list are scored
+      // kStageQuads quads at a time; after the first stage the trial with
+      // the highest partial count is counted exactly (it leads from then
+      // on), and after every stage a trial whose partial count plus the
+      // points still to come cannot beat the lead's key leaves the list
+      // (U = -1).  Each remaining point adds at most one to a count and
+      // C_h <= U_h, so a trial dropped this way cannot win: the winner is
+      // the one scoring every trial over every point gives, found by the
+      // best-first counts below among the trials that stayed.
+      const int nq = (N + 3) >> 2;
+      int A = compact_list(S, nh, false, [&](int h) { return S.kind[h] == kHypNormal; }, cs.red_i);
+      bool led = false;
+      unsigned long long scored = 0;
+      int sq = kStageQuads;
+      for (int q0 = 0; q0 < nq && A > 0;) {
+        int q1 = min(nq, q0 + sq);
+        if (nq - q1 < sq / 2) q1 = nq;  // no short last stage
+#if RVH_STAGE_GROWTH
+        sq = (sq * 3) >> 1;
+#endif
+        // (trial group, quad) units split evenly over the warps
+        const int span = q1 - q0, total = ((A + 127) >> 7) * span;
+        const int per = (total + kWarps - 1) / kWarps;
+        for (int u = (tid >> 5) * per, e = min(total, u + per); u < e;) {
+          const int g = u / span, qa = q0 + u % span, qb = min(q0 + span, qa + (e - u));
+          scored += (unsigned long long)score_segment<DIM>(rows, N, S, A, g, qa, qb);
+          u += qb - qa;
+        }
+        __syncthreads();
+        q0 = q1;
+        if (q0 >= nq) break;
+        const int rem = N - 4 * q0;
+        if (!led) {
+          led = true;
+          unsigned long long km = 0;
+          for (int i = tid; i < A; i += kThreads) {
+            const int h = S.list[i];
+            km = max(km, best_key(S.U[h], hc0 + h));
+          }
+          km = block_max_u64(km, cs.red_u);
+          const int c = (int)(0xFFFFFFFFu - (uint32_t)(km & 0xFFFFFFFFull)) - hc0;
+          if (km != 0ull && best_key(S.U[c] + rem, hc0 + c) > cs.best) count_trial(c);
+        }
+        const unsigned long long lead = cs.best;
+        A = compact_list(S, A, true, [&](int h) {
+              const int u = S.U[h];
+              const bool keep = u >= 0 && best_key(u + rem, hc0 + h) > lead;
+              if (!keep) S.U[h] = -1;
+              return keep;
+            }, cs.red_i);
+      }
+      if ((tid & 31) == 0) n_scored += scored;
+    }
+    __syncthreads();
+    stage_done(2);
+
+    // a5 + a6: exact counts of the trials whose upper bound can still win,
+    // best first: the trial with the highest key (U, then lowest index) is
+    // counted next, until no remaining key beats the lead.  C_h <= U_h, so a
+    // trial whose key (U_h, h) does not beat the lead cannot win with its
+    // exact count either, and the winner -- the highest exact count, the
+    // lowest index among equals -- is the one counting every trial would
+    // give.  Trials of earlier chunks have lower indices; the lead's key
+    // already ranks them.  A counted trial leaves the pool (U = -1).
+    for (;;) {
+      unsigned long long km = 0;
+      for (int hl = tid; hl < nh; hl += kThreads) {
+        const int u = S.U[hl];
+        if (u >= 0) km = max(km, best_key(u, hc0 + hl));
+      }
+      km = block_max_u64(km, cs.red_u);
+      if (km <= cs.best) break;  // also km == 0: no trial left
+      count_trial((int)(0xFFFFFFFFu - (uint32_t)(km & 0xFFFFFFFFull)) - hc0);
     }
     __syncthreads();
     stage_done(3);
@@ -1046,6 +1166,7 @@ __device__ void process_cluster(const FrameDesc& a, const Smem& S, ClusterShared
   }
 
   if (tid == 0) cs.ctr[0] += n_cand;
+  if (n_scored) atomicAdd(&cs.scored, n_scored);
   if constexpr (EXT) {
     if (tid == 0) {
       cs.runs[0] += (unsigned long long)trials_run;
@@ -1118,13 +1239,18 @@ __global__ void __launch_bounds__(kThreads, RVH_MIN_BLOCKS) fused_kernel(const _
   S.U = reinterpret_cast<int*>(p);
   p += (size_t)a.hchunk * sizeof(int);
   S.kind = reinterpret_cast<int8_t*>(p);
+  p += ((size_t)a.hchunk * sizeof(int8_t) + 15) & ~(size_t)15;
+  S.list = reinterpret_cast<uint16_t*>(p);
 
   if (threadIdx.x < 4) cs.ctr[threadIdx.x] = 0ull;
   if constexpr (EXT) {
     if (threadIdx.x < 2) cs.runs[threadIdx.x] = 0ull;
   }
   if (threadIdx.x < 6) cs.clk[threadIdx.x] = 0ull;
-  if (threadIdx.x == 0) fq_n = 0;
+  if (threadIdx.x == 0) {
+    fq_n = 0;
+    cs.scored = 0ull;
+  }
   // the queued clusters' solves and headings, one lane each
   auto flush = [&]() {
     const int n = fq_n;
@@ -1163,9 +1289,9 @@ __global__ void __launch_bounds__(kThreads, RVH_MIN_BLOCKS) fused_kernel(const _
     double4_32a* cta_pre =
         a.cta_rows64 ? a.cta_rows64 + (size_t)blockIdx.x * smem_row_capacity(2, a.nmax_smem) : nullptr;
     if (e - o <= (int64_t)smem_row_capacity(DIM, a.nmax_smem) || e < o) {
-      process_cluster<DIM, true, EXT>(F, S, cs, ci, a.hchunk, a.pw, a.hpl, fc.x, fq, &fq_n, cta_pre);
+      process_cluster<DIM, true, EXT>(F, S, cs, ci, a.hchunk, a.pw, a.hpl, a.prune, fc.x, fq, &fq_n, cta_pre);
     } else {
-      process_cluster<DIM, false, EXT>(F, S, cs, ci, a.hchunk, a.pw, a.hpl, fc.x, fq, &fq_n, cta_pre);
+      process_cluster<DIM, false, EXT>(F, S, cs, ci, a.hchunk, a.pw, a.hpl, a.prune, fc.x, fq, &fq_n, cta_pre);
     }
     __syncthreads();
     if (fq_n == kFinishBatch) flush();
@@ -1184,37 +1310,57 @@ __global__ void __launch_bounds__(kThreads, RVH_MIN_BLOCKS) fused_kernel(const _
     if (v) atomicAdd(&a.stats[threadIdx.x], v);
   }
   if (threadIdx.x < 6 && a.stats) atomicAdd(&a.stats[4 + threadIdx.x], cs.clk[threadIdx.x]);
+  if (threadIdx.x == 0 && a.stats) atomicAdd(&a.stats[12], cs.scored);
   if constexpr (EXT) {
     if (threadIdx.x < 2 && a.stats) atomicAdd(&a.stats[10 + threadIdx.x], cs.runs[threadIdx.x]);
   }
 }
 
-// Orders the batch's (frame, cluster) items by decreasing floor(log2(N * H))
-// (H: the trial_block of adaptive frames, which mostly stop after one block)
-// (longest-processing-time first) and resets the work counter.  One CTA.
+// Orders the batch's (frame, cluster) items by decreasing cost N * H (H: the
+// trial_block of adaptive frames, which mostly stop after one block),
+// longest-processing-time first, in buckets of an eighth of an octave (the
+// floor of log2 of the cost and its next three bits), and resets the work
+// counter.  One CTA.
+constexpr int kCostBuckets = 512;
 __device__ __forceinline__ int item_bucket(const FrameDesc& F, int ci) {
   const int64_t n = (int64_t)F.offsets[ci + 1] - F.offsets[ci];
   const int64_t cost = n > 0 ? n * (int64_t)(F.trial_block > 0 ? min(F.trial_block, F.H) : F.H) : 1;
-  return 63 - min(63 - __clzll(cost), 63);  // 0 = most expensive
+  const int lg = 63 - __clzll(cost);
+  const int sub = (int)((lg >= 3 ? cost >> (lg - 3) : cost << (3 - lg)) & 7);
+  return kCostBuckets - 1 - min((lg << 3) | sub, kCostBuckets - 1);  // 0 = most expensive
 }
 
 __global__ void worklist_kernel(FusedArgs a) {
-  __shared__ int hist[64];
-  if (threadIdx.x < 64) hist[threadIdx.x] = 0;
+  __shared__ int hist[kCostBuckets];
+  for (int b = threadIdx.x; b < kCostBuckets; b += blockDim.x) hist[b] = 0;
   __syncthreads();
   for (int f = 0; f < a.n_frames; ++f) {
     const FrameDesc& F = a.f[f];
     for (int i = threadIdx.x; i < F.n_clusters; i += blockDim.x) atomicAdd(&hist[item_bucket(F, i)], 1);
   }
   __syncthreads();
-  if (threadIdx.x == 0) {
-    int s = 0;
-    for (int b = 0; b < 64; ++b) {
-      const int c = hist[b];
-      hist[b] = s;
-      s += c;
+  if (threadIdx.x < 32) {  // exclusive scan of the histogram, 16 buckets per lane
+    constexpr int kPer = kCostBuckets / 32;
+    const int lane = threadIdx.x;
+    int c[kPer], sum = 0;
+#pragma unroll
+    for (int k = 0; k < kPer; ++k) {
+      c[k] = hist[lane * kPer + k];
+      sum += c[k];
     }
-    *a.work_counter = 0;
+    int incl = sum;
+#pragma unroll
+    for (int d = 1; d < 32; d <<= 1) {
+      const int t = __shfl_up_sync(0xffffffffu, incl, d);
+      if (lane >= d) incl += t;
+    }
+    int run = incl - sum;
+#pragma unroll
+    for (int k = 0; k < kPer; ++k) {
+      hist[lane * kPer + k] = run;
+      run += c[k];
+    }
+    if (lane == 0) *a.work_counter = 0;
   }
   __syncthreads();
   for (int f = 0; f < a.n_frames; ++f) {
@@ -1226,7 +1372,8 @@ __global__ void worklist_kernel(FusedArgs a) {
 
 size_t fused_smem_bytes(int nmax_smem, int hchunk) {
   // the trial area also holds the final reduction (up to 9 sums per thread)
-  const size_t trials = (size_t)hchunk * (sizeof(float4) + sizeof(float) + sizeof(int) + 1);
+  const size_t trials = (size_t)hchunk * (sizeof(float4) + sizeof(float) + sizeof(int) + sizeof(uint16_t)) +
+                        (((size_t)hchunk + 15) & ~(size_t)15);
   const size_t reduction = (size_t)9 * kThreads * sizeof(double);
   return (size_t)((nmax_smem + 31) & ~31) * sizeof(float4) + (trials > reduction ? trials : reduction);
 }

@@ -51,6 +51,7 @@ struct FrameDesc {
 };
 
 constexpr int kMaxBatchFrames = 32;
+constexpr int kStatsWords = 13;
 
 // A batch of frames of one model dimension, processed by one persistent launch.
 struct FusedArgs {
@@ -59,12 +60,14 @@ struct FusedArgs {
   int n_items;               // sum of n_clusters over the frames
   int2* worklist;            // [n_items] (frame, cluster), written by the worklist kernel
   int* work_counter;
-  unsigned long long* stats;  // [4 + 6 + 2]: exact counts, band points, fp64 trials, refined trials,
-                              // stage cycles, trials run, pairs scored
+  unsigned long long* stats;  // [kStatsWords]: exact counts, band points, fp64 trials, refined trials,
+                              // 6 stage cycles, trials run, pairs of the trials run (extensions),
+                              // pairs the scoring pass evaluated
   int nmax_smem;
   int hchunk;
   int pw, hpl;
   int direct;                // 1: one item per CTA, item = blockIdx.x (no work list)
+  int prune;                 // 1: staged scoring pass with exact pruning of trials that cannot win
   // [grid * smem_row_capacity(2, nmax_smem)] FP64 rows, one slot per CTA,
   // used for clusters whose rows fit shared memory (a working set that
   // stays in L2); NULL: every cluster uses its frame's per-point rows64_g

@@ -126,6 +126,7 @@ extern "C" int rvh_estimate_noalloc(const rvh_frame* f, const rvh_params* p, rvh
   a.worklist = (int2*)d->scratch;
   a.work_counter = (int*)(d->scratch + kWorklistBytes);  // zeroed by the worklist kernel each call
   a.stats = nullptr;
+  a.prune = 1;
   a.nmax_smem = kNmaxSmem;
   a.hchunk = kHchunk;
   // the scoring schedule follows the trials scored together (the adaptive block, or all)

@@ -26,6 +26,7 @@ struct Smem {
   float* tlo;         // [hchunk]
   int* U;             // [hchunk] upper bounds of the exact counts (-1 = rejected)
   int8_t* kind;       // [hchunk]
+  uint16_t* list;     // [hchunk] trials still scored by the staged pass
 };
 
 // ---- FP32 rows of the cluster being processed ---------------------------------------
@@ -105,21 +106,81 @@ __device__ __forceinline__ float neg_count_bound(float thi) {
   return -__uint_as_float(__float_as_uint(__fmul_ru(thi, thi)) + 1u);
 }
 
-// a4 over tiled rows: the residuals of two points per instruction.  Lane l
+// HPL trial records of one lane in packed registers: (-X, -X), (-Y, -Y),
+// (-Z, -Z), (-C, -C) and the sign-mask accumulator of each.
+template <int HPL>
+struct LaneTrials {
+  unsigned long long nx[HPL], ny[HPL], nz[HPL], nc[HPL];
+  uint32_t acc[HPL];
+  // record (-X, -Y, -Z, thi) into slot m; a NaN thi never counts
+  __device__ __forceinline__ void load(int m, float4 v) {
+    nx[m] = pack2(v.x, v.x);
+    ny[m] = pack2(v.y, v.y);
+    nz[m] = pack2(v.z, v.z);
+    const float c = neg_count_bound(v.w);
+    nc[m] = pack2(c, c);
+    acc[m] = 0u;
+  }
+};
+
+// Scores points 4q .. 4q + 3 against the lane's trials: the residuals of two
+// points per instruction, per element resid_f32's arithmetic (w + nz z +
+// ny y + nx x by fmaf); the test e = r r - C (one packed FMA for two points,
+// exact until its final rounding, which keeps the sign): e < 0 exactly when
+// r^2 < C, and C exceeds thi^2 (neg_count_bound), so a count is an upper
+// bound of #{|r32| <= thi} that exceeds it only by points within two ulps
+// of thi^2.  NaN residuals (NaN Dopplers, the padding) give the canonical
+// NaN, whose sign bit is clear, so they do not count (a NaN that did would
+// only loosen the bound).  The count leaves the FP32 pipe: two byte permutes
+// turn the four sign bits into 16-bit masks and one three-input integer add
+// accumulates them (sign_pair / sign_count: the even and the odd points of a
+// lane stay below 2^16 each, since a cluster in shared memory has at most
+// 227 KB / 12 B points).
+template <int DIM, int HPL>
+__device__ __forceinline__ void score_quad(const TileRowsOf<DIM>& rows, int q, LaneTrials<HPL>& T) {
+  const float4 c = rows.quad(q, 0), sn = rows.quad(q, 1), w = rows.quad(q, DIM == 2 ? 2 : 3);
+  const unsigned long long c01 = pack2(c.x, c.y), c23 = pack2(c.z, c.w);
+  const unsigned long long s01 = pack2(sn.x, sn.y), s23 = pack2(sn.z, sn.w);
+  const unsigned long long w01 = pack2(w.x, w.y), w23 = pack2(w.z, w.w);
+  unsigned long long z01 = 0ull, z23 = 0ull;
+  if (DIM == 3) {
+    const float4 z = rows.quad(q, 2);
+    z01 = pack2(z.x, z.y);
+    z23 = pack2(z.z, z.w);
+  }
+#pragma unroll
+  for (int m = 0; m < HPL; ++m) {
+    unsigned long long r01, r23;
+    if (DIM == 2) {
+      r01 = fma2(T.nx[m], c01, fma2(T.ny[m], s01, w01));
+      r23 = fma2(T.nx[m], c23, fma2(T.ny[m], s23, w23));
+    } else {
+      r01 = fma2(T.nx[m], c01, fma2(T.ny[m], s01, fma2(T.nz[m], z01, w01)));
+      r23 = fma2(T.nx[m], c23, fma2(T.ny[m], s23, fma2(T.nz[m], z23, w23)));
+    }
+    float e0, e1, e2, e3;
+    unpack2(fma2(r01, r01, T.nc[m]), e0, e1);
+    unpack2(fma2(r23, r23, T.nc[m]), e2, e3);
+    T.acc[m] += sign_pair(e0, e1) + sign_pair(e2, e3);
+  }
+}
+
+// Quads q0, q0 + step, ... below q1, unrolled by the measured factor.
+template <int DIM, int HPL>
+__device__ __forceinline__ void score_quads(const TileRowsOf<DIM>& rows, int q0, int q1, int step,
+                                            LaneTrials<HPL>& T) {
+  constexpr int UN = DIM == 2 ? 8 : 4;  // quads per loop iteration (measured)
+  int q = q0;
+  for (; q + (UN - 1) * step < q1; q += UN * step) {
+#pragma unroll
+    for (int u = 0; u < UN; ++u) score_quad<DIM, HPL>(rows, q + u * step, T);
+  }
+  for (; q < q1; q += step) score_quad<DIM, HPL>(rows, q, T);
+}
+
+// a4 over tiled rows, every trial of the chunk over every point.  Lane l
 // handles trial sub-group l / PW and point quads l % PW, l % PW + PW, ...;
 // the rows stage pads the last quad with NaN Dopplers, which never count.
-// Per element the arithmetic is resid_f32's: w + nz z + ny y + nx x by fmaf.
-// The test is e = r r - C (one packed FMA for two points, exact until its
-// final rounding, which keeps the sign): e < 0 exactly when r^2 < C, and C
-// exceeds thi^2 (neg_count_bound), so the count U_h is an upper bound of
-// #{|r32| <= thi} that exceeds it only by points within two ulps of thi^2.
-// NaN residuals (NaN Dopplers, the padding) give the canonical NaN, whose
-// sign bit is clear, so they do not count (a NaN that did would only loosen
-// the bound).  The count leaves the FP32 pipe: per quad and trial two byte
-// permutes turn the four sign bits into 16-bit masks and one three-input
-// integer add accumulates them (sign_pair / sign_count: even and odd points
-// of a lane stay below 2^16 each, since a cluster in shared memory has at
-// most 227 KB / 16 B points).
 template <int DIM, int PW, int HPL>
 __device__ __forceinline__ void phase_a_tiles(const TileRowsOf<DIM> rows, int N, const Smem& S, int nh) {
   constexpr int NHL = 32 / PW;
@@ -130,57 +191,17 @@ __device__ __forceinline__ void phase_a_tiles(const TileRowsOf<DIM> rows, int N,
   const int nq = (N + 3) >> 2;
   for (int g = warp; g < ngroups; g += kWarps) {
     const int base = g * G + hl * HPL;
-    unsigned long long nx[HPL], ny[HPL], nz[HPL], nc[HPL];
-    uint32_t acc[HPL];
+    LaneTrials<HPL> T;
 #pragma unroll
     for (int m = 0; m < HPL; ++m) {
       const int h = base + m;
-      const float4 v = (h < nh) ? S.hyp[h] : make_float4(0.f, 0.f, 0.f, __int_as_float(0x7fc00000));
-      nx[m] = pack2(v.x, v.x);
-      ny[m] = pack2(v.y, v.y);
-      nz[m] = pack2(v.z, v.z);
-      const float c = neg_count_bound(v.w);
-      nc[m] = pack2(c, c);
-      acc[m] = 0u;
+      T.load(m, (h < nh) ? S.hyp[h] : make_float4(0.f, 0.f, 0.f, __int_as_float(0x7fc00000)));
     }
-    auto quad = [&](int q) {
-      const float4 c = rows.quad(q, 0), sn = rows.quad(q, 1), w = rows.quad(q, DIM == 2 ? 2 : 3);
-      const unsigned long long c01 = pack2(c.x, c.y), c23 = pack2(c.z, c.w);
-      const unsigned long long s01 = pack2(sn.x, sn.y), s23 = pack2(sn.z, sn.w);
-      const unsigned long long w01 = pack2(w.x, w.y), w23 = pack2(w.z, w.w);
-      unsigned long long z01 = 0ull, z23 = 0ull;
-      if (DIM == 3) {
-        const float4 z = rows.quad(q, 2);
-        z01 = pack2(z.x, z.y);
-        z23 = pack2(z.z, z.w);
-      }
-#pragma unroll
-      for (int m = 0; m < HPL; ++m) {
-        unsigned long long r01, r23;
-        if (DIM == 2) {
-          r01 = fma2(nx[m], c01, fma2(ny[m], s01, w01));
-          r23 = fma2(nx[m], c23, fma2(ny[m], s23, w23));
-        } else {
-          r01 = fma2(nx[m], c01, fma2(ny[m], s01, fma2(nz[m], z01, w01)));
-          r23 = fma2(nx[m], c23, fma2(ny[m], s23, fma2(nz[m], z23, w23)));
-        }
-        float e0, e1, e2, e3;
-        unpack2(fma2(r01, r01, nc[m]), e0, e1);
-        unpack2(fma2(r23, r23, nc[m]), e2, e3);
-        acc[m] += sign_pair(e0, e1) + sign_pair(e2, e3);
-      }
-    };
-    constexpr int UN = DIM == 2 ? 8 : 4;  // quads per loop iteration (measured)
-    int q = pl;
-    for (; q + (UN - 1) * PW < nq; q += UN * PW) {
-#pragma unroll
-      for (int u = 0; u < UN; ++u) quad(q + u * PW);
-    }
-    for (; q < nq; q += PW) quad(q);
+    score_quads<DIM, HPL>(rows, pl, nq, PW, T);
     int cnt[HPL];
 #pragma unroll
     for (int m = 0; m < HPL; ++m) {
-      cnt[m] = sign_count(acc[m]);
+      cnt[m] = sign_count(T.acc[m]);
 #pragma unroll
       for (int o = PW / 2; o > 0; o >>= 1) cnt[m] += __shfl_xor_sync(0xffffffffu, cnt[m], o);
     }
@@ -192,6 +213,31 @@ __device__ __forceinline__ void phase_a_tiles(const TileRowsOf<DIM> rows, int N,
       }
     }
   }
+}
+
+__device__ __forceinline__ int list_trial(const Smem& S, int A, int i) { return i < A ? (int)S.list[i] : -1; }
+
+// One piece of the staged scoring pass: the 128 trials of group g of the
+// list S.list[0 .. A) (four per lane, lane-major) over quads [qa, qb),
+// their counts added to S.U (several warps may share a group, each over
+// its own quads).  Returns the (trial, point) pairs this warp scored.
+template <int DIM>
+__device__ __forceinline__ long long score_segment(const TileRowsOf<DIM> rows, int N, const Smem& S, int A, int g,
+                                                   int qa, int qb) {
+  const int lane = threadIdx.x & 31;
+  LaneTrials<4> T;
+  int hs[4];
+#pragma unroll
+  for (int m = 0; m < 4; ++m) {
+    hs[m] = list_trial(S, A, g * 128 + lane * 4 + m);
+    T.load(m, hs[m] >= 0 ? S.hyp[hs[m]] : make_float4(0.f, 0.f, 0.f, __int_as_float(0x7fc00000)));
+  }
+  score_quads<DIM, 4>(rows, qa, qb, 1, T);
+#pragma unroll
+  for (int m = 0; m < 4; ++m)
+    if (hs[m] >= 0) atomicAdd(&S.U[hs[m]], sign_count(T.acc[m]));
+  const int trials = min(128, A - g * 128);
+  return (long long)trials * (min(4 * qb, N) - 4 * qa);
 }
 
 }  // namespace rvh

@@ -65,7 +65,8 @@ class rvh_stats(ctypes.Structure):
                 ("hyps_per_lane", ctypes.c_int32), ("phase_cycles", ctypes.c_int64 * 6),
                 ("refined_hypotheses", ctypes.c_int64), ("graph_replays", ctypes.c_int64),
                 ("kernel_launches", ctypes.c_int32), ("graph_builds", ctypes.c_int64),
-                ("serving_steps", ctypes.c_int64), ("serving_graph_replays", ctypes.c_int64)]
+                ("serving_steps", ctypes.c_int64), ("serving_graph_replays", ctypes.c_int64),
+                ("pairs_scored", ctypes.c_int64)]
 
 
 # exported symbols and their ctypes signatures (restype, argtypes)
@@ -86,6 +87,7 @@ SIGNATURES = {
     "rvh_last_error": (ctypes.c_char_p, [_P]),
     "rvh_get_stats": (ctypes.c_int, [_P, ctypes.POINTER(rvh_stats)]),
     "rvh_set_schedule": (ctypes.c_int, [_P, ctypes.c_int32, ctypes.c_int32]),
+    "rvh_set_pruning": (ctypes.c_int, [_P, ctypes.c_int32]),
     "rvh_autotune": (ctypes.c_int, [_P, ctypes.POINTER(rvh_frame), ctypes.POINTER(rvh_params),
                                     ctypes.POINTER(rvh_result), ctypes.c_int32, ctypes.POINTER(rvh_schedule)]),
     "rvh_cluster": (ctypes.c_int, [_P, _P, ctypes.c_int64, ctypes.c_int32, ctypes.c_double, ctypes.c_int32,
@@ -159,6 +161,10 @@ def rvh_get_stats(ctx, out) -> int:
 
 def rvh_set_schedule(ctx, points_per_warp: int, hyps_per_lane: int) -> int:
     return load().rvh_set_schedule(ctx, points_per_warp, hyps_per_lane)
+
+
+def rvh_set_pruning(ctx, enabled: int) -> int:
+    return load().rvh_set_pruning(ctx, enabled)
 
 
 def rvh_autotune(ctx, frame, params, result, reps: int, best) -> int:

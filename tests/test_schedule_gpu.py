@@ -221,3 +221,48 @@ def test_cta_row_slots_equal_per_point_rows(torch, monkeypatch):
         for key in results[("1", k)]:
             assert np.array_equal(results[("1", k)][key], results[("0", k)][key], equal_nan=True), (k, key)
 
+
+
+@pytest.mark.parametrize("case", ["dense2d", "stress2d", "dense3d", "adaptive", "local_opt", "paper_line"])
+def test_pruning_same_result(torch, case):
+    """The staged scoring pass with exact pruning (the default) and the plain
+    pass give identical outputs -- masks, counts, winners, status,
+    velocities and headings bit for bit -- while the pruned one evaluates
+    fewer (trial, point) pairs.  Sizes 2..2600 include clusters below the
+    staging threshold (256 points), ragged quads and clusters beyond the
+    shared-memory capacity (never staged); 3D runs two chunks of trials."""
+    ext = {"adaptive": {"confidence": 0.99, "trial_block": 128}, "local_opt": {"refine_iterations": 2},
+           "paper_line": {"hypothesis_model": rvh.RVH_MODEL_PAPER_LINE}}.get(case, {})
+    w = synth.WORKLOADS[case if case in ("dense2d", "stress2d", "dense3d") else "dense2d"]
+    rng = np.random.default_rng(5)
+    sizes = np.concatenate([[2, 3, 255, 256, 257, 383, 1000, 1535, 1536, 2047, 2048, 2049, 2600],
+                            rng.integers(200, 2048, 180)]).astype(np.int64)
+    f = synth.make_frame(w, sizes=sizes, gen_seed=81)
+    keep, frame = _device_frame(torch, f)
+    H = 2048 if w.model_dim == 3 else 1024
+    params = rvh.make_params(w.model_dim, H, w.tau, 13, **ext)
+    dev = torch.device("cuda", 0)
+    ctx = rvh.Context(0)
+    out, scored = {}, {}
+    try:
+        for on in (1, 0):
+            ctx.check(rvh.rvh_set_pruning(ctx.handle, on), "pruning")
+            outs = rvh.alloc_outputs(f.n_clusters, f.n_points, dev, threshold=True)
+            ctx.check(rvh.rvh_estimate(ctx.handle, frame, params, rvh.make_result(outs), None), "estimate")
+            torch.cuda.synchronize()
+            out[on] = _np(outs, f.n_points)
+            st = rvh.rvh_stats()
+            ctx.check(rvh.rvh_get_stats(ctx.handle, st), "stats")
+            scored[on] = st.pairs_scored
+        assert rvh.rvh_set_pruning(ctx.handle, 2) == rvh.RVH_EINVAL
+    finally:
+        ctx.close()
+    for k in out[1]:
+        assert np.array_equal(out[1][k], out[0][k], equal_nan=True), k
+    # the adaptive count scores blocks of 128 trials, under the lanes-over-points
+    # schedule, which the staged pass does not take
+    assert 0 < scored[1] <= scored[0] if case == "adaptive" else 0 < scored[1] < scored[0], scored
+    if not ext:
+        n = np.diff(f.offsets)
+        assert scored[0] == int(n[n >= w.model_dim].sum()) * H, scored
+        print(f"pruning {case}: {scored[1] / scored[0]:.3f} of the pairs scored")
