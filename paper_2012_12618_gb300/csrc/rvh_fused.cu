@@ -824,14 +824,12 @@ __device__ __forceinline__ int compact_list(const Smem& S, int n, bool from_list
   return out;
 }
 
-// Quads (4 points) per stage of the staged scoring pass.
+// Staged scoring pass: the first stage covers kStageQuads quads (4 points
+// each), every later one half as many again as the one before; clusters
+// of fewer than kStageMinPoints points are scored in one pass (measured:
+// below that the stages cost more than pruning saves).
 constexpr int kStageQuads = 32;
-#ifndef RVH_STAGE_MIN_N
-#define RVH_STAGE_MIN_N 512
-#endif
-#ifndef RVH_STAGE_GROWTH
-#define RVH_STAGE_GROWTH 1
-#endif
+constexpr int kStageMinPoints = 512;
 
 // a2 + a3 for trials hc0 .. hc0 + nh - 1 of cluster ci under the cosine
 // model: draw, FP32 solve (refined when ill-conditioned), bound, records
@@ -1071,7 +1069,7 @@ __device__ void process_cluster(const FrameDesc& a, const Smem& S, ClusterShared
 
     // a4: scoring pass (the hot loop)
     bool staged = false;
-    if constexpr (SMEM_ROWS) staged = prune && pw == 1 && N >= RVH_STAGE_MIN_N;
+    if constexpr (SMEM_ROWS) staged = prune && pw == 1 && N >= kStageMinPoints;
     if (!staged) {
       phase_a_dispatch<DIM>(pw, hpl, rows, N, S, nh);
       if (tid == 0) n_scored += (unsigned long long)nh * (unsigned long long)N;
@@ -1093,9 +1091,7 @@ __device__ void process_cluster(const FrameDesc& a, const Smem& S, ClusterShared
       for (int q0 = 0; q0 < nq && A > 0;) {
         int q1 = min(nq, q0 + sq);
         if (nq - q1 < sq / 2) q1 = nq;  // no short last stage
-#if RVH_STAGE_GROWTH
         sq = (sq * 3) >> 1;
-#endif
         // (trial group, quad) units split evenly over the warps
         const int span = q1 - q0, total = ((A + 127) >> 7) * span;
         const int per = (total + kWarps - 1) / kWarps;
