@@ -600,7 +600,7 @@ struct Staged {
   unsigned long long* stats;
   void* rows;               // float4[n_points] (fused) or double[4 n_points] (baseline)
   double4_32a* rows64;      // double4_32a[n_points] (fused)
-  double4_32a* cta_rows64;  // double4_32a[resident CTAs * smem_row_capacity(2, nmax_smem)] (fused)
+  double4_32a* cta_rows64;  // double4_32a[resident CTAs * max over dims of cta_slot_stride] (fused)
 };
 
 static int stage(rvh_ctx* ctx, const rvh_frame* f, const rvh_params* p, rvh_result* r, cudaStream_t s,
@@ -652,7 +652,8 @@ static int stage(rvh_ctx* ctx, const rvh_frame* f, const rvh_params* p, rvh_resu
   if (fused) {
     const int rc = configure_dim(ctx, p->model_dim);
     if (rc) return rc;
-    o_cta64 = take(sizeof(double4_32a) * (size_t)rvh::smem_row_capacity(2, ctx->nmax_smem) *
+    o_cta64 = take(sizeof(double4_32a) *
+                   (size_t)std::max(rvh::cta_slot_stride(2, ctx->nmax_smem), rvh::cta_slot_stride(3, ctx->nmax_smem)) *
                    (size_t)(ctx->sms * ctx->occ[p->model_dim]));
   }
   const size_t o_az = d_az ? 0 : take(4 * (size_t)np);

@@ -1283,7 +1283,7 @@ __global__ void __launch_bounds__(kThreads, RVH_MIN_BLOCKS) fused_kernel(const _
     const int ci = fc.y;
     const int64_t o = F.offsets[ci], e = F.offsets[ci + 1];
     double4_32a* cta_pre =
-        a.cta_rows64 ? a.cta_rows64 + (size_t)blockIdx.x * smem_row_capacity(2, a.nmax_smem) : nullptr;
+        a.cta_rows64 ? a.cta_rows64 + (size_t)blockIdx.x * cta_slot_stride(DIM, a.nmax_smem) : nullptr;
     if (e - o <= (int64_t)smem_row_capacity(DIM, a.nmax_smem) || e < o) {
       process_cluster<DIM, true, EXT>(F, S, cs, ci, a.hchunk, a.pw, a.hpl, a.prune, fc.x, fq, &fq_n, cta_pre);
     } else {

@@ -68,7 +68,7 @@ struct FusedArgs {
   int pw, hpl;
   int direct;                // 1: one item per CTA, item = blockIdx.x (no work list)
   int prune;                 // 1: staged scoring pass with exact pruning of trials that cannot win
-  // [grid * smem_row_capacity(2, nmax_smem)] FP64 rows, one slot per CTA,
+  // [grid * cta_slot_stride(dim, nmax_smem)] FP64 rows, one slot per CTA,
   // used for clusters whose rows fit shared memory (a working set that
   // stays in L2); NULL: every cluster uses its frame's per-point rows64_g
   double4_32a* cta_rows64;
@@ -80,6 +80,13 @@ struct FusedArgs {
 // The CTAs' FP64 row slots hold the 2D capacity, the larger one.
 __host__ __device__ inline int smem_row_capacity(int dim, int nmax_smem) {
   return dim == 2 ? ((((nmax_smem + 31) & ~31) * 4 / 3) & ~31) : nmax_smem;
+}
+// Entries between consecutive CTAs' FP64 row slots for the model dimension
+// dim: its shared-memory capacity, padded in 2D, whose capacity is a power of
+// two (2048 entries, 64 KB) -- slots at power-of-two strides fall on the
+// same L2 sets and were written back; the API allocates the larger stride.
+__host__ __device__ inline int cta_slot_stride(int dim, int nmax_smem) {
+  return dim == 2 ? smem_row_capacity(2, nmax_smem) + 64 : nmax_smem;
 }
 
 size_t fused_smem_bytes(int nmax_smem, int hchunk);
