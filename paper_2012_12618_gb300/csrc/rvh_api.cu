@@ -342,8 +342,9 @@ int launch_graph(rvh_ctx* ctx, FusedArgs& a, int dim, cudaStream_t s) {
   size_t smem = 0;
   int rc = prepare_launch(ctx, a, dim, &grid, &smem);
   if (rc) return rc;
-  RVH_CUDA(cudaMemsetAsync(a.stats, 0, sizeof(unsigned long long) * kStatsWords, s));
-  if (!a.direct) RVH_CUDA(launch_worklist(a, s));
+  // the work-list kernel zeroes the stats; a direct launch has none before it
+  if (a.direct) RVH_CUDA(cudaMemsetAsync(a.stats, 0, sizeof(unsigned long long) * kStatsWords, s));
+  else RVH_CUDA(launch_worklist(a, s));
   RVH_CUDA(cudaEventRecord(ctx->ev0, s));
   const cudaError_t e = ctx->graph[dim == 3][fused_ext(a) ? 1 : 0].launch(a, dim, grid, smem, false, s);
   if (e != cudaSuccess) {

@@ -1326,13 +1326,24 @@ __device__ __forceinline__ int item_bucket(const FrameDesc& F, int ci) {
   return kCostBuckets - 1 - min((lg << 3) | sub, kCostBuckets - 1);  // 0 = most expensive
 }
 
-__global__ void worklist_kernel(FusedArgs a) {
+// Items are numbered frame-major; each thread keeps the buckets of its first
+// kItemsKept items in registers between the two passes.  Also zeroes the
+// launch's stats counters (the fused kernel adds to them).
+constexpr int kItemsKept = 8;
+__global__ void worklist_kernel(const __grid_constant__ FusedArgs a) {
   __shared__ int hist[kCostBuckets];
   for (int b = threadIdx.x; b < kCostBuckets; b += blockDim.x) hist[b] = 0;
+  if (a.stats && threadIdx.x < kStatsWords) a.stats[threadIdx.x] = 0ull;
   __syncthreads();
-  for (int f = 0; f < a.n_frames; ++f) {
-    const FrameDesc& F = a.f[f];
-    for (int i = threadIdx.x; i < F.n_clusters; i += blockDim.x) atomicAdd(&hist[item_bucket(F, i)], 1);
+  int kept[kItemsKept];
+  {
+    int f = 0, base = 0, k = 0;
+    for (int it = threadIdx.x; it < a.n_items; it += blockDim.x, ++k) {
+      while (it - base >= a.f[f].n_clusters) base += a.f[f++].n_clusters;
+      const int b = item_bucket(a.f[f], it - base);
+      if (k < kItemsKept) kept[k] = b;
+      atomicAdd(&hist[b], 1);
+    }
   }
   __syncthreads();
   if (threadIdx.x < 32) {  // exclusive scan of the histogram, 16 buckets per lane
@@ -1359,10 +1370,13 @@ __global__ void worklist_kernel(FusedArgs a) {
     if (lane == 0) *a.work_counter = 0;
   }
   __syncthreads();
-  for (int f = 0; f < a.n_frames; ++f) {
-    const FrameDesc& F = a.f[f];
-    for (int i = threadIdx.x; i < F.n_clusters; i += blockDim.x)
-      a.worklist[atomicAdd(&hist[item_bucket(F, i)], 1)] = make_int2(f, i);
+  {
+    int f = 0, base = 0, k = 0;
+    for (int it = threadIdx.x; it < a.n_items; it += blockDim.x, ++k) {
+      while (it - base >= a.f[f].n_clusters) base += a.f[f++].n_clusters;
+      const int b = k < kItemsKept ? kept[k] : item_bucket(a.f[f], it - base);
+      a.worklist[atomicAdd(&hist[b], 1)] = make_int2(f, it - base);
+    }
   }
 }
 
