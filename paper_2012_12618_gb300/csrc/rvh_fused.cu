@@ -795,7 +795,7 @@ __device__ __forceinline__ int compact_list(const Smem& S, int n, bool from_list
       int h = -1;
       if (i < n) {
         h = from_list ? (int)S.list[i] : i;
-        if (!keep(h)) h = -1;
+        if (h == (int)kDropped || !keep(h)) h = -1;
       }
       hv[k] = h;
       c += h >= 0 ? 1 : 0;
@@ -822,6 +822,49 @@ __device__ __forceinline__ int compact_list(const Smem& S, int n, bool from_list
     __syncthreads();
   }
   return out;
+}
+
+// Drops the entries of S.list[0 .. n) (n <= 4 kThreads) for which keep(h)
+// fails: marked kDropped in place, and the list compacted (in order) only
+// when its groups of 128 would be fewer.  Returns the new list length
+// (marked entries included when it was not compacted).  red: kWarps ints.
+template <typename Keep>
+__device__ __forceinline__ int prune_list(const Smem& S, int n, Keep keep, int* red) {
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+  int hv[4], c = 0;
+#pragma unroll
+  for (int k = 0; k < 4; ++k) {
+    const int i = 4 * tid + k;
+    int h = i < n ? (int)S.list[i] : (int)kDropped;
+    if (h != (int)kDropped && !keep(h)) {
+      S.list[i] = kDropped;
+      h = (int)kDropped;
+    }
+    hv[k] = h;
+    c += h != (int)kDropped ? 1 : 0;
+  }
+  int incl = c;
+#pragma unroll
+  for (int d = 1; d < 32; d <<= 1) {
+    const int t = __shfl_up_sync(0xffffffffu, incl, d);
+    if (lane >= d) incl += t;
+  }
+  if (lane == 31) red[warp] = incl;
+  __syncthreads();
+  int pos = incl - c, tot = 0;
+#pragma unroll
+  for (int w = 0; w < kWarps; ++w) {
+    const int v = red[w];
+    tot += v;
+    pos += w < warp ? v : 0;
+  }
+  if (((tot + 127) >> 7) == ((n + 127) >> 7)) return n;  // as many groups: keep the marks
+  // every entry was read before the barrier above: compact in place
+#pragma unroll
+  for (int k = 0; k < 4; ++k)
+    if (hv[k] != (int)kDropped) S.list[pos++] = (uint16_t)hv[k];
+  __syncthreads();
+  return tot;
 }
 
 // Staged scoring pass: the first stage covers kStageQuads quads (4 points
@@ -1109,19 +1152,20 @@ __device__ void process_cluster(const FrameDesc& a, const Smem& S, ClusterShared
           unsigned long long km = 0;
           for (int i = tid; i < A; i += kThreads) {
             const int h = S.list[i];
-            km = max(km, best_key(S.U[h], hc0 + h));
+            if (h != (int)kDropped) km = max(km, best_key(S.U[h], hc0 + h));
           }
           km = block_max_u64(km, cs.red_u);
           const int c = (int)(0xFFFFFFFFu - (uint32_t)(km & 0xFFFFFFFFull)) - hc0;
           if (km != 0ull && best_key(S.U[c] + rem, hc0 + c) > cs.best) count_trial(c);
         }
         const unsigned long long lead = cs.best;
-        A = compact_list(S, A, true, [&](int h) {
-              const int u = S.U[h];
-              const bool keep = u >= 0 && best_key(u + rem, hc0 + h) > lead;
-              if (!keep) S.U[h] = -1;
-              return keep;
-            }, cs.red_i);
+        auto alive = [&](int h) {
+          const int u = S.U[h];
+          const bool keep = u >= 0 && best_key(u + rem, hc0 + h) > lead;
+          if (!keep) S.U[h] = -1;
+          return keep;
+        };
+        A = A <= 4 * kThreads ? prune_list(S, A, alive, cs.red_i) : compact_list(S, A, true, alive, cs.red_i);
       }
       if ((tid & 31) == 0) n_scored += scored;
     }

@@ -215,7 +215,13 @@ __device__ __forceinline__ void phase_a_tiles(const TileRowsOf<DIM> rows, int N,
   }
 }
 
-__device__ __forceinline__ int list_trial(const Smem& S, int A, int i) { return i < A ? (int)S.list[i] : -1; }
+// A list entry of a trial dropped in place (the list is compacted only when
+// that saves a group of 128).
+constexpr uint16_t kDropped = 0xFFFF;
+__device__ __forceinline__ int list_trial(const Smem& S, int A, int i) {
+  const int e = i < A ? (int)S.list[i] : (int)kDropped;
+  return e == (int)kDropped ? -1 : e;
+}
 
 // One piece of the staged scoring pass: the 128 trials of group g of the
 // list S.list[0 .. A) (four per lane, lane-major) over quads [qa, qb),
@@ -233,10 +239,12 @@ __device__ __forceinline__ long long score_segment(const TileRowsOf<DIM> rows, i
     T.load(m, hs[m] >= 0 ? S.hyp[hs[m]] : make_float4(0.f, 0.f, 0.f, __int_as_float(0x7fc00000)));
   }
   score_quads<DIM, 4>(rows, qa, qb, 1, T);
+  int trials = 0;
 #pragma unroll
-  for (int m = 0; m < 4; ++m)
+  for (int m = 0; m < 4; ++m) {
     if (hs[m] >= 0) atomicAdd(&S.U[hs[m]], sign_count(T.acc[m]));
-  const int trials = min(128, A - g * 128);
+    trials += __popc(__ballot_sync(0xffffffffu, hs[m] >= 0));
+  }
   return (long long)trials * (min(4 * qb, N) - 4 * qa);
 }
 
