@@ -40,6 +40,7 @@ def test_null_context_is_rejected():
     assert "ctx" in rvh.rvh_last_error(None)
     assert rvh.rvh_poll(None, 1) == rvh.RVH_EINVAL
     assert rvh.rvh_set_schedule(None, 1, 4) == rvh.RVH_EINVAL
+    assert rvh.rvh_set_pruning(None, 1) == rvh.RVH_EINVAL
 
 
 def test_create_without_gpu_reports_cuda_error():
