@@ -228,14 +228,14 @@ def test_pruning_same_result(torch, case):
     """The staged scoring pass with exact pruning (the default) and the plain
     pass give identical outputs -- masks, counts, winners, status,
     velocities and headings bit for bit -- while the pruned one evaluates
-    fewer (trial, point) pairs.  Sizes 2..2600 include clusters below the
-    staging threshold (256 points), ragged quads and clusters beyond the
+    fewer (trial, point) pairs.  Sizes 2..2600 include clusters around the
+    staging threshold (512 points), ragged quads and clusters beyond the
     shared-memory capacity (never staged); 3D runs two chunks of trials."""
     ext = {"adaptive": {"confidence": 0.99, "trial_block": 128}, "local_opt": {"refine_iterations": 2},
            "paper_line": {"hypothesis_model": rvh.RVH_MODEL_PAPER_LINE}}.get(case, {})
     w = synth.WORKLOADS[case if case in ("dense2d", "stress2d", "dense3d") else "dense2d"]
     rng = np.random.default_rng(5)
-    sizes = np.concatenate([[2, 3, 255, 256, 257, 383, 1000, 1535, 1536, 2047, 2048, 2049, 2600],
+    sizes = np.concatenate([[2, 3, 255, 256, 257, 383, 511, 512, 513, 1000, 1535, 1536, 2047, 2048, 2049, 2600],
                             rng.integers(200, 2048, 180)]).astype(np.int64)
     f = synth.make_frame(w, sizes=sizes, gen_seed=81)
     keep, frame = _device_frame(torch, f)
