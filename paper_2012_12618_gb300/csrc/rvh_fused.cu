@@ -1118,11 +1118,12 @@ __device__ void process_cluster(const FrameDesc& a, const Smem& S, ClusterShared
       if (tid == 0) n_scored += (unsigned long long)nh * (unsigned long long)N;
     } else if constexpr (SMEM_ROWS) {
       // Staged, with exact pruning: the trials still in the list are scored
-      // kStageQuads quads at a time; after the first stage the trial with
-      // the highest partial count is counted exactly (it leads from then
-      // on), and after every stage a trial whose partial count plus the
-      // points still to come cannot beat the lead's key leaves the list
-      // (U = -1).  Each remaining point adds at most one to a count and
+      // in stages (kStageQuads quads, then each stage half as long again);
+      // after the first stage the trial with the highest partial count is
+      // counted exactly (it leads from then on), and after every stage a
+      // trial whose partial count plus the points still to come cannot beat
+      // the lead's key leaves the list (U = -1; marked kDropped, or
+      // compacted away).  Each remaining point adds at most one to a count and
       // C_h <= U_h, so a trial dropped this way cannot win: the winner is
       // the one scoring every trial over every point gives, found by the
       // best-first counts below among the trials that stayed.
