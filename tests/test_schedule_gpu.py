@@ -266,3 +266,36 @@ def test_pruning_same_result(torch, case):
         n = np.diff(f.offsets)
         assert scored[0] == int(n[n >= w.model_dim].sum()) * H, scored
         print(f"pruning {case}: {scored[1] / scored[0]:.3f} of the pairs scored")
+
+
+@pytest.mark.parametrize("name", ["dense2d", "dense3d"])
+def test_pruning_with_tied_counts(torch, name):
+    """Noise-free clusters without outliers: nearly every trial counts every
+    point, so the winner is decided by the lowest index among equal counts.
+    The staged pass's lead and drops compare (count, index) keys; pruned
+    and unpruned runs agree bit for bit and both equal the oracle."""
+    import dataclasses
+    w = dataclasses.replace(synth.WORKLOADS[name], outlier_frac=0.0, noise_sigma=0.0)
+    sizes = np.random.default_rng(17).integers(512, 1600, 24).astype(np.int64)
+    f = synth.make_frame(w, sizes=sizes, gen_seed=91)
+    keep, frame = _device_frame(torch, f)
+    H = 1024
+    params = rvh.make_params(w.model_dim, H, w.tau, 21)
+    dev = torch.device("cuda", 0)
+    ctx = rvh.Context(0)
+    out = {}
+    try:
+        for on in (1, 0):
+            ctx.check(rvh.rvh_set_pruning(ctx.handle, on), "pruning")
+            outs = rvh.alloc_outputs(f.n_clusters, f.n_points, dev)
+            ctx.check(rvh.rvh_estimate(ctx.handle, frame, params, rvh.make_result(outs), None), "estimate")
+            torch.cuda.synchronize()
+            out[on] = _np(outs, f.n_points)
+    finally:
+        ctx.close()
+    for k in out[1]:
+        assert np.array_equal(out[1][k], out[0][k], equal_nan=True), k
+    assert (out[1]["inlier_count"] == np.diff(f.offsets)).mean() > 0.9  # the ties are real
+    o = G.run_oracle(f.azimuth, f.doppler, f.offsets, el=f.elevation, H=H, tau=w.tau, seed=21)
+    rep = G.compare(out[1], o, f.offsets)
+    assert not rep["mismatch"], rep["mismatch"][:10]
