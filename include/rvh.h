@@ -344,9 +344,10 @@ int rvh_get_stats(rvh_ctx* ctx, rvh_stats* out);
 int rvh_set_schedule(rvh_ctx* ctx, int32_t points_per_warp, int32_t hyps_per_lane);
 
 /* Staged scoring with exact pruning (default on): the scoring pass of a
- * cluster of at least 256 points whose rows fit shared memory (the
- * lanes-over-trials schedule, points_per_warp 1) runs in stages of 128
- * points; after the first, the trial with the highest partial count is
+ * cluster of at least 512 points whose rows fit shared memory (the
+ * lanes-over-trials schedule, points_per_warp 1) runs in stages, the first
+ * of 128 points and each later one half as long again; after the first,
+ * the trial with the highest partial count is
  * counted exactly and leads, and after each stage a trial whose partial
  * count plus the points still to come cannot beat the lead's (count, lower
  * index) key is dropped.  Counts only grow by one per point and the exact
